@@ -1,0 +1,171 @@
+"""One-particle bases and the sparse invariant index set (oracle; test infrastructure only).
+
+Paper passages followed:
+  * section 2.4: O(3) one-particle basis phi_nlm = R_n Y_l^m, k = (n, l, m),
+    invariance requires sum_t m_t = 0 and sum_t l_t even.
+  * section 2.2: SO(2) basis R_n e^{-i m theta}, k = (n, m), sum_t m_t = 0.
+  * section 2.3: torus basis e^{i m theta}, k = m, sum_t m_t = 0.
+  * section 2.5, Eq. 3: K_G^p(D) = {k invariant : ||k||_p <= D}; for p = 1 the
+    degree of a tuple is the sum of its one-particle degrees (n + l for O(3),
+    n + |m| for SO(2), |m| for the torus).
+  * section 1 / section 2.6: permutation symmetry, so only sorted tuples
+    (multisets) are kept.
+
+Readings of points the paper leaves open:
+  * The one-particle degree is wn*n + wl*l (the paper's n + l is wn = wl = 1;
+    the workloads use n + 2l).
+  * One-particle ids: O(3) id = (n - nmin)(lmax+1)^2 + l^2 + (l + m), i.e. n
+    outer, then l, then m ascending.  Torus id = m + mmax.  SO(2) id =
+    (n - nmin)(2 mmax + 1) + (m + mmax).
+  * A tuple is stored non-decreasing in id; the basis order is (nu, then
+    lexicographic on ids).  This one order fixes the coefficient draws and the
+    insertion order of Algorithm 1.
+  * p = 1 only (the sum of one-particle degrees) on the evaluated path; p = 2 and
+    p = infinity are provided for counting.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+import numpy as np
+
+
+@dataclass
+class OneParticleBasis:
+    """A finite one-particle basis: per id its labels, degree and symmetry charges."""
+    group: str            # "O3", "SO2" or "T"
+    labels: np.ndarray    # (K, 3) rows (n, l, m); unused labels are 0
+    deg: np.ndarray       # (K,) int64 one-particle degree
+    m: np.ndarray         # (K,) int64
+    l: np.ndarray         # (K,) int64 (zeros outside O(3))
+
+    @property
+    def K(self) -> int:
+        return int(self.deg.shape[0])
+
+
+def o3_basis(nmin: int, nmax: int, lmax: int, wn: int = 1, wl: int = 1) -> OneParticleBasis:
+    """k = (n, l, m), nmin <= n <= nmax, 0 <= l <= lmax, |m| <= l (section 2.4)."""
+    rows = [(n, l, m) for n in range(nmin, nmax + 1)
+            for l in range(lmax + 1) for m in range(-l, l + 1)]
+    lab = np.array(rows, dtype=np.int64)
+    return OneParticleBasis("O3", lab, wn * lab[:, 0] + wl * lab[:, 1],
+                            lab[:, 2].copy(), lab[:, 1].copy())
+
+
+def so2_basis(nmin: int, nmax: int, mmax: int, wn: int = 1, wm: int = 1) -> OneParticleBasis:
+    """k = (n, m), degree wn*n + wm*|m| (section 2.2, degree of section 2.5)."""
+    rows = [(n, 0, m) for n in range(nmin, nmax + 1) for m in range(-mmax, mmax + 1)]
+    lab = np.array(rows, dtype=np.int64)
+    return OneParticleBasis("SO2", lab, wn * lab[:, 0] + wm * np.abs(lab[:, 2]),
+                            lab[:, 2].copy(), np.zeros(len(rows), dtype=np.int64))
+
+
+def torus_basis(mmax: int) -> OneParticleBasis:
+    """k = m, -mmax <= m <= mmax, degree |m| (section 2.3 and section 2.5)."""
+    m = np.arange(-mmax, mmax + 1, dtype=np.int64)
+    lab = np.stack([np.zeros_like(m), np.zeros_like(m), m], axis=1)
+    return OneParticleBasis("T", lab, np.abs(m), m.copy(), np.zeros_like(m))
+
+
+def _sorted_tuples_within_degree(deg: np.ndarray, nu_max: int, deg_max: float, p: float):
+    """All non-decreasing id tuples of length 1..nu_max with ||deg||_p <= deg_max.
+
+    Yields (nu, T) with T an int64 array (count, nu).  Degree truncation is the
+    only filter here: a non-invariant tuple can still extend to an invariant one.
+    """
+    K = deg.shape[0]
+    ids = np.arange(K, dtype=np.int64)
+
+    def measure(d):       # per-tuple accumulated degree in the p-norm
+        if p == 1:
+            return d
+        if p == np.inf:
+            return d
+        return d ** p
+
+    def within(acc):
+        if p == 1:
+            return acc <= deg_max
+        if p == np.inf:
+            return acc <= deg_max
+        return acc <= deg_max ** p + 1e-9
+
+    def combine(acc, d):
+        if p == np.inf:
+            return np.maximum(acc, d)
+        return acc + d
+
+    dm = measure(deg.astype(np.float64))
+    keep = within(dm)
+    T = ids[keep][:, None]
+    acc = dm[keep]
+    yield 1, T
+    for nu in range(2, nu_max + 1):
+        last = T[:, -1]
+        new_T, new_acc = [], []
+        for j in range(K):
+            a = combine(acc, dm[j])
+            sel = (last <= j) & within(a)
+            if np.any(sel):
+                rows = T[sel]
+                new_T.append(np.concatenate([rows, np.full((rows.shape[0], 1), j, np.int64)], axis=1))
+                new_acc.append(a[sel])
+        if not new_T:
+            return
+        T = np.concatenate(new_T, axis=0)
+        acc = np.concatenate(new_acc, axis=0)
+        order = np.lexsort(T.T[::-1])        # lexicographic on (k_1, ..., k_nu)
+        T, acc = T[order], acc[order]
+        yield nu, T
+
+
+@dataclass
+class IndexSet:
+    """The basis set K: sorted tuples in canonical order (nu, lexicographic)."""
+    basis: OneParticleBasis
+    nu_max: int
+    deg_max: int
+    tuples: np.ndarray     # (n_basis, nu_max) int64, -1 padded
+    nu: np.ndarray         # (n_basis,) int64 correlation order
+    deg: np.ndarray        # (n_basis,) int64 summed one-particle degree
+
+    @property
+    def n_basis(self) -> int:
+        return int(self.nu.shape[0])
+
+    def counts_per_nu(self) -> list[int]:
+        return [int(np.sum(self.nu == v)) for v in range(1, self.nu_max + 1)]
+
+    def as_tuples(self) -> list[tuple]:
+        return [tuple(int(x) for x in row[:n]) for row, n in zip(self.tuples, self.nu)]
+
+
+def index_set(basis: OneParticleBasis, nu_max: int, deg_max: int, p: float = 1,
+              require_l_even: bool | None = None) -> IndexSet:
+    """K_G^p(D) restricted to 1 <= nu <= nu_max (section 2.5, Eq. 3).
+
+    Invariance filter: sum_t m_t = 0 for every group (sections 2.2-2.4); for O(3)
+    additionally sum_t l_t even (section 2.4).
+    """
+    if require_l_even is None:
+        require_l_even = basis.group == "O3"
+    blocks, nus = [], []
+    for nu, T in _sorted_tuples_within_degree(basis.deg, nu_max, deg_max, p):
+        ok = basis.m[T].sum(axis=1) == 0
+        if require_l_even:
+            ok &= (basis.l[T].sum(axis=1) % 2) == 0
+        T = T[ok]
+        pad = np.full((T.shape[0], nu_max), -1, dtype=np.int64)
+        pad[:, :nu] = T
+        blocks.append(pad)
+        nus.append(np.full(T.shape[0], nu, dtype=np.int64))
+    tuples = np.concatenate(blocks, axis=0) if blocks else np.zeros((0, nu_max), np.int64)
+    nu = np.concatenate(nus) if nus else np.zeros(0, np.int64)
+    d = np.where(tuples >= 0, basis.deg[np.maximum(tuples, 0)], 0).sum(axis=1)
+    return IndexSet(basis, nu_max, deg_max, tuples, nu, d.astype(np.int64))
+
+
+def workload_index_set(w) -> IndexSet:
+    """Index set of a ``workloads.Workload`` (O(3), p = 1, degree wn*n + wl*l)."""
+    b = o3_basis(w.nmin, w.nmax, w.lmax, w.wn, w.wl)
+    return index_set(b, w.nu_max, w.deg_max)

@@ -1,0 +1,110 @@
+"""Pins for the oracle's one-particle basis R_n Y_lm, the pooling A_nlm and the forces.
+
+Convention-free identities (addition theorem, orthonormality by exact
+quadrature), scipy's complex harmonics, Chebyshev's closed form, finite
+differences and neighbour-permutation invariance.
+"""
+from math import pi
+
+import numpy as np
+import pytest
+import scipy.special as sps
+
+from oracle.pooling import forces, lm_index, one_particle, pool_A, radial, real_sph_harm
+from oracle.basis import o3_basis, index_set
+from oracle.evaluate import grad_naive, phi_naive
+import workloads as W
+
+LMAX = 6
+
+
+def unit(n, seed):
+    d = np.random.default_rng(seed).standard_normal((n, 3))
+    return d / np.linalg.norm(d, axis=1)[:, None]
+
+
+def test_addition_theorem():
+    """sum_m Y_lm(u)^2 = (2l + 1) / (4 pi) for every direction u."""
+    Y, _ = real_sph_harm(unit(50, 1) * 2.3, LMAX)
+    for l in range(LMAX + 1):
+        s = sum(Y[:, lm_index(l, m)] ** 2 for m in range(-l, l + 1))
+        assert np.allclose(s, (2 * l + 1) / (4 * pi), rtol=1e-12)
+
+
+def test_orthonormality_by_quadrature():
+    """Gauss-Legendre in cos(theta) x uniform phi grid integrates Y Y' exactly for l, l' <= 6."""
+    nu, nphi = 16, 32
+    x, wx = np.polynomial.legendre.leggauss(nu)
+    phis = 2 * pi * np.arange(nphi) / nphi
+    X, PH = np.meshgrid(x, phis, indexing="ij")
+    st = np.sqrt(1 - X ** 2)
+    P = np.stack([st * np.cos(PH), st * np.sin(PH), X], axis=-1).reshape(-1, 3)
+    w = (wx[:, None] * np.full(nphi, 2 * pi / nphi)[None, :]).reshape(-1)
+    Y, _ = real_sph_harm(P, LMAX)
+    G = (Y * w[:, None]).T @ Y
+    assert np.allclose(G, np.eye(G.shape[0]), atol=1e-12)
+
+
+def test_against_scipy_complex_harmonics():
+    """Ours (no Condon-Shortley phase): Y_lm = sqrt2 (-1)^m Re Y_l^m, Y_l-m = sqrt2 (-1)^m Im Y_l^m."""
+    P = unit(40, 2) * 0.7
+    Y, _ = real_sph_harm(P, LMAX)
+    theta = np.arccos(np.clip(P[:, 2] / np.linalg.norm(P, axis=1), -1, 1))
+    phi = np.arctan2(P[:, 1], P[:, 0])
+    for l in range(LMAX + 1):
+        ref0 = sps.sph_harm_y(l, 0, theta, phi)
+        assert np.allclose(Y[:, lm_index(l, 0)], ref0.real, atol=1e-12)
+        for m in range(1, l + 1):
+            ref = sps.sph_harm_y(l, m, theta, phi)
+            assert np.allclose(Y[:, lm_index(l, m)], np.sqrt(2) * (-1) ** m * ref.real, atol=1e-12)
+            assert np.allclose(Y[:, lm_index(l, -m)], np.sqrt(2) * (-1) ** m * ref.imag, atol=1e-12)
+
+
+def test_radial_chebyshev_closed_form():
+    """T_n(cos t) = cos(n t): R_n(r) = cos(n t)(1 - r/rc)^2 with cos t = 2 r/rc - 1."""
+    rc = 5.0
+    r = np.linspace(0.01, 4.99, 37)
+    R, _ = radial(r, 1, 8, rc)
+    t = np.arccos(2 * r / rc - 1)
+    for i, n in enumerate(range(1, 9)):
+        assert np.allclose(R[:, i], np.cos(n * t) * (1 - r / rc) ** 2, atol=1e-13)
+
+
+def test_gradients_by_finite_differences():
+    rc, h = 5.0, 1e-6
+    P = unit(7, 3) * np.random.default_rng(5).uniform(0.5, 4.5, 7)[:, None]
+    phi0, g = one_particle(P, 1, 8, LMAX, rc, with_grad=True)
+    for d in range(3):
+        Pp, Pm = P.copy(), P.copy()
+        Pp[:, d] += h
+        Pm[:, d] -= h
+        fd = (one_particle(Pp, 1, 8, LMAX, rc)[0] - one_particle(Pm, 1, 8, LMAX, rc)[0]) / (2 * h)
+        assert np.allclose(fd, g[:, :, d], atol=2e-8)
+
+
+def test_pooling_forces_permutation_and_fd():
+    """A is invariant under permutation of neighbours, F permutes with them; F = -dphi/dr by FD."""
+    rc = 5.0
+    b = o3_basis(1, 3, 2, 1, 2)
+    s = index_set(b, 3, 8)
+    c = W.draw_c(s.deg, 1)
+    offsets, P = W.draw_neighbours(3, rc=rc, j_range=(4, 7))
+    A = pool_A(P, offsets, 1, 3, 2, rc)
+    G = grad_naive(A, s, c)
+    F = forces(P, offsets, G, 1, 3, 2, rc)
+    perm = np.arange(P.shape[0])
+    a, bb = offsets[1], offsets[2]
+    perm[a:bb] = perm[a:bb][::-1]
+    A2 = pool_A(P[perm], offsets, 1, 3, 2, rc)
+    assert np.allclose(A2, A, rtol=1e-13, atol=1e-14)
+    F2 = forces(P[perm], offsets, G, 1, 3, 2, rc)
+    assert np.allclose(F2, F[perm], rtol=1e-12, atol=1e-14)
+    h = 1e-6
+    for j in (0, a + 1, P.shape[0] - 1):
+        for d in range(3):
+            Pp, Pm = P.copy(), P.copy()
+            Pp[j, d] += h
+            Pm[j, d] -= h
+            fp = phi_naive(pool_A(Pp, offsets, 1, 3, 2, rc), s, c).sum()
+            fm = phi_naive(pool_A(Pm, offsets, 1, 3, 2, rc), s, c).sum()
+            assert abs(-(fp - fm) / (2 * h) - F[j, d]) < 1e-7 * max(1.0, abs(F[j, d]))
