@@ -1,0 +1,240 @@
+/*
+ * ace.h - C ABI of the GB300 (sm_103a) implementation of the recursive
+ * contraction of sparse symmetric tensors for symmetry-adapted n-correlations
+ * (Kaliuzhnyi & Ortner, arXiv 2202.04140).
+ *
+ * The library evaluates, for a batch of environments e,
+ *     phi[e][ch] = sum_{k in K} c[k][ch] * prod_{t=1}^{nu(k)} A[e][k_t]        (Eq. 1, Eq. 2)
+ * over a sparse, permutation-sorted, degree-truncated set K of invariant
+ * multi-indices, by the recursive computational graph of section 2.6: every
+ * node AA_k of order >= 2 is the product AA_{k1} * AA_{k2} of two earlier nodes
+ * (Eq. 4), auxiliary nodes (c = 0) fill in the sub-products that are not in K,
+ * and the graph is built by Algorithm 1 (section 3.2) or Algorithm 2
+ * (section 3.3).  It also evaluates the adjoint dphi/dA and, for O(3) bases,
+ * the neighbour pooling A_nlm = sum_j R_n(r_j) Y_lm(r_j/|r_j|) and its adjoint
+ * (the forces).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns an ace_status and never throws or aborts; on error
+ *    a thread-local message is available from ace_last_error().
+ *  - Handles (ace_spec, ace_dag) are owned by the library; free them with
+ *    ace_spec_free / ace_dag_free.  Device buffers of a handle are allocated by
+ *    the library with cudaMalloc on the current device, the first time the
+ *    handle is used on that device (ace_dag_upload does it explicitly).
+ *  - Tensors passed by pointer are owned by the caller.  "dev" pointers are
+ *    CUDA device pointers on the current device, contiguous, 16-byte aligned;
+ *    "host" pointers are ordinary host memory.  Row-major layouts throughout.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *    work is enqueued asynchronously; nothing synchronises except
+ *    ace_stream_status.  Launch errors are reported at enqueue time.
+ *  - One-particle ids: O(3) id = (n - nmin)(lmax+1)^2 + l^2 + (l + m);
+ *    SO(2) id = (n - nmin)(2 lmax + 1) + (m + lmax); torus id = m + lmax.
+ *  - Basis order ("canonical"): by correlation order nu, then lexicographic on
+ *    the non-decreasing id tuple.  c is given in this order.
+ */
+#ifndef ACE_H_
+#define ACE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ACE_ABI_VERSION 1
+
+typedef enum {
+  ACE_OK = 0,
+  ACE_ERR_INVALID_ARG = -1, /* bad pointer, size, shape, alignment or parameter */
+  ACE_ERR_OOM = -2,         /* host or device allocation failed */
+  ACE_ERR_CUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+  ACE_ERR_TIMEOUT = -4,     /* a bounded device wait gave up (status word) */
+  ACE_ERR_BOUNDS = -5,      /* a checked kernel saw an out-of-range index (status word) */
+  ACE_ERR_UNSUPPORTED = -6, /* valid request this build does not implement */
+  ACE_ERR_NO_DEVICE = -7    /* no CUDA device is available */
+} ace_status;
+
+enum { ACE_GROUP_O3 = 0, ACE_GROUP_SO2 = 1, ACE_GROUP_TORUS = 2 };
+enum { ACE_ALGO_1 = 1, ACE_ALGO_2 = 2 };
+enum { ACE_SPLIT_BALANCED = 0, ACE_SPLIT_PEEL = 1 };
+enum { ACE_F32 = 0, ACE_F64 = 1 };
+enum { ACE_READOUT_PLAIN = 0, ACE_READOUT_COMPENSATED = 1, ACE_READOUT_FP64_FINAL = 2 };
+
+typedef struct ace_spec ace_spec; /* the index set K (library-owned) */
+typedef struct ace_dag ace_dag;   /* the graph G and its device plan (library-owned) */
+
+/* Index-set parameters (sections 2.2-2.5, Eq. 3, with p = 1 on the evaluated path).
+ *  O(3):  k = (n, l, m), nmin <= n <= nmax, 0 <= l <= lmax, |m| <= l,
+ *         degree wn*n + wl*l; invariance sum m = 0 and (if require_l_even) sum l even.
+ *  SO(2): k = (n, m), |m| <= lmax, degree wn*n + wl*|m|; invariance sum m = 0.
+ *  Torus: k = m, |m| <= lmax, degree |m|; invariance sum m = 0.
+ *  p_norm: 1 (sum of one-particle degrees), 2, or 0 for the maximum.
+ *  nu_max in [1, 8]. */
+typedef struct {
+  int32_t group;
+  int32_t nmin, nmax;
+  int32_t lmax;
+  int32_t nu_max;
+  int32_t deg_max;
+  int32_t wn, wl;
+  int32_t p_norm;
+  int32_t require_l_even;
+} ace_spec_params;
+
+/* ---- library ---------------------------------------------------------------- */
+
+/* Thread-local message for the last error of this thread (never NULL). */
+const char* ace_last_error(void);
+/* ACE_ABI_VERSION of the loaded library. */
+int32_t ace_abi_version(void);
+
+/* ---- index set (host only, no GPU needed) ----------------------------------- */
+
+/* Build K_G^p(D) (section 2.5, Eq. 3; invariance of sections 2.2-2.4).
+ * params: host, read only.  *out receives a new handle.
+ * Errors: INVALID_ARG for out-of-range parameters, OOM. */
+ace_status ace_build_spec(const ace_spec_params* params, ace_spec** out);
+
+/* Sizes of the set.  n_basis = |K|; K = number of one-particle functions;
+ * counts_per_nu (host, may be NULL) receives nu_max entries: |K| per order 1..nu_max. */
+ace_status ace_spec_info(const ace_spec* spec, int64_t* n_basis, int32_t* K, int64_t* counts_per_nu);
+
+/* Copy the canonical tuples (host int32 [n_basis][nu_max], -1 padded) and the
+ * total degree of each tuple (host int32 [n_basis]).  Either pointer may be NULL. */
+ace_status ace_spec_tuples(const ace_spec* spec, int32_t* tuples, int32_t* deg);
+
+void ace_spec_free(ace_spec* spec);
+
+/* ---- graph (host only) --------------------------------------------------------- */
+
+/* Build the computational graph G (section 2.6) with Algorithm 1 (algo = 1,
+ * section 3.2) or Algorithm 2 (algo = 2, section 3.3, parameter n_split >= 1).
+ * Leaves are the K one-particle nodes (ids 0..K-1); the basis is inserted in
+ * canonical order; node ids are insertion order.  split_rule fixes the order in
+ * which decompositions are tried (ACE_SPLIT_BALANCED: part sizes nu/2 down to
+ * 1; ACE_SPLIT_PEEL: 1 up to nu/2).  Also builds the evaluation plan (host side).
+ * Errors: INVALID_ARG, OOM. */
+ace_status ace_build_dag(const ace_spec* spec, int32_t algo, int32_t split_rule, int32_t n_split,
+                         ace_dag** out);
+
+/* Counts: n_nodes (all nodes incl. leaves), n_aux (auxiliary nodes, c = 0,
+ * section 2.6), n_operands (nodes of order >= 2 used as a factor of another
+ * node), n_levels (highest correlation order = number of topological levels).
+ * Any pointer may be NULL. */
+ace_status ace_dag_info(const ace_dag* dag, int64_t* n_nodes, int64_t* n_aux, int64_t* n_operands,
+                        int32_t* n_levels);
+
+/* Export G in canonical ids (host buffers of n_nodes entries, any may be NULL):
+ * left/right factor ids (-1 for leaves), level = correlation order, is_aux;
+ * basis_node (host int32 [n_basis], may be NULL) = node id of each basis tuple. */
+ace_status ace_dag_export(const ace_dag* dag, int32_t* left, int32_t* right, int32_t* level,
+                          uint8_t* is_aux, int32_t* basis_node);
+
+/* Plan statistics: n_slots (values stored per environment: leaves + operand
+ * nodes), n_sinks (nodes of order >= 2 without consumers, folded into the
+ * readout), n_entries (entries of the symmetric sink matrix), smem_bytes_f32
+ * (shared memory per environment of the fused FP32 forward+adjoint kernel).
+ * Any pointer may be NULL. */
+ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_sinks, int64_t* n_entries,
+                             int64_t* smem_bytes_f32);
+
+/* Copy one array of the evaluation plan, for inspection and tests.  `name` is
+ * one of: "slot_node", "slot_basis", "n_g", "fwd_slot", "fwd_l", "fwd_r",
+ * "fwd_off", "rev_slot", "rev_l", "rev_r", "rev_off", and for the symmetric
+ * ("sym_") and one-sided ("one_") sink forms: "tasks" (4 int32 per task: row,
+ * flags, factor slots), "slice_off", "slice_steps", "col", "ebasis", "ew2".
+ * Every array is exported as int32.  *count receives the number of int32
+ * values; out (host) may be NULL to query the size.  Errors: INVALID_ARG for an
+ * unknown name. */
+ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out, int64_t* count);
+
+void ace_dag_free(ace_dag* dag);
+
+/* ---- evaluation (device) ------------------------------------------------------ */
+
+/* Allocate and upload the device plan on the current device (done implicitly
+ * by the first evaluation; call it first when the evaluation is to be captured
+ * in a CUDA graph). */
+ace_status ace_dag_upload(ace_dag* dag, void* stream);
+
+/* Forward: phi = sum_k c_k AA_k (Eq. 2) evaluated through G (Eq. 4).
+ *  A   : dev [n_env][K] in dtype (ACE_F32 float, ACE_F64 double).
+ *  c   : dev [n_basis][n_out] in dtype, canonical basis order.  Bound into the
+ *        plan by a small gather kernel on `stream`; NULL reuses the
+ *        coefficients bound by the previous call with the same n_out and dtype.
+ *  phi : dev [n_env][n_out] in dtype, written.
+ *  n_out in {1, 2, 4, 8, 16}.  readout: ACE_READOUT_PLAIN (FP32 sums),
+ *  ACE_READOUT_COMPENSATED (per-task partial sums in FP32, combined with
+ *  compensated (TwoSum) FP32 accumulation), ACE_READOUT_FP64_FINAL (partials
+ *  combined in FP64).  For ACE_F64 all arithmetic is FP64 and readout is ignored.
+ * Errors: INVALID_ARG (null/misaligned pointer, n_env < 0, n_out), UNSUPPORTED,
+ * NO_DEVICE, CUDA, OOM.  n_env = 0 is a no-op. */
+ace_status ace_eval(ace_dag* dag, const void* A, const void* c, int64_t n_env, int32_t n_out,
+                    int32_t dtype, int32_t readout, void* phi, void* stream);
+
+/* Forward and reverse sweep (the adjoint of Eq. 4; not in the paper) fused in
+ * one kernel: dA[e][k] = sum_ch phi_bar[e][ch] dphi[e][ch]/dA[e][k].
+ *  phi_bar: dev [n_env][n_out] in dtype, or NULL meaning all ones.
+ *  phi    : dev [n_env][n_out] or NULL (then phi is not written).
+ *  dA     : dev [n_env][K] in dtype, written.
+ * Other arguments and errors as ace_eval. */
+ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void* phi_bar,
+                         int64_t n_env, int32_t n_out, int32_t dtype, int32_t readout, void* phi,
+                         void* dA, void* stream);
+
+/* The plain FP64 GPU evaluation of G: one thread per environment walks every
+ * node in id order (Eq. 4), keeping every node value in global memory, reads
+ * out phi and, if dA != NULL, runs the reverse sweep.  It is the baseline the
+ * fused kernels are compared with.
+ *  workspace: dev, at least ace_eval_plain_workspace_bytes(...) bytes, owned by
+ *  the caller, contents irrelevant on entry.
+ * Other arguments as ace_eval_grad (FP64 only, n_out in {1..16}). */
+ace_status ace_eval_plain_workspace_bytes(const ace_dag* dag, int64_t n_env, int32_t with_grad,
+                                          size_t* bytes);
+ace_status ace_eval_plain_f64(ace_dag* dag, const double* A, const double* c, const double* phi_bar,
+                              int64_t n_env, int32_t n_out, double* phi, double* dA, void* workspace,
+                              size_t workspace_bytes, void* stream);
+
+/* ---- neighbour pooling (device, O(3) only) ------------------------------------ */
+
+/* A[e][id(n,l,m)] = sum_{j in env e} R_n(|r_j|) Y_lm(r_j/|r_j|)   (Eq. 2, section 2.4)
+ * with R_n(r) = T_n(2r/rc - 1)(1 - r/rc)^2 (Chebyshev T_n, n = nmin..nmax) and
+ * real orthonormal spherical harmonics without Condon-Shortley phase.
+ *  pos     : dev float [n_pairs][3], neighbour positions relative to the centre.
+ *  offsets : dev int64 [n_env + 1], CSR ranges of the neighbours of each env
+ *            (offsets[0] = 0, non-decreasing, offsets[n_env] = n_pairs).
+ *  A       : dev float [n_env][K], K = (nmax-nmin+1)(lmax+1)^2, written.
+ * Neighbours with |r| >= rc or |r| = 0 contribute zero.  lmax <= 8.
+ * Errors: INVALID_ARG, UNSUPPORTED (lmax > 8), CUDA. */
+ace_status ace_pool_A(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs,
+                      float rc, int32_t nmin, int32_t nmax, int32_t lmax, float* A, void* stream);
+
+/* Adjoint of ace_pool_A: dpos[j] = sum_k dA[e(j)][k] grad_{r_j} (R_n Y_lm)(r_j).
+ * Forces are F_j = -dpos[j] when dA = dphi/dA.
+ *  dA   : dev float [n_env][K];  dpos : dev float [n_pairs][3], written. */
+ace_status ace_pool_A_grad(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs,
+                           float rc, int32_t nmin, int32_t nmax, int32_t lmax, const float* dA,
+                           float* dpos, void* stream);
+
+/* ---- status / utilities --------------------------------------------------------- */
+
+/* Synchronise `stream` and read the device status word of `dag` (written by
+ * kernels that check DAG indices or bound their waits).  Returns ACE_OK,
+ * ACE_ERR_BOUNDS or ACE_ERR_TIMEOUT, and clears the word. */
+ace_status ace_stream_status(ace_dag* dag, void* stream);
+
+/* Device properties the planner uses: SM count and opt-in shared memory per block. */
+ace_status ace_device_info(int32_t* sm_count, int32_t* smem_optin_bytes, int32_t* cc_major,
+                           int32_t* cc_minor);
+
+/* FP32 FMA throughput microbenchmark: runs `iters` dependent FMA chains per
+ * thread on every SM and writes the elapsed device time (ms) and the FMA
+ * count; used to measure the ALU roofline on the device. */
+ace_status ace_fma_peak(int64_t iters, double* ms, double* fma_count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACE_H_ */

@@ -1,0 +1,100 @@
+// Internal host-side structures of libace: index set, graph and evaluation plan.
+//
+// The index set follows sections 2.2-2.5 (Eq. 3), the graph section 2.6 with
+// Algorithm 1 (section 3.2) / Algorithm 2 (section 3.3), and the plan is the
+// GPU layout of the recursive evaluation of Eq. 4 (not in the paper).
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../../include/ace.h"
+
+namespace ace {
+
+constexpr int kMaxNu = 8;
+
+// Error reporting: a status plus a thread-local message.
+ace_status fail(ace_status st, const std::string& msg);
+void clear_error();
+
+struct Spec {
+  ace_spec_params p{};
+  int32_t K = 0;                      // one-particle functions
+  std::vector<int32_t> one_deg;       // per one-particle id: degree
+  std::vector<int32_t> one_m;         // per id: m
+  std::vector<int32_t> one_l;         // per id: l (O(3)), 0 otherwise
+  int32_t nu_max = 0;
+  std::vector<int32_t> tuples;        // [n_basis][nu_max], -1 padded, canonical order
+  std::vector<int32_t> nu;            // [n_basis]
+  std::vector<int32_t> deg;           // [n_basis] total degree (sum of one-particle degrees)
+  std::vector<int64_t> counts_per_nu; // [nu_max]
+  int64_t n_basis() const { return (int64_t)nu.size(); }
+};
+
+ace_status build_spec(const ace_spec_params& p, std::unique_ptr<Spec>& out);
+
+// Graph G in canonical (insertion) ids.
+struct Graph {
+  int32_t K = 0;
+  int32_t nu_max = 0;
+  std::vector<int32_t> left, right;   // -1 for leaves
+  std::vector<int32_t> order;         // correlation order (topological level)
+  std::vector<uint8_t> is_aux;
+  std::vector<int32_t> basis_node;    // basis index -> node id
+  std::vector<int32_t> node_basis;    // node id -> basis index or -1
+  int64_t n_nodes() const { return (int64_t)left.size(); }
+};
+
+ace_status build_graph(const Spec& spec, int algo, int split_rule, int n_split, Graph& g);
+
+// Evaluation plan (section 2.6 recursion laid out for the fused kernels).
+//
+// Slots are the values kept per environment: [0, K) the leaves A_k, then the
+// operand nodes (order >= 2 with at least one consumer).  Operand nodes whose
+// consumers include other operand nodes ("inner" operands) come first, so that
+// the adjoint accumulators G exist exactly for slots [0, n_g).  Sink nodes
+// (order >= 2, no consumer) are never stored: sink i = [p, q] contributes
+// c_i AA_p AA_q to phi, which is folded into a sparse contraction over slots.
+struct Task {
+  int32_t row;    // slot whose sparse row this task covers (-1: padding)
+  int32_t flags;  // bit0: first task of its row (adds the row's own coefficient)
+                  // bit1: row is a top operand (push to its factors) else G row
+  int32_t pl, pr; // factor slots of a top operand row, else -1
+};
+
+struct TaskSet {
+  // Tasks grouped in slices of 32 (one per lane); entries of a slice are
+  // interleaved: entry k of lane j sits at slice_off[s] + 32 k + j.
+  std::vector<Task> tasks;            // [n_slices * 32]
+  std::vector<int32_t> slice_off;     // [n_slices + 1] entry offsets
+  std::vector<int32_t> slice_steps;   // [n_slices]
+  std::vector<int32_t> col;           // [n_entries_padded] slot index
+  std::vector<int32_t> ebasis;        // [n_entries_padded] basis index (-1 padding)
+  std::vector<uint8_t> ew2;           // [n_entries_padded] 1: weight 2 (diagonal of the symmetric form)
+  int64_t n_entries = 0;              // real (unpadded) entries
+  int32_t n_slices() const { return (int32_t)slice_steps.size(); }
+};
+
+struct LevelList {
+  std::vector<int32_t> slot, l, r;    // node slot and its two factor slots
+  std::vector<int32_t> off;           // level offsets (size n_levels + 1)
+};
+
+struct Plan {
+  int32_t K = 0, n_slots = 0, n_g = 0;
+  int64_t n_sinks = 0;
+  std::vector<int32_t> node_slot;     // node id -> slot or -1
+  std::vector<int32_t> slot_node;     // slot -> node id
+  std::vector<int32_t> slot_basis;    // slot -> basis index or -1 (linear coefficient)
+  LevelList fwd;                      // operand nodes by increasing order
+  LevelList rev;                      // inner operand nodes by decreasing order
+  TaskSet sym;                        // symmetric sink form (forward + adjoint)
+  TaskSet one;                        // one-sided sink form (forward only)
+};
+
+ace_status build_plan(const Spec& spec, const Graph& g, int task_len, Plan& plan);
+
+}  // namespace ace

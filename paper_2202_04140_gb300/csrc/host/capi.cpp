@@ -1,0 +1,666 @@
+// extern "C" entry points of libace (include/ace.h).
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../kernels/fused.cuh"
+#include "../kernels/launch.hpp"
+#include "ace_internal.hpp"
+
+namespace ace {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+ace_status fail(ace_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+}  // namespace ace
+
+using namespace ace;
+
+struct ace_spec {
+  std::unique_ptr<Spec> s;
+};
+
+namespace {
+
+struct DevTaskSet {
+  int4* tasks = nullptr;
+  int32_t* slice_off = nullptr;
+  int32_t* slice_steps = nullptr;
+  int32_t* col = nullptr;
+  int32_t* ebasis = nullptr;
+  uint8_t* ew2 = nullptr;
+  int32_t n_slices = 0;
+  int64_t n_pad = 0;
+  // coefficients bound into this task set
+  void* vals = nullptr;
+  size_t vals_bytes = 0;
+  void* lin = nullptr;
+  size_t lin_bytes = 0;
+  bool bound = false;
+  int bound_dtype = -1, bound_nout = -1;
+};
+
+}  // namespace
+
+struct ace_dag {
+  int32_t K = 0;
+  int64_t n_basis = 0;
+  Graph g;
+  Plan plan;
+  int device = -1;
+  int sm_count = 0, smem_optin = 0;
+  int32_t *fwd_slot = nullptr, *fwd_l = nullptr, *fwd_r = nullptr;
+  int32_t *rev_slot = nullptr, *rev_l = nullptr, *rev_r = nullptr;
+  int32_t *node_left = nullptr, *node_right = nullptr, *node_basis = nullptr, *slot_basis = nullptr;
+  DevTaskSet sym, one;
+  uint32_t* status = nullptr;
+  std::vector<void*> allocations;
+};
+
+namespace {
+
+ace_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? ACE_ERR_OOM : ACE_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename V>
+ace_status upload_vec(ace_dag* d, const std::vector<V>& v, V** out, cudaStream_t st) {
+  *out = nullptr;
+  size_t bytes = std::max<size_t>(v.size() * sizeof(V), 16);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  d->allocations.push_back(p);
+  if (!v.empty()) {
+    e = cudaMemcpyAsync(p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  }
+  *out = static_cast<V*>(p);
+  return ACE_OK;
+}
+
+ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStream_t st) {
+  std::vector<int4> t4(ts.tasks.size());
+  for (size_t i = 0; i < ts.tasks.size(); ++i)
+    t4[i] = make_int4(ts.tasks[i].row, ts.tasks[i].flags, ts.tasks[i].pl, ts.tasks[i].pr);
+  ace_status s;
+  if ((s = upload_vec(d, t4, &dt.tasks, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.slice_off, &dt.slice_off, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.slice_steps, &dt.slice_steps, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.col, &dt.col, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.ebasis, &dt.ebasis, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.ew2, &dt.ew2, st)) != ACE_OK) return s;
+  dt.n_slices = ts.n_slices();
+  dt.n_pad = (int64_t)ts.col.size();
+  return ACE_OK;
+}
+
+// Host-side validation of every index the kernels read (done once, before upload).
+ace_status validate_plan(const Plan& p) {
+  auto in = [](int32_t v, int32_t hi) { return v >= 0 && v < hi; };
+  for (size_t i = 0; i < p.fwd.slot.size(); ++i)
+    if (!in(p.fwd.slot[i], p.n_slots) || !in(p.fwd.l[i], p.n_slots) || !in(p.fwd.r[i], p.n_slots))
+      return fail(ACE_ERR_BOUNDS, "plan: forward index out of range");
+  for (size_t i = 0; i < p.rev.slot.size(); ++i)
+    if (!in(p.rev.slot[i], p.n_g) || !in(p.rev.l[i], p.n_g) || !in(p.rev.r[i], p.n_g))
+      return fail(ACE_ERR_BOUNDS, "plan: adjoint index out of range");
+  for (const TaskSet* ts : {&p.sym, &p.one}) {
+    for (int32_t c : ts->col)
+      if (!in(c, p.n_slots)) return fail(ACE_ERR_BOUNDS, "plan: entry column out of range");
+    for (const Task& t : ts->tasks) {
+      if (t.row < 0) continue;
+      if (!in(t.row, p.n_slots)) return fail(ACE_ERR_BOUNDS, "plan: task row out of range");
+      if ((t.flags & 2) && (!in(t.pl, p.n_g) || !in(t.pr, p.n_g)))
+        return fail(ACE_ERR_BOUNDS, "plan: task factor out of range");
+    }
+  }
+  return ACE_OK;
+}
+
+ace_status ensure_uploaded(ace_dag* d, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(ACE_ERR_NO_DEVICE, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  if (d->device >= 0) {
+    if (d->device != dev) return fail(ACE_ERR_UNSUPPORTED, "graph was uploaded to another device");
+    return ACE_OK;
+  }
+  cudaDeviceGetAttribute(&d->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&d->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  ace_status s = validate_plan(d->plan);
+  if (s != ACE_OK) return s;
+  const Plan& p = d->plan;
+  if ((s = upload_vec(d, p.fwd.slot, &d->fwd_slot, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, p.fwd.l, &d->fwd_l, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, p.fwd.r, &d->fwd_r, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, p.rev.slot, &d->rev_slot, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, p.rev.l, &d->rev_l, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, p.rev.r, &d->rev_r, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, d->g.left, &d->node_left, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, d->g.right, &d->node_right, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, d->g.node_basis, &d->node_basis, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, p.slot_basis, &d->slot_basis, st)) != ACE_OK) return s;
+  if ((s = upload_tasks(d, p.sym, d->sym, st)) != ACE_OK) return s;
+  if ((s = upload_tasks(d, p.one, d->one, st)) != ACE_OK) return s;
+  void* stw = nullptr;
+  if ((e = cudaMalloc(&stw, 16)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  d->allocations.push_back(stw);
+  d->status = static_cast<uint32_t*>(stw);
+  if ((e = cudaMemsetAsync(stw, 0, 16, st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  // the host vectors above must outlive the copies
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  d->device = dev;
+  return ACE_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+int nout_pad_of(int n_out) { return n_out == 1 ? 1 : 16; }
+
+ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype, cudaStream_t st) {
+  const int npad = nout_pad_of(n_out);
+  const size_t tsz = dtype == ACE_F32 ? 4 : 8;
+  if (c == nullptr) {
+    if (!dt.bound || dt.bound_dtype != dtype || dt.bound_nout != n_out)
+      return fail(ACE_ERR_INVALID_ARG, "c is NULL and no coefficients of this n_out/dtype are bound");
+    return ACE_OK;
+  }
+  const size_t vb = std::max<size_t>((size_t)dt.n_pad * npad * tsz, 16);
+  const size_t lb = std::max<size_t>((size_t)d->plan.n_slots * npad * tsz, 16);
+  cudaError_t e;
+  if (vb > dt.vals_bytes) {
+    if (dt.vals) cudaFree(dt.vals);
+    dt.vals = nullptr;
+    dt.vals_bytes = 0;
+    if ((e = cudaMalloc(&dt.vals, vb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    dt.vals_bytes = vb;
+  }
+  if (lb > dt.lin_bytes) {
+    if (dt.lin) cudaFree(dt.lin);
+    dt.lin = nullptr;
+    dt.lin_bytes = 0;
+    if ((e = cudaMalloc(&dt.lin, lb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    dt.lin_bytes = lb;
+  }
+  e = launch_bind(dtype, c, n_out, npad, dt.ebasis, dt.ew2, dt.n_pad, dt.vals, d->slot_basis, d->plan.n_slots,
+                  dt.lin, st);
+  if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
+  dt.bound = true;
+  dt.bound_dtype = dtype;
+  dt.bound_nout = n_out;
+  return ACE_OK;
+}
+
+bool checked_mode() {
+  const char* v = std::getenv("ACE_CHECKED");
+  return v && v[0] && v[0] != '0';
+}
+
+// Environments per CTA: the largest compiled E whose shared-memory tile fits,
+// with E * NOUT <= 64 accumulators per lane, and not so large that fewer tiles
+// than SMs remain.
+ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t n_env, int* E_out, int* nt_out,
+                       size_t* smem_out, const void** kern_out) {
+  const int cands_f32_1[] = {16, 8, 4, 2, 1};
+  const int cands_f32_16[] = {4, 2, 1};
+  const int cands_f64_1[] = {8, 4, 2, 1};
+  const int cands_f64_16[] = {2, 1};
+  const int* cands;
+  int nc;
+  if (dtype == ACE_F32) {
+    cands = npad == 1 ? cands_f32_1 : cands_f32_16;
+    nc = npad == 1 ? 5 : 3;
+  } else {
+    cands = npad == 1 ? cands_f64_1 : cands_f64_16;
+    nc = npad == 1 ? 4 : 2;
+  }
+  const size_t tsz = dtype == ACE_F32 ? 4 : 8;
+  const int64_t per_sm = std::max<int64_t>(1, n_env / std::max(1, d->sm_count));
+  for (int i = 0; i < nc; ++i) {
+    const int E = cands[i];
+    if (E > 1 && E > per_sm) continue;
+    int nt = 0;
+    const void* k = fused_kernel_ptr(dtype, E, npad, grad, 0, &nt);
+    if (!k) continue;
+    dev::SmemLayout L = dev::smem_layout(E, npad, grad, d->plan.n_slots, d->plan.n_g, nt, (int)tsz);
+    if (L.total > (size_t)d->smem_optin) continue;
+    *E_out = E;
+    *nt_out = nt;
+    *smem_out = L.total;
+    *kern_out = k;
+    return ACE_OK;
+  }
+  return fail(ACE_ERR_UNSUPPORTED,
+              "the stored values of one environment do not fit in shared memory (graph too large for the tiled "
+              "kernel)");
+}
+
+ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phibar, int64_t n_env, int n_out,
+                     int dtype, int readout, void* phi, void* dA, bool grad, cudaStream_t st) {
+  DevTaskSet& dt = grad ? d->sym : d->one;
+  ace_status s = bind(d, dt, c, n_out, dtype, st);
+  if (s != ACE_OK) return s;
+  const int npad = nout_pad_of(n_out);
+  int E = 0, nt = 0;
+  size_t smem = 0;
+  const void* k = nullptr;
+  if ((s = choose_tile(d, dtype, npad, grad, n_env, &E, &nt, &smem, &k)) != ACE_OK) return s;
+  const int ro = dtype == ACE_F32 ? readout : 0;
+  k = fused_kernel_ptr(dtype, E, npad, grad, ro, &nt);
+  if (!k) return fail(ACE_ERR_UNSUPPORTED, "no kernel for this readout mode");
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  int bps = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, nt, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  if (bps < 1) return fail(ACE_ERR_UNSUPPORTED, "fused kernel cannot be resident with this tile");
+  const int64_t n_tiles = (n_env + E - 1) / E;
+  const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)d->sm_count * bps);
+  const Plan& p = d->plan;
+  auto fill = [&](auto& a) {
+    using TT = std::remove_pointer_t<decltype(a.phi)>;
+    a.A = static_cast<const TT*>(A);
+    a.phibar = static_cast<const TT*>(phibar);
+    a.phi = static_cast<TT*>(phi);
+    a.dA = static_cast<TT*>(dA);
+    a.n_env = n_env;
+    a.n_tiles = n_tiles;
+    a.K = p.K;
+    a.n_slots = p.n_slots;
+    a.n_g = p.n_g;
+    a.n_out = n_out;
+    a.fwd_slot = d->fwd_slot;
+    a.fwd_l = d->fwd_l;
+    a.fwd_r = d->fwd_r;
+    a.rev_slot = d->rev_slot;
+    a.rev_l = d->rev_l;
+    a.rev_r = d->rev_r;
+    a.n_fwd_levels = (int32_t)p.fwd.off.size() - 1;
+    a.n_rev_levels = (int32_t)p.rev.off.size() - 1;
+    for (int i = 0; i <= dev::kMaxLevels; ++i) {
+      a.fwd_off[i] = i < (int)p.fwd.off.size() ? p.fwd.off[i] : 0;
+      a.rev_off[i] = i < (int)p.rev.off.size() ? p.rev.off[i] : 0;
+    }
+    a.tasks = dt.tasks;
+    a.slice_off = dt.slice_off;
+    a.slice_steps = dt.slice_steps;
+    a.n_slices = dt.n_slices;
+    a.col = dt.col;
+    a.vals = static_cast<const TT*>(dt.vals);
+    a.lin = static_cast<const TT*>(dt.lin);
+    a.check = checked_mode() ? 1 : 0;
+    a.status = d->status;
+  };
+  if (dtype == ACE_F32) {
+    dev::FusedArgs<float> a{};
+    fill(a);
+    void* args[] = {&a};
+    e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(nt), args, smem, st);
+  } else {
+    dev::FusedArgs<double> a{};
+    fill(a);
+    void* args[] = {&a};
+    e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(nt), args, smem, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  return ACE_OK;
+}
+
+ace_status check_eval_args(const ace_dag* d, const void* A, int64_t n_env, int n_out, int dtype, int readout) {
+  if (!d) return fail(ACE_ERR_INVALID_ARG, "dag is NULL");
+  if (n_env < 0) return fail(ACE_ERR_INVALID_ARG, "n_env must be >= 0");
+  if (n_out < 1 || n_out > 16) return fail(ACE_ERR_INVALID_ARG, "n_out must be in [1, 16]");
+  if (dtype != ACE_F32 && dtype != ACE_F64) return fail(ACE_ERR_INVALID_ARG, "dtype must be ACE_F32 or ACE_F64");
+  if (readout < 0 || readout > 2) return fail(ACE_ERR_INVALID_ARG, "unknown readout mode");
+  if (n_env > 0 && !A) return fail(ACE_ERR_INVALID_ARG, "A is NULL");
+  if (A && !aligned16(A)) return fail(ACE_ERR_INVALID_ARG, "A must be 16-byte aligned");
+  return ACE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ace_last_error(void) { return ace::last_error_cstr(); }
+
+int32_t ace_abi_version(void) { return ACE_ABI_VERSION; }
+
+ace_status ace_build_spec(const ace_spec_params* params, ace_spec** out) {
+  if (!params || !out) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  try {
+    std::unique_ptr<Spec> s;
+    ace_status st = build_spec(*params, s);
+    if (st != ACE_OK) return st;
+    auto* h = new ace_spec;
+    h->s = std::move(s);
+    *out = h;
+    return ACE_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(ACE_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(ACE_ERR_INVALID_ARG, "unexpected error building the index set");
+  }
+}
+
+ace_status ace_spec_info(const ace_spec* spec, int64_t* n_basis, int32_t* K, int64_t* counts_per_nu) {
+  if (!spec) return fail(ACE_ERR_INVALID_ARG, "spec is NULL");
+  if (n_basis) *n_basis = spec->s->n_basis();
+  if (K) *K = spec->s->K;
+  if (counts_per_nu)
+    std::memcpy(counts_per_nu, spec->s->counts_per_nu.data(), spec->s->counts_per_nu.size() * sizeof(int64_t));
+  return ACE_OK;
+}
+
+ace_status ace_spec_tuples(const ace_spec* spec, int32_t* tuples, int32_t* deg) {
+  if (!spec) return fail(ACE_ERR_INVALID_ARG, "spec is NULL");
+  if (tuples) std::memcpy(tuples, spec->s->tuples.data(), spec->s->tuples.size() * sizeof(int32_t));
+  if (deg) std::memcpy(deg, spec->s->deg.data(), spec->s->deg.size() * sizeof(int32_t));
+  return ACE_OK;
+}
+
+void ace_spec_free(ace_spec* spec) { delete spec; }
+
+ace_status ace_build_dag(const ace_spec* spec, int32_t algo, int32_t split_rule, int32_t n_split, ace_dag** out) {
+  if (!spec || !out) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  try {
+    auto d = std::make_unique<ace_dag>();
+    ace_status st = build_graph(*spec->s, algo, split_rule, n_split, d->g);
+    if (st != ACE_OK) return st;
+    int task_len = 64;
+    if (const char* v = std::getenv("ACE_TASK_LEN")) task_len = std::max(1, std::atoi(v));
+    st = build_plan(*spec->s, d->g, task_len, d->plan);
+    if (st != ACE_OK) return st;
+    d->K = spec->s->K;
+    d->n_basis = spec->s->n_basis();
+    *out = d.release();
+    return ACE_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(ACE_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(ACE_ERR_INVALID_ARG, "unexpected error building the graph");
+  }
+}
+
+ace_status ace_dag_info(const ace_dag* dag, int64_t* n_nodes, int64_t* n_aux, int64_t* n_operands,
+                        int32_t* n_levels) {
+  if (!dag) return fail(ACE_ERR_INVALID_ARG, "dag is NULL");
+  const Graph& g = dag->g;
+  if (n_nodes) *n_nodes = g.n_nodes();
+  if (n_aux) {
+    int64_t a = 0;
+    for (uint8_t x : g.is_aux) a += x;
+    *n_aux = a;
+  }
+  if (n_operands) *n_operands = dag->plan.n_slots - dag->plan.K;
+  if (n_levels) {
+    int32_t m = 1;
+    for (int32_t o : g.order) m = std::max(m, o);
+    *n_levels = m;
+  }
+  return ACE_OK;
+}
+
+ace_status ace_dag_export(const ace_dag* dag, int32_t* left, int32_t* right, int32_t* level, uint8_t* is_aux,
+                          int32_t* basis_node) {
+  if (!dag) return fail(ACE_ERR_INVALID_ARG, "dag is NULL");
+  const Graph& g = dag->g;
+  const size_t n = (size_t)g.n_nodes();
+  if (left) std::memcpy(left, g.left.data(), n * sizeof(int32_t));
+  if (right) std::memcpy(right, g.right.data(), n * sizeof(int32_t));
+  if (level) std::memcpy(level, g.order.data(), n * sizeof(int32_t));
+  if (is_aux) std::memcpy(is_aux, g.is_aux.data(), n);
+  if (basis_node) std::memcpy(basis_node, g.basis_node.data(), g.basis_node.size() * sizeof(int32_t));
+  return ACE_OK;
+}
+
+ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_sinks, int64_t* n_entries,
+                             int64_t* smem_bytes_f32) {
+  if (!dag) return fail(ACE_ERR_INVALID_ARG, "dag is NULL");
+  const Plan& p = dag->plan;
+  if (n_slots) *n_slots = p.n_slots;
+  if (n_sinks) *n_sinks = p.n_sinks;
+  if (n_entries) *n_entries = p.sym.n_entries;
+  if (smem_bytes_f32) *smem_bytes_f32 = (int64_t)(p.n_slots + p.n_g) * 4;
+  return ACE_OK;
+}
+
+ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out, int64_t* count) {
+  if (!dag || !name || !count) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
+  const Plan& p = dag->plan;
+  std::vector<int32_t> tmp;
+  const std::vector<int32_t>* v = nullptr;
+  const std::string n(name);
+  auto from_ts = [&](const TaskSet& ts, const std::string& field) -> bool {
+    if (field == "tasks") {
+      for (const Task& t : ts.tasks) tmp.insert(tmp.end(), {t.row, t.flags, t.pl, t.pr});
+      v = &tmp;
+    } else if (field == "slice_off") v = &ts.slice_off;
+    else if (field == "slice_steps") v = &ts.slice_steps;
+    else if (field == "col") v = &ts.col;
+    else if (field == "ebasis") v = &ts.ebasis;
+    else if (field == "ew2") {
+      tmp.assign(ts.ew2.begin(), ts.ew2.end());
+      v = &tmp;
+    } else return false;
+    return true;
+  };
+  if (n == "slot_node") v = &p.slot_node;
+  else if (n == "slot_basis") v = &p.slot_basis;
+  else if (n == "n_g") {
+    tmp = {p.n_g};
+    v = &tmp;
+  } else if (n == "fwd_slot") v = &p.fwd.slot;
+  else if (n == "fwd_l") v = &p.fwd.l;
+  else if (n == "fwd_r") v = &p.fwd.r;
+  else if (n == "fwd_off") v = &p.fwd.off;
+  else if (n == "rev_slot") v = &p.rev.slot;
+  else if (n == "rev_l") v = &p.rev.l;
+  else if (n == "rev_r") v = &p.rev.r;
+  else if (n == "rev_off") v = &p.rev.off;
+  else if (n.rfind("sym_", 0) == 0) {
+    if (!from_ts(p.sym, n.substr(4))) v = nullptr;
+  } else if (n.rfind("one_", 0) == 0) {
+    if (!from_ts(p.one, n.substr(4))) v = nullptr;
+  }
+  if (!v) return fail(ACE_ERR_INVALID_ARG, "unknown plan array: " + n);
+  *count = (int64_t)v->size();
+  if (out && !v->empty()) std::memcpy(out, v->data(), v->size() * sizeof(int32_t));
+  return ACE_OK;
+}
+
+void ace_dag_free(ace_dag* dag) {
+  if (!dag) return;
+  if (dag->device >= 0) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(dag->device);
+    for (void* p : dag->allocations) cudaFree(p);
+    for (DevTaskSet* t : {&dag->sym, &dag->one}) {
+      if (t->vals) cudaFree(t->vals);
+      if (t->lin) cudaFree(t->lin);
+    }
+    cudaSetDevice(cur);
+  }
+  delete dag;
+}
+
+ace_status ace_dag_upload(ace_dag* dag, void* stream) {
+  if (!dag) return fail(ACE_ERR_INVALID_ARG, "dag is NULL");
+  return ensure_uploaded(dag, (cudaStream_t)stream);
+}
+
+ace_status ace_eval(ace_dag* dag, const void* A, const void* c, int64_t n_env, int32_t n_out, int32_t dtype,
+                    int32_t readout, void* phi, void* stream) {
+  ace_status s = check_eval_args(dag, A, n_env, n_out, dtype, readout);
+  if (s != ACE_OK) return s;
+  if (n_env > 0 && !phi) return fail(ACE_ERR_INVALID_ARG, "phi is NULL");
+  if (phi && !aligned16(phi)) return fail(ACE_ERR_INVALID_ARG, "phi must be 16-byte aligned");
+  if (c && !aligned16(c)) return fail(ACE_ERR_INVALID_ARG, "c must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = ensure_uploaded(dag, st)) != ACE_OK) return s;
+  if (n_env == 0) return bind(dag, dag->one, c, n_out, dtype, st);
+  return run_fused(dag, A, c, nullptr, n_env, n_out, dtype, readout, phi, nullptr, false, st);
+}
+
+ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void* phi_bar, int64_t n_env,
+                         int32_t n_out, int32_t dtype, int32_t readout, void* phi, void* dA, void* stream) {
+  ace_status s = check_eval_args(dag, A, n_env, n_out, dtype, readout);
+  if (s != ACE_OK) return s;
+  if (n_env > 0 && !dA) return fail(ACE_ERR_INVALID_ARG, "dA is NULL");
+  for (const void* p : {(const void*)phi, (const void*)dA, phi_bar, c})
+    if (p && !aligned16(p)) return fail(ACE_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = ensure_uploaded(dag, st)) != ACE_OK) return s;
+  if (n_env == 0) return bind(dag, dag->sym, c, n_out, dtype, st);
+  return run_fused(dag, A, c, phi_bar, n_env, n_out, dtype, readout, phi, dA, true, st);
+}
+
+ace_status ace_eval_plain_workspace_bytes(const ace_dag* dag, int64_t n_env, int32_t with_grad, size_t* bytes) {
+  if (!dag || !bytes) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
+  if (n_env < 0) return fail(ACE_ERR_INVALID_ARG, "n_env must be >= 0");
+  *bytes = (size_t)dag->g.n_nodes() * (size_t)n_env * sizeof(double) * (with_grad ? 2 : 1);
+  return ACE_OK;
+}
+
+ace_status ace_eval_plain_f64(ace_dag* dag, const double* A, const double* c, const double* phi_bar,
+                              int64_t n_env, int32_t n_out, double* phi, double* dA, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+  ace_status s = check_eval_args(dag, A, n_env, n_out, ACE_F64, 0);
+  if (s != ACE_OK) return s;
+  if (n_env == 0) return ACE_OK;
+  if (!c) return fail(ACE_ERR_INVALID_ARG, "c is NULL");
+  if (!phi && !dA) return fail(ACE_ERR_INVALID_ARG, "nothing to compute: phi and dA are NULL");
+  size_t need = 0;
+  ace_eval_plain_workspace_bytes(dag, n_env, dA != nullptr, &need);
+  if (!workspace || workspace_bytes < need) return fail(ACE_ERR_INVALID_ARG, "workspace missing or too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = ensure_uploaded(dag, st)) != ACE_OK) return s;
+  double* AA = static_cast<double*>(workspace);
+  double* abar = dA ? AA + (size_t)dag->g.n_nodes() * n_env : nullptr;
+  cudaError_t e = launch_plain_f64(A, c, phi_bar, n_env, n_out, dag->K, dag->g.n_nodes(), dag->node_left,
+                                   dag->node_right, dag->node_basis, phi, dA, AA, abar, st);
+  if (e != cudaSuccess) return cuda_fail(e, "plain kernel launch");
+  return ACE_OK;
+}
+
+static ace_status check_pool_args(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
+                                  int32_t nmin, int32_t nmax, int32_t lmax) {
+  if (n_env < 0 || n_pairs < 0) return fail(ACE_ERR_INVALID_ARG, "sizes must be >= 0");
+  if (!offsets && n_env > 0) return fail(ACE_ERR_INVALID_ARG, "offsets is NULL");
+  if (!pos && n_pairs > 0) return fail(ACE_ERR_INVALID_ARG, "pos is NULL");
+  if (!(rc > 0.f)) return fail(ACE_ERR_INVALID_ARG, "rc must be > 0");
+  if (nmin < 0 || nmax < nmin) return fail(ACE_ERR_INVALID_ARG, "need 0 <= nmin <= nmax");
+  if (nmax - nmin + 1 > 16) return fail(ACE_ERR_UNSUPPORTED, "at most 16 radial functions");
+  if (lmax < 0) return fail(ACE_ERR_INVALID_ARG, "lmax must be >= 0");
+  if (lmax > 8) return fail(ACE_ERR_UNSUPPORTED, "lmax > 8 is not compiled");
+  return ACE_OK;
+}
+
+ace_status ace_pool_A(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
+                      int32_t nmin, int32_t nmax, int32_t lmax, float* A, void* stream) {
+  ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax);
+  if (s != ACE_OK) return s;
+  if (n_env == 0) return ACE_OK;
+  if (!A) return fail(ACE_ERR_INVALID_ARG, "A is NULL");
+  cudaError_t e = launch_pool(pos, offsets, n_env, rc, nmin, nmax, lmax, A, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pooling kernel launch");
+  return ACE_OK;
+}
+
+ace_status ace_pool_A_grad(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
+                           int32_t nmin, int32_t nmax, int32_t lmax, const float* dA, float* dpos, void* stream) {
+  ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax);
+  if (s != ACE_OK) return s;
+  if (n_env == 0) return ACE_OK;
+  if (!dA || (!dpos && n_pairs > 0)) return fail(ACE_ERR_INVALID_ARG, "dA or dpos is NULL");
+  cudaError_t e = launch_pool_grad(pos, offsets, n_env, rc, nmin, nmax, lmax, dA, dpos, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pooling adjoint launch");
+  return ACE_OK;
+}
+
+ace_status ace_stream_status(ace_dag* dag, void* stream) {
+  if (!dag) return fail(ACE_ERR_INVALID_ARG, "dag is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (dag->device < 0) return ACE_OK;
+  uint32_t w = 0;
+  if ((e = cudaMemcpy(&w, dag->status, sizeof(w), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "status read");
+  if ((e = cudaMemset(dag->status, 0, sizeof(uint32_t))) != cudaSuccess) return cuda_fail(e, "status clear");
+  if (w & dev::kStatusBounds) return fail(ACE_ERR_BOUNDS, "a checked kernel saw an out-of-range index");
+  if (w & dev::kStatusTimeout) return fail(ACE_ERR_TIMEOUT, "a bounded device wait gave up");
+  return ACE_OK;
+}
+
+ace_status ace_device_info(int32_t* sm_count, int32_t* smem_optin_bytes, int32_t* cc_major, int32_t* cc_minor) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(ACE_ERR_NO_DEVICE, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  int v = 0;
+  if (sm_count) {
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    *sm_count = v;
+  }
+  if (smem_optin_bytes) {
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    *smem_optin_bytes = v;
+  }
+  if (cc_major) {
+    cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMajor, dev);
+    *cc_major = v;
+  }
+  if (cc_minor) {
+    cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMinor, dev);
+    *cc_minor = v;
+  }
+  return ACE_OK;
+}
+
+ace_status ace_fma_peak(int64_t iters, double* ms, double* fma_count, void* stream) {
+  if (iters < 1 || !ms || !fma_count) return fail(ACE_ERR_INVALID_ARG, "bad argument");
+  int32_t sms = 0;
+  ace_status s = ace_device_info(&sms, nullptr, nullptr, nullptr);
+  if (s != ACE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int threads = 256, blocks = sms * 8;
+  float* out = nullptr;
+  cudaError_t e = cudaMalloc(&out, (size_t)blocks * sizeof(float));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  launch_fma_probe(iters / 10 + 1, blocks, threads, out, st);  // warm-up
+  cudaEventRecord(a, st);
+  e = launch_fma_probe(iters, blocks, threads, out, st);
+  cudaEventRecord(b, st);
+  cudaError_t e2 = cudaEventSynchronize(b);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_fail(e, "probe launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "probe sync");
+  *ms = t;
+  *fma_count = (double)iters * 8.0 * threads * blocks;
+  return ACE_OK;
+}
+
+}  // extern "C"

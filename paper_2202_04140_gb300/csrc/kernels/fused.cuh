@@ -1,0 +1,402 @@
+// Fused evaluation of the recursive contraction (section 2.6, Eq. 4) for a
+// tile of E environments per CTA, with every stored value of the tile resident
+// in shared memory.
+//
+// Per tile:
+//  1. A rows -> AA[k][e] (leaves), transposed so that the E values of one slot
+//     are contiguous (one vector load per slot).
+//  2. Operand nodes level by level (correlation order ascending):
+//     AA_i = AA_l * AA_r  (Eq. 4).
+//  3. Sink contraction: each lane owns one task (a piece of one row s of the
+//     sink matrix), streams its (column, coefficient) entries, and forms
+//     u = sum_j S_sj AA_j.  Its epilogue adds AA_s (c_s + u/2) (symmetric form)
+//     or AA_s (c_s + u) (one-sided form) to the lane's phi accumulator, and in
+//     the adjoint pass adds g = phibar . (c_s + u) to G_s, or pushes it to the
+//     factors of s (G_l += g AA_r, G_r += g AA_l) when s is a top operand.
+//  4. Adjoint through the inner operand nodes, order descending:
+//     G_l += G_i AA_r, G_r += G_i AA_l.
+//  5. dA[e][k] = G[k][e]; phi[e] = block sum of the lane accumulators.
+// No global scratch memory, no inter-CTA communication: tiles are assigned
+// statically (tile = blockIdx.x + i * gridDim.x).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ace {
+namespace dev {
+
+constexpr int kMaxLevels = 8;
+
+enum : int { kReadPlain = 0, kReadComp = 1, kReadF64 = 2 };
+enum : uint32_t { kStatusBounds = 1u, kStatusTimeout = 2u };
+
+template <typename T>
+struct FusedArgs {
+  const T* A;
+  const T* phibar;  // may be null (= ones)
+  T* phi;           // may be null
+  T* dA;            // adjoint output (GRAD)
+  int64_t n_env;
+  int64_t n_tiles;
+  int32_t K, n_slots, n_g, n_out;
+  const int32_t* fwd_slot;
+  const int32_t* fwd_l;
+  const int32_t* fwd_r;
+  const int32_t* rev_slot;
+  const int32_t* rev_l;
+  const int32_t* rev_r;
+  int32_t fwd_off[kMaxLevels + 1];
+  int32_t rev_off[kMaxLevels + 1];
+  int32_t n_fwd_levels, n_rev_levels;
+  const int4* tasks;
+  const int32_t* slice_off;
+  const int32_t* slice_steps;
+  int32_t n_slices;
+  const int32_t* col;
+  const T* vals;  // [entries][NOUT]
+  const T* lin;   // [n_slots][NOUT]
+  int32_t check;
+  uint32_t* status;
+};
+
+// Byte offsets of the shared-memory regions of one CTA (each 16-byte aligned):
+// AA [n_slots][E], G [n_g][E] (adjoint only), phibar [E][NOUT], phi partials
+// [warps][E][NOUT] in FP64.
+struct SmemLayout {
+  size_t g, pb, red, total;
+};
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__host__ __device__ inline SmemLayout smem_layout(int E, int NOUT, bool grad, int n_slots, int n_g, int NT,
+                                                  int tsize) {
+  SmemLayout L;
+  L.g = align16((size_t)n_slots * E * tsize);
+  L.pb = L.g + (grad ? align16((size_t)n_g * E * tsize) : 0);
+  L.red = L.pb + align16((size_t)E * NOUT * tsize);
+  L.total = L.red + (size_t)(NT / 32) * E * NOUT * sizeof(double);
+  return L;
+}
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---- vector helpers ---------------------------------------------------------------
+
+template <typename T, int E>
+struct Vec {
+  T v[E];
+};
+
+template <typename T, int E>
+__device__ __forceinline__ void load_slot(const T* __restrict__ p, T (&x)[E]) {
+  constexpr int bytes = E * (int)sizeof(T);
+  if constexpr (bytes % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < bytes / 16; ++i) {
+      float4 f = reinterpret_cast<const float4*>(p)[i];
+      const T* q = reinterpret_cast<const T*>(&f);
+#pragma unroll
+      for (int j = 0; j < 16 / (int)sizeof(T); ++j) x[i * (16 / (int)sizeof(T)) + j] = q[j];
+    }
+  } else if constexpr (bytes == 8) {
+    float2 f = *reinterpret_cast<const float2*>(p);
+    const T* q = reinterpret_cast<const T*>(&f);
+#pragma unroll
+    for (int j = 0; j < E; ++j) x[j] = q[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < E; ++j) x[j] = p[j];
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void store_slot(T* __restrict__ p, const T (&x)[E]) {
+  constexpr int bytes = E * (int)sizeof(T);
+  if constexpr (bytes % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < bytes / 16; ++i) {
+      float4 f;
+      T* q = reinterpret_cast<T*>(&f);
+#pragma unroll
+      for (int j = 0; j < 16 / (int)sizeof(T); ++j) q[j] = x[i * (16 / (int)sizeof(T)) + j];
+      reinterpret_cast<float4*>(p)[i] = f;
+    }
+  } else if constexpr (bytes == 8) {
+    float2 f;
+    T* q = reinterpret_cast<T*>(&f);
+#pragma unroll
+    for (int j = 0; j < E; ++j) q[j] = x[j];
+    *reinterpret_cast<float2*>(p) = f;
+  } else {
+#pragma unroll
+    for (int j = 0; j < E; ++j) p[j] = x[j];
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void load_vals(const T* __restrict__ p, T (&x)[N]) {
+  constexpr int bytes = N * (int)sizeof(T);
+  if constexpr (bytes % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < bytes / 16; ++i) {
+      float4 f = __ldg(reinterpret_cast<const float4*>(p) + i);
+      const T* q = reinterpret_cast<const T*>(&f);
+#pragma unroll
+      for (int j = 0; j < 16 / (int)sizeof(T); ++j) x[i * (16 / (int)sizeof(T)) + j] = q[j];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = __ldg(p + j);
+  }
+}
+
+// ---- readout accumulators (FP32 plain, FP32 compensated, FP64) -----------------------
+
+template <typename T, int RO>
+struct Acc;
+
+template <>
+struct Acc<float, kReadPlain> {
+  float s = 0.f;
+  __device__ __forceinline__ void add(float x) { s += x; }
+  __device__ __forceinline__ void add_acc(const Acc& o) { s += o.s; }
+  __device__ __forceinline__ double value() const { return (double)s; }
+  __device__ __forceinline__ void shfl_down_add(int d) { s += __shfl_down_sync(0xffffffffu, s, d); }
+};
+
+// TwoSum (Knuth): s + e holds the running sum exactly up to one rounding per
+// combination of two compensated values.
+template <>
+struct Acc<float, kReadComp> {
+  float s = 0.f, e = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t = s + x;
+    float z = t - s;
+    e += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  __device__ __forceinline__ void add_acc(const Acc& o) {
+    add(o.s);
+    e += o.e;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+  __device__ __forceinline__ void shfl_down_add(int d) {
+    Acc o;
+    o.s = __shfl_down_sync(0xffffffffu, s, d);
+    o.e = __shfl_down_sync(0xffffffffu, e, d);
+    add_acc(o);
+  }
+};
+
+template <typename T>
+struct AccD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T x) { s += (double)x; }
+  __device__ __forceinline__ void add_acc(const AccD& o) { s += o.s; }
+  __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ void shfl_down_add(int d) { s += __shfl_down_sync(0xffffffffu, s, d); }
+};
+template <>
+struct Acc<float, kReadF64> : AccD<float> {};
+template <>
+struct Acc<double, kReadPlain> : AccD<double> {};
+
+// ---- the kernel ------------------------------------------------------------------------
+
+template <typename T, int E, int NOUT, bool GRAD, int RO, int NT, bool CHECK>
+__device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
+                                          const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT]) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  for (int sl = warp; sl < a.n_slices; sl += NW) {
+    const int4 task = __ldg(a.tasks + (size_t)sl * 32 + lane);
+    const int steps = __ldg(a.slice_steps + sl);
+    const int32_t off = __ldg(a.slice_off + sl);
+    T acc[E][NOUT];
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) acc[e][c] = T(0);
+    const int32_t* colp = a.col + off + lane;
+    const T* valp = a.vals + ((size_t)off + lane) * NOUT;
+#pragma unroll 4
+    for (int k = 0; k < steps; ++k) {
+      int32_t j = __ldg(colp + (size_t)k * 32);
+      T v[NOUT];
+      load_vals<T, NOUT>(valp + (size_t)k * 32 * NOUT, v);
+      if constexpr (CHECK) {
+        if ((unsigned)j >= (unsigned)a.n_slots) {
+          atomicOr(a.status, kStatusBounds);
+          continue;
+        }
+      }
+      T x[E];
+      load_slot<T, E>(AA + (size_t)j * E, x);
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) acc[e][c] = fma_t(v[c], x[e], acc[e][c]);
+    }
+    const int row = task.x;
+    if (row < 0) continue;
+    if constexpr (CHECK) {
+      bool bad = (unsigned)row >= (unsigned)a.n_slots;
+      if (GRAD && (task.y & 2)) bad |= (unsigned)task.z >= (unsigned)a.n_g || (unsigned)task.w >= (unsigned)a.n_g;
+      if (GRAD && !(task.y & 2)) bad |= (unsigned)row >= (unsigned)a.n_g;
+      if (bad) {
+        atomicOr(a.status, kStatusBounds);
+        continue;
+      }
+    }
+    T lin[NOUT];
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) lin[c] = T(0);
+    if (task.y & 1) load_vals<T, NOUT>(a.lin + (size_t)row * NOUT, lin);
+    T ap[E];
+    load_slot<T, E>(AA + (size_t)row * E, ap);
+    const T half = GRAD ? T(0.5) : T(1);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) phiacc[e][c].add(ap[e] * fma_t(half, acc[e][c], lin[c]));
+    if constexpr (GRAD) {
+      T g[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) s = fma_t(pb[e * NOUT + c], acc[e][c] + lin[c], s);
+        g[e] = s;
+      }
+      if (task.y & 2) {
+        const int pl = task.z, pr = task.w;
+        T xl[E], xr[E];
+        load_slot<T, E>(AA + (size_t)pl * E, xl);
+        load_slot<T, E>(AA + (size_t)pr * E, xr);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          atomicAdd(G + (size_t)pl * E + e, g[e] * xr[e]);
+          atomicAdd(G + (size_t)pr * E + e, g[e] * xl[e]);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)row * E + e, g[e]);
+      }
+    }
+  }
+}
+
+template <typename T, int E, int NOUT, bool GRAD, int RO, int NT>
+__global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NW = NT / 32;
+  const SmemLayout L = smem_layout(E, NOUT, GRAD, a.n_slots, a.n_g, NT, (int)sizeof(T));
+  T* AA = reinterpret_cast<T*>(smem_raw);
+  T* G = reinterpret_cast<T*>(smem_raw + L.g);
+  T* pb = reinterpret_cast<T*>(smem_raw + L.pb);
+  double* red = reinterpret_cast<double*>(smem_raw + L.red);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int K = a.K;
+
+  for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int64_t env0 = tile * E;
+    // 1. leaves
+    for (int i = tid; i < E * K; i += NT) {
+      const int e = i / K, k = i - e * K;
+      const int64_t env = env0 + e;
+      AA[(size_t)k * E + e] = env < a.n_env ? a.A[env * K + k] : T(0);
+    }
+    if constexpr (GRAD) {
+      for (int i = tid; i < a.n_g * E; i += NT) G[i] = T(0);
+      for (int i = tid; i < E * NOUT; i += NT) {
+        const int e = i / NOUT, c = i - e * NOUT;
+        const int64_t env = env0 + e;
+        T v = T(0);
+        if (env < a.n_env && c < a.n_out) v = a.phibar ? a.phibar[env * a.n_out + c] : T(1);
+        pb[i] = v;
+      }
+    }
+    __syncthreads();
+    // 2. operand nodes, order ascending (Eq. 4)
+    for (int lv = 0; lv < a.n_fwd_levels; ++lv) {
+      const int b = a.fwd_off[lv], eidx = a.fwd_off[lv + 1];
+      for (int i = b + tid; i < eidx; i += NT) {
+        const int s = __ldg(a.fwd_slot + i), l = __ldg(a.fwd_l + i), r = __ldg(a.fwd_r + i);
+        if (a.check && ((unsigned)s >= (unsigned)a.n_slots || (unsigned)l >= (unsigned)a.n_slots ||
+                        (unsigned)r >= (unsigned)a.n_slots)) {
+          atomicOr(a.status, kStatusBounds);
+          continue;
+        }
+        T xl[E], xr[E], y[E];
+        load_slot<T, E>(AA + (size_t)l * E, xl);
+        load_slot<T, E>(AA + (size_t)r * E, xr);
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] = xl[e] * xr[e];
+        store_slot<T, E>(AA + (size_t)s * E, y);
+      }
+      __syncthreads();
+    }
+    // 3. sink contraction + readout (+ adjoint seeds)
+    Acc<T, RO> phiacc[E][NOUT];
+    if (a.check) run_tasks<T, E, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc);
+    else run_tasks<T, E, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc);
+    __syncthreads();
+    // 4. adjoint through the inner operand nodes, order descending
+    if constexpr (GRAD) {
+      for (int lv = 0; lv < a.n_rev_levels; ++lv) {
+        const int b = a.rev_off[lv], eidx = a.rev_off[lv + 1];
+        for (int i = b + tid; i < eidx; i += NT) {
+          const int s = __ldg(a.rev_slot + i), l = __ldg(a.rev_l + i), r = __ldg(a.rev_r + i);
+          if (a.check && ((unsigned)s >= (unsigned)a.n_g || (unsigned)l >= (unsigned)a.n_g ||
+                          (unsigned)r >= (unsigned)a.n_g)) {
+            atomicOr(a.status, kStatusBounds);
+            continue;
+          }
+          T g[E], xl[E], xr[E];
+          load_slot<T, E>(G + (size_t)s * E, g);
+          load_slot<T, E>(AA + (size_t)l * E, xl);
+          load_slot<T, E>(AA + (size_t)r * E, xr);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            atomicAdd(G + (size_t)l * E + e, g[e] * xr[e]);
+            atomicAdd(G + (size_t)r * E + e, g[e] * xl[e]);
+          }
+        }
+        __syncthreads();
+      }
+      for (int i = tid; i < E * K; i += NT) {
+        const int e = i / K, k = i - e * K;
+        const int64_t env = env0 + e;
+        if (env < a.n_env) a.dA[env * K + k] = G[(size_t)k * E + e];
+      }
+    }
+    // 5. phi: warp reduction, then the warps in fixed order
+    if (a.phi) {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) {
+#pragma unroll
+          for (int d = 16; d >= 1; d >>= 1) phiacc[e][c].shfl_down_add(d);
+          if (lane == 0) red[(warp * E + e) * NOUT + c] = phiacc[e][c].value();
+        }
+      __syncthreads();
+      for (int i = tid; i < E * NOUT; i += NT) {
+        const int e = i / NOUT, c = i - e * NOUT;
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += red[(w * E + e) * NOUT + c];
+        const int64_t env = env0 + e;
+        if (env < a.n_env && c < a.n_out) a.phi[env * a.n_out + c] = (T)s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+
+}  // namespace dev
+}  // namespace ace

@@ -1,0 +1,21 @@
+// Instantiations of the fused kernel: FP32, up to 16 output channels, forward.
+#include "fused.cuh"
+#include "launch.hpp"
+
+namespace ace {
+
+const void* fused_ptr_f32_n16_fwd(int E, int ro) {
+  using namespace dev;
+  if (E == 1 && ro == 0) return (const void*)&fused_kernel<float, 1, 16, false, 0, 256>;
+  if (E == 1 && ro == 1) return (const void*)&fused_kernel<float, 1, 16, false, 1, 256>;
+  if (E == 1 && ro == 2) return (const void*)&fused_kernel<float, 1, 16, false, 2, 256>;
+  if (E == 2 && ro == 0) return (const void*)&fused_kernel<float, 2, 16, false, 0, 256>;
+  if (E == 2 && ro == 1) return (const void*)&fused_kernel<float, 2, 16, false, 1, 256>;
+  if (E == 2 && ro == 2) return (const void*)&fused_kernel<float, 2, 16, false, 2, 256>;
+  if (E == 4 && ro == 0) return (const void*)&fused_kernel<float, 4, 16, false, 0, 256>;
+  if (E == 4 && ro == 1) return (const void*)&fused_kernel<float, 4, 16, false, 1, 256>;
+  if (E == 4 && ro == 2) return (const void*)&fused_kernel<float, 4, 16, false, 2, 256>;
+  return nullptr;
+}
+
+}  // namespace ace

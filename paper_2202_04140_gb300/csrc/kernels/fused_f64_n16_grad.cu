@@ -1,0 +1,14 @@
+// Instantiations of the fused kernel: FP64, up to 16 output channels, forward + adjoint.
+#include "fused.cuh"
+#include "launch.hpp"
+
+namespace ace {
+
+const void* fused_ptr_f64_n16_grad(int E, int ro) {
+  using namespace dev;
+  if (E == 1 && ro == 0) return (const void*)&fused_kernel<double, 1, 16, true, 0, 256>;
+  if (E == 2 && ro == 0) return (const void*)&fused_kernel<double, 2, 16, true, 0, 256>;
+  return nullptr;
+}
+
+}  // namespace ace

@@ -1,0 +1,16 @@
+// Instantiations of the fused kernel: FP64, one output channel, forward.
+#include "fused.cuh"
+#include "launch.hpp"
+
+namespace ace {
+
+const void* fused_ptr_f64_n1_fwd(int E, int ro) {
+  using namespace dev;
+  if (E == 1 && ro == 0) return (const void*)&fused_kernel<double, 1, 1, false, 0, 512>;
+  if (E == 2 && ro == 0) return (const void*)&fused_kernel<double, 2, 1, false, 0, 512>;
+  if (E == 4 && ro == 0) return (const void*)&fused_kernel<double, 4, 1, false, 0, 512>;
+  if (E == 8 && ro == 0) return (const void*)&fused_kernel<double, 8, 1, false, 0, 512>;
+  return nullptr;
+}
+
+}  // namespace ace

@@ -1,0 +1,32 @@
+// Host-callable launchers of the device kernels (internal to libace).
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../../include/ace.h"
+
+namespace ace {
+
+// Returns the fused kernel instantiation for (dtype, E, NOUT, grad, readout) or
+// nullptr when that combination is not compiled; *nt receives its block size.
+const void* fused_kernel_ptr(int dtype, int E, int nout, bool grad, int readout, int* nt);
+
+cudaError_t launch_bind(int dtype, const void* c, int n_out, int nout_pad, const int32_t* ebasis, const uint8_t* ew2,
+                        int64_t n_entries, void* vals, const int32_t* slot_basis, int64_t n_slots, void* lin,
+                        cudaStream_t st);
+
+cudaError_t launch_plain_f64(const double* A, const double* c, const double* phibar, int64_t n_env, int n_out, int K,
+                             int64_t n_nodes, const int32_t* left, const int32_t* right, const int32_t* node_basis,
+                             double* phi, double* dA, double* AA, double* abar, cudaStream_t st);
+
+cudaError_t launch_fma_probe(int64_t iters, int blocks, int threads, float* out, cudaStream_t st);
+
+cudaError_t launch_pool(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
+                        int lmax, float* A, cudaStream_t st);
+
+cudaError_t launch_pool_grad(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
+                             int lmax, const float* dA, float* dpos, cudaStream_t st);
+
+}  // namespace ace

@@ -1,0 +1,331 @@
+// Neighbour pooling A_nlm = sum_j R_n(r_j) Y_lm(r_j/|r_j|) (Eq. 2, section 2.4)
+// and its adjoint (forces).
+//
+// Basis (the paper fixes neither R_n nor a real form of Y_l^m):
+//   R_n(r) = T_n(2r/rc - 1) (1 - r/rc)^2, T_n by T_{n+1} = 2t T_n - T_{n-1};
+//   dR_n/dr by T'_{n+1} = 2 T_n + 2t T'_n - T'_{n-1}.
+//   Y_l0 = N_l0 Q_l^0(u), Y_lm = sqrt2 N_lm Q_l^m(u) C_m, Y_l-m = sqrt2 N_lm Q_l^m(u) S_m
+//   (m > 0), with u = z/r, C_m + i S_m = ((x + i y)/r)^m and Q_l^m = d^m P_l/du^m,
+//   computed by Q_m^m = (2m-1)!!, Q_{m+1}^m = (2m+1) u Q_m^m,
+//   (l-m) Q_l^m = (2l-1) u Q_{l-1}^m - (l+m-1) Q_{l-2}^m.  This is the real
+//   orthonormal harmonic without Condon-Shortley phase, evaluated from the
+//   Cartesian direction (no angles).
+// Gradients treat Y as a polynomial in the unit vector (xh, yh, zh):
+//   dY/dxh = K Q m C_{m-1} (cos) or K Q m S_{m-1} (sin),
+//   dY/dyh = -K Q m S_{m-1} (cos) or K Q m C_{m-1} (sin),
+//   dY/dzh = K Q_l^{m+1} C_m (cos) or K Q_l^{m+1} S_m (sin),
+// and grad_r Y = (g - rh (rh . g)) / r.
+#include <cmath>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "launch.hpp"
+
+namespace ace {
+namespace dev {
+
+constexpr int kPoolLmax = 8;
+constexpr int kPoolNL = (kPoolLmax + 1) * (kPoolLmax + 1);
+constexpr int kPoolMaxR = 16;
+constexpr int kPoolQ = (kPoolLmax + 2) * (kPoolLmax + 3) / 2;  // Q_l^m for 0 <= m <= l+1 <= lmax+1
+constexpr int kPoolWarps = 4;
+constexpr int kPoolChunk = 32;  // neighbours staged per pass
+
+// K_lm (sqrt2 N_lm for m > 0, N_l0 for m = 0) and the recurrence coefficients,
+// filled once from the host in double precision.
+__constant__ float c_norm[kPoolLmax + 1][kPoolLmax + 1];
+__constant__ float c_ra[kPoolLmax + 1][kPoolLmax + 1];  // (2l-1)/(l-m)
+__constant__ float c_rb[kPoolLmax + 1][kPoolLmax + 1];  // (l+m-1)/(l-m)
+__constant__ float c_dfac[kPoolLmax + 2];               // (2m-1)!!
+
+__device__ __forceinline__ int qidx(int l, int m) { return l * (l + 1) / 2 + m; }
+
+// Q[qidx(l,m)] = Q_l^m(u) for 0 <= m <= l <= lmax.
+template <int LMAX>
+__device__ __forceinline__ void legendre_q(float u, float (&Q)[kPoolQ]) {
+#pragma unroll
+  for (int m = 0; m <= LMAX; ++m) {
+    Q[qidx(m, m)] = c_dfac[m];
+    if (m + 1 <= LMAX) Q[qidx(m + 1, m)] = (2 * m + 1) * u * c_dfac[m];
+#pragma unroll
+    for (int l = m + 2; l <= LMAX; ++l)
+      Q[qidx(l, m)] = c_ra[l][m] * u * Q[qidx(l - 1, m)] - c_rb[l][m] * Q[qidx(l - 2, m)];
+  }
+}
+
+// A: one warp per environment; lanes compute R and Y of one neighbour each into
+// shared memory, then lane owns lm = lane + 32 i for all radial n.
+template <int LMAX>
+__global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __restrict__ pos,
+                                                               const int64_t* __restrict__ offsets, int64_t n_env,
+                                                               float rc, int nmin, int nmax, float* __restrict__ A) {
+  constexpr int NL = (LMAX + 1) * (LMAX + 1);
+  constexpr int NI = (NL + 31) / 32;
+  __shared__ float sR[kPoolWarps][kPoolChunk][kPoolMaxR];
+  __shared__ float sY[kPoolWarps][kPoolChunk][NL];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nR = nmax - nmin + 1;
+  const int K = nR * NL;
+  for (int64_t env = blockIdx.x * (int64_t)kPoolWarps + warp; env < n_env; env += (int64_t)gridDim.x * kPoolWarps) {
+    float acc[NI][kPoolMaxR];
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+#pragma unroll
+      for (int n = 0; n < kPoolMaxR; ++n) acc[i][n] = 0.f;
+    const int64_t j0 = offsets[env], j1 = offsets[env + 1];
+    for (int64_t jb = j0; jb < j1; jb += kPoolChunk) {
+      const int64_t j = jb + lane;
+      const int cnt = (int)((j1 - jb) < kPoolChunk ? (j1 - jb) : kPoolChunk);
+      if (lane < cnt) {
+        const float x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
+        const float r = sqrtf(x * x + y * y + z * z);
+        const bool ok = r > 0.f && r < rc;
+        const float ir = ok ? 1.f / r : 0.f;
+        const float xh = x * ir, yh = y * ir, u = z * ir;
+        // radial
+        const float t = 2.f * r / rc - 1.f;
+        const float w = (1.f - r / rc);
+        const float env2 = ok ? w * w : 0.f;
+        float Tm1 = 1.f, T = t;
+        for (int n = 1; n <= nmax; ++n) {
+          if (n >= nmin) sR[warp][lane][n - nmin] = T * env2;
+          const float Tn = 2.f * t * T - Tm1;
+          Tm1 = T;
+          T = Tn;
+        }
+        if (nmin == 0) sR[warp][lane][0] = env2;
+        float Q[kPoolQ];
+        legendre_q<LMAX>(u, Q);
+        float C = 1.f, S = 0.f;
+#pragma unroll
+        for (int m = 0; m <= LMAX; ++m) {
+#pragma unroll
+          for (int l = m; l <= LMAX; ++l) {
+            const float q = c_norm[l][m] * Q[qidx(l, m)];
+            if (m == 0) {
+              sY[warp][lane][l * l + l] = ok ? q : 0.f;
+            } else {
+              sY[warp][lane][l * l + l + m] = ok ? q * C : 0.f;
+              sY[warp][lane][l * l + l - m] = ok ? q * S : 0.f;
+            }
+          }
+          const float Cn = C * xh - S * yh;
+          S = S * xh + C * yh;
+          C = Cn;
+        }
+      }
+      __syncwarp();
+      for (int jj = 0; jj < cnt; ++jj) {
+        float y[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) y[i] = (lane + 32 * i < NL) ? sY[warp][jj][lane + 32 * i] : 0.f;
+#pragma unroll
+        for (int n = 0; n < kPoolMaxR; ++n) {
+          if (n < nR) {
+            const float rn = sR[warp][jj][n];
+#pragma unroll
+            for (int i = 0; i < NI; ++i) acc[i][n] = __fmaf_rn(rn, y[i], acc[i][n]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int n = 0; n < kPoolMaxR; ++n) {
+      if (n < nR) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+          const int lm = lane + 32 * i;
+          if (lm < NL) A[env * K + n * NL + lm] = acc[i][n];
+        }
+      }
+    }
+  }
+}
+
+// Adjoint: one warp per environment, one lane per neighbour.
+template <int LMAX>
+__global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float* __restrict__ pos,
+                                                                    const int64_t* __restrict__ offsets,
+                                                                    int64_t n_env, float rc, int nmin, int nmax,
+                                                                    const float* __restrict__ dA,
+                                                                    float* __restrict__ dpos) {
+  constexpr int NL = (LMAX + 1) * (LMAX + 1);
+  __shared__ float sG[kPoolWarps][kPoolMaxR * NL];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nR = nmax - nmin + 1;
+  const int K = nR * NL;
+  for (int64_t env = blockIdx.x * (int64_t)kPoolWarps + warp; env < n_env; env += (int64_t)gridDim.x * kPoolWarps) {
+    __syncwarp();
+    for (int i = lane; i < K; i += 32) sG[warp][i] = dA[env * K + i];
+    __syncwarp();
+    const int64_t j0 = offsets[env], j1 = offsets[env + 1];
+    for (int64_t j = j0 + lane; j < j1; j += 32) {
+      const float x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
+      const float r = sqrtf(x * x + y * y + z * z);
+      if (!(r > 0.f && r < rc)) {
+        dpos[3 * j] = 0.f;
+        dpos[3 * j + 1] = 0.f;
+        dpos[3 * j + 2] = 0.f;
+        continue;
+      }
+      const float ir = 1.f / r;
+      const float xh = x * ir, yh = y * ir, u = z * ir;
+      const float t = 2.f * r / rc - 1.f;
+      const float w = 1.f - r / rc;
+      const float env2 = w * w, denv = -2.f * w / rc;
+      float R[kPoolMaxR], dR[kPoolMaxR];
+      {
+        float Tm1 = 1.f, T = t, dTm1 = 0.f, dT = 1.f;
+        if (nmin == 0) {
+          R[0] = env2;
+          dR[0] = denv;
+        }
+#pragma unroll
+        for (int n = 1; n <= kPoolMaxR; ++n) {
+          if (n >= nmin && n <= nmax) {
+            R[n - nmin] = T * env2;
+            dR[n - nmin] = dT * (2.f / rc) * env2 + T * denv;
+          }
+          const float Tn = 2.f * t * T - Tm1;
+          const float dTn = 2.f * T + 2.f * t * dT - dTm1;
+          Tm1 = T;
+          T = Tn;
+          dTm1 = dT;
+          dT = dTn;
+        }
+      }
+      float Q[kPoolQ];
+      legendre_q<LMAX>(u, Q);
+      float gx = 0.f, gy = 0.f, gz = 0.f, ys = 0.f;
+      float C = 1.f, S = 0.f, Cp = 0.f, Sp = 0.f;  // (x+iy)^m and (x+iy)^(m-1)
+#pragma unroll
+      for (int m = 0; m <= LMAX; ++m) {
+#pragma unroll
+        for (int l = m; l <= LMAX; ++l) {
+          const float kq = c_norm[l][m] * Q[qidx(l, m)];
+          const float kq1 = (m + 1 <= l) ? c_norm[l][m] * Q[qidx(l, m + 1)] : 0.f;
+          const int base = l * l + l;
+          float h = 0.f, hd = 0.f, h2 = 0.f, hd2 = 0.f;
+          for (int n = 0; n < nR; ++n) {
+            const float ga = sG[warp][n * NL + base + m];
+            h = __fmaf_rn(ga, R[n], h);
+            hd = __fmaf_rn(ga, dR[n], hd);
+            if (m > 0) {
+              const float gb = sG[warp][n * NL + base - m];
+              h2 = __fmaf_rn(gb, R[n], h2);
+              hd2 = __fmaf_rn(gb, dR[n], hd2);
+            }
+          }
+          if (m == 0) {
+            ys = __fmaf_rn(hd, kq, ys);
+            gz = __fmaf_rn(h, kq1, gz);
+          } else {
+            const float fm = (float)m;
+            // cos part
+            ys = __fmaf_rn(hd, kq * C, ys);
+            gx = __fmaf_rn(h, kq * fm * Cp, gx);
+            gy = __fmaf_rn(h, -kq * fm * Sp, gy);
+            gz = __fmaf_rn(h, kq1 * C, gz);
+            // sin part
+            ys = __fmaf_rn(hd2, kq * S, ys);
+            gx = __fmaf_rn(h2, kq * fm * Sp, gx);
+            gy = __fmaf_rn(h2, kq * fm * Cp, gy);
+            gz = __fmaf_rn(h2, kq1 * S, gz);
+          }
+        }
+        Cp = C;
+        Sp = S;
+        const float Cn = C * xh - S * yh;
+        S = S * xh + C * yh;
+        C = Cn;
+      }
+      const float rg = xh * gx + yh * gy + u * gz;
+      dpos[3 * j] = ys * xh + (gx - xh * rg) * ir;
+      dpos[3 * j + 1] = ys * yh + (gy - yh * rg) * ir;
+      dpos[3 * j + 2] = ys * u + (gz - u * rg) * ir;
+    }
+  }
+}
+
+}  // namespace dev
+
+namespace {
+
+bool g_pool_consts_ready = false;
+
+cudaError_t ensure_pool_constants() {
+  if (g_pool_consts_ready) return cudaSuccess;
+  float norm[dev::kPoolLmax + 1][dev::kPoolLmax + 1] = {};
+  float ra[dev::kPoolLmax + 1][dev::kPoolLmax + 1] = {};
+  float rb[dev::kPoolLmax + 1][dev::kPoolLmax + 1] = {};
+  float dfac[dev::kPoolLmax + 2] = {};
+  const double pi = 3.14159265358979323846;
+  for (int l = 0; l <= dev::kPoolLmax; ++l)
+    for (int m = 0; m <= l; ++m) {
+      double ratio = 1.0;  // (l-m)!/(l+m)!
+      for (int i = l - m + 1; i <= l + m; ++i) ratio /= (double)i;
+      double N = std::sqrt((2.0 * l + 1.0) / (4.0 * pi) * ratio);
+      norm[l][m] = (float)(m == 0 ? N : std::sqrt(2.0) * N);
+      if (l > m) {
+        ra[l][m] = (float)((2.0 * l - 1.0) / (double)(l - m));
+        rb[l][m] = (float)((double)(l + m - 1) / (double)(l - m));
+      }
+    }
+  double df = 1.0;
+  for (int m = 0; m <= dev::kPoolLmax + 1; ++m) {
+    if (m > 0) df *= (2.0 * m - 1.0);
+    dfac[m] = (float)df;
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(dev::c_norm, norm, sizeof(norm))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(dev::c_ra, ra, sizeof(ra))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(dev::c_rb, rb, sizeof(rb))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(dev::c_dfac, dfac, sizeof(dfac))) != cudaSuccess) return e;
+  g_pool_consts_ready = true;
+  return cudaSuccess;
+}
+
+int pool_grid(int64_t n_env) {
+  int dev_id = 0, sms = 148;
+  cudaGetDevice(&dev_id);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+  int64_t need = (n_env + dev::kPoolWarps - 1) / dev::kPoolWarps;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
+}
+
+}  // namespace
+
+#define ACE_POOL_DISPATCH(KERNEL, ...)                                                              \
+  switch (lmax) {                                                                                   \
+    case 0: dev::KERNEL<0><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
+    case 1: dev::KERNEL<1><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
+    case 2: dev::KERNEL<2><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
+    case 3: dev::KERNEL<3><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
+    case 4: dev::KERNEL<4><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
+    case 5: dev::KERNEL<5><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
+    case 6: dev::KERNEL<6><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
+    case 7: dev::KERNEL<7><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
+    case 8: dev::KERNEL<8><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
+    default: return cudaErrorInvalidValue;                                                          \
+  }
+
+cudaError_t launch_pool(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
+                        int lmax, float* A, cudaStream_t st) {
+  cudaError_t e = ensure_pool_constants();
+  if (e != cudaSuccess) return e;
+  const int grid = pool_grid(n_env);
+  ACE_POOL_DISPATCH(pool_kernel, pos, offsets, n_env, rc, nmin, nmax, A)
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pool_grad(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
+                             int lmax, const float* dA, float* dpos, cudaStream_t st) {
+  cudaError_t e = ensure_pool_constants();
+  if (e != cudaSuccess) return e;
+  const int grid = pool_grid(n_env);
+  ACE_POOL_DISPATCH(pool_grad_kernel, pos, offsets, n_env, rc, nmin, nmax, dA, dpos)
+  return cudaGetLastError();
+}
+
+}  // namespace ace

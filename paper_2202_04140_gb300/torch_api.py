@@ -1,0 +1,203 @@
+"""PyTorch-facing API over libace: tensors in, tensors out, every step in libace.
+
+PyTorch supplies device memory, streams and autograd only.  ``Spec`` and ``Dag``
+own the library handles; ``Dag.energy`` is differentiable (its backward is the
+fused adjoint kernel); ``pool_A`` / ``forces`` wrap the neighbour pooling.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import ace as L
+
+_DTYPE = {torch.float32: L.ACE_F32, torch.float64: L.ACE_F64}
+_READOUT = {"plain": L.ACE_READOUT_PLAIN, "compensated": L.ACE_READOUT_COMPENSATED,
+            "fp64": L.ACE_READOUT_FP64_FINAL}
+_RULE = {"balanced": L.ACE_SPLIT_BALANCED, "peel": L.ACE_SPLIT_PEEL}
+_GROUP = {"O3": L.ACE_GROUP_O3, "SO2": L.ACE_GROUP_SO2, "T": L.ACE_GROUP_TORUS}
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dev(t: torch.Tensor, name: str, dtype=None) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}")
+    return t.contiguous()
+
+
+class Spec:
+    """The index set K (sections 2.2-2.5, Eq. 3), built by libace."""
+
+    def __init__(self, group="O3", nmin=1, nmax=1, lmax=0, nu_max=1, deg_max=0, wn=1, wl=1, p_norm=1,
+                 require_l_even=True):
+        self.group = group
+        self.nu_max = nu_max
+        self.handle = L.ace_build_spec(_GROUP[group], nmin, nmax, lmax, nu_max, deg_max, wn, wl, p_norm,
+                                       int(require_l_even))
+        self.n_basis, self.K, self.counts_per_nu = L.ace_spec_info(self.handle, nu_max)
+        self._tuples = None
+
+    @classmethod
+    def from_workload(cls, w) -> "Spec":
+        return cls("O3", w.nmin, w.nmax, w.lmax, w.nu_max, w.deg_max, w.wn, w.wl, 1, True)
+
+    def tuples(self):
+        if self._tuples is None:
+            self._tuples = L.ace_spec_tuples(self.handle, self.n_basis, self.nu_max)
+        return self._tuples
+
+    @property
+    def deg(self) -> np.ndarray:
+        return self.tuples()[1]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            L.ace_spec_free(h)
+            self.handle = None
+
+
+class Dag:
+    """The computational graph G (section 2.6, Algorithm 1 or 2) and its device plan."""
+
+    def __init__(self, spec: Spec, algo: int = 1, rule: str = "balanced", n_split: int = 2):
+        self.spec = spec
+        self.handle = L.ace_build_dag(spec.handle, algo, _RULE[rule], n_split)
+        self.n_nodes, self.n_aux, self.n_operands, self.n_levels = L.ace_dag_info(self.handle)
+        self.n_slots, self.n_sinks, self.n_entries, self.smem_bytes_f32 = L.ace_dag_plan_info(self.handle)
+        self.K = spec.K
+        self.n_basis = spec.n_basis
+        self._bound = {}
+
+    def export(self) -> dict:
+        left, right, level, aux, bnode = L.ace_dag_export(self.handle, self.n_nodes, self.n_basis)
+        return {"left": left, "right": right, "level": level, "is_aux": aux, "basis_node": bnode}
+
+    def upload(self):
+        L.ace_dag_upload(self.handle, _stream())
+
+    def _c_arg(self, mode: str, c: torch.Tensor, n_out: int) -> int:
+        """Device pointer of c, or 0 when the same, unmodified tensor is already bound for this mode."""
+        key = (c.data_ptr(), c._version, n_out, c.dtype, c.device)
+        if self._bound.get(mode) == key:
+            return 0
+        self._bound[mode] = key
+        return c.data_ptr()
+
+    def evaluate(self, A: torch.Tensor, c: torch.Tensor, readout: str = "plain") -> torch.Tensor:
+        """phi[e][ch] = sum_k c[k][ch] prod_t A[e][k_t] (Eq. 2) through G (Eq. 4)."""
+        A = _dev(A, "A")
+        c = _dev(c, "c", A.dtype)
+        n_env = A.shape[0]
+        c2 = c.reshape(self.n_basis, -1)
+        n_out = c2.shape[1]
+        phi = torch.empty((n_env, n_out), dtype=A.dtype, device=A.device)
+        L.ace_eval(self.handle, A.data_ptr(), self._c_arg("one", c2, n_out), n_env, n_out, _DTYPE[A.dtype],
+                   _READOUT[readout], phi.data_ptr(), _stream())
+        return phi
+
+    def evaluate_grad(self, A: torch.Tensor, c: torch.Tensor, phi_bar: torch.Tensor | None = None,
+                      readout: str = "plain", want_phi: bool = True):
+        """(phi, dA) with dA[e][k] = sum_ch phi_bar[e][ch] dphi[e][ch]/dA[e][k] (phi_bar = 1 if None)."""
+        A = _dev(A, "A")
+        c = _dev(c, "c", A.dtype)
+        n_env = A.shape[0]
+        c2 = c.reshape(self.n_basis, -1)
+        n_out = c2.shape[1]
+        pb = 0
+        if phi_bar is not None:
+            phi_bar = _dev(phi_bar, "phi_bar", A.dtype).reshape(n_env, n_out)
+            pb = phi_bar.data_ptr()
+        phi = torch.empty((n_env, n_out), dtype=A.dtype, device=A.device) if want_phi else None
+        dA = torch.empty_like(A)
+        L.ace_eval_grad(self.handle, A.data_ptr(), self._c_arg("sym", c2, n_out), pb, n_env, n_out,
+                        _DTYPE[A.dtype], _READOUT[readout], phi.data_ptr() if want_phi else 0, dA.data_ptr(),
+                        _stream())
+        return phi, dA
+
+    def evaluate_plain_f64(self, A: torch.Tensor, c: torch.Tensor, phi_bar: torch.Tensor | None = None,
+                           grad: bool = False, workspace: torch.Tensor | None = None):
+        """The plain FP64 graph walk (one thread per environment, node values in global memory)."""
+        A = _dev(A, "A", torch.float64)
+        c = _dev(c, "c", torch.float64)
+        n_env = A.shape[0]
+        c2 = c.reshape(self.n_basis, -1)
+        n_out = c2.shape[1]
+        need = L.ace_eval_plain_workspace_bytes(self.handle, n_env, grad)
+        if workspace is None or workspace.numel() * workspace.element_size() < need:
+            workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=A.device)
+        phi = torch.empty((n_env, n_out), dtype=torch.float64, device=A.device)
+        dA = torch.empty_like(A) if grad else None
+        pb = _dev(phi_bar, "phi_bar", torch.float64).data_ptr() if phi_bar is not None else 0
+        L.ace_eval_plain_f64(self.handle, A.data_ptr(), c2.data_ptr(), pb, n_env, n_out, phi.data_ptr(),
+                             dA.data_ptr() if grad else 0, workspace.data_ptr(),
+                             workspace.numel() * workspace.element_size(), _stream())
+        return phi, dA
+
+    def status(self) -> int:
+        """Synchronise and read the device status word (0, or -5 bounds / -4 timeout)."""
+        return L.ace_stream_status(self.handle, _stream())
+
+    def energy(self, A: torch.Tensor, c: torch.Tensor, readout: str = "plain") -> torch.Tensor:
+        """Differentiable phi (w.r.t. A): backward runs the fused forward+adjoint kernel."""
+        return _AceEnergy.apply(A, c, self, readout)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            L.ace_dag_free(h)
+            self.handle = None
+
+
+class _AceEnergy(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, c, dag, readout):
+        ctx.save_for_backward(A, c)
+        ctx.dag = dag
+        ctx.readout = readout
+        return dag.evaluate(A, c, readout)
+
+    @staticmethod
+    def backward(ctx, gphi):
+        A, c = ctx.saved_tensors
+        _, dA = ctx.dag.evaluate_grad(A, c, gphi.contiguous(), ctx.readout, want_phi=False)
+        return dA, None, None, None
+
+
+def pool_A(pos: torch.Tensor, offsets: torch.Tensor, nmin: int, nmax: int, lmax: int, rc: float) -> torch.Tensor:
+    """A[e][id(n,l,m)] = sum_{j in e} R_n(|r_j|) Y_lm(r_j/|r_j|) on the GPU."""
+    pos = _dev(pos, "pos", torch.float32)
+    offsets = _dev(offsets, "offsets", torch.int64)
+    n_env = offsets.numel() - 1
+    K = (nmax - nmin + 1) * (lmax + 1) ** 2
+    A = torch.empty((n_env, K), dtype=torch.float32, device=pos.device)
+    L.ace_pool_A(pos.data_ptr(), offsets.data_ptr(), n_env, pos.shape[0], rc, nmin, nmax, lmax, A.data_ptr(),
+                 _stream())
+    return A
+
+
+def pool_A_grad(pos: torch.Tensor, offsets: torch.Tensor, dA: torch.Tensor, nmin: int, nmax: int, lmax: int,
+                rc: float) -> torch.Tensor:
+    """dpos[j] = sum_k dA[e(j)][k] grad (R_n Y_lm)(r_j); forces are -dpos when dA = dphi/dA."""
+    pos = _dev(pos, "pos", torch.float32)
+    offsets = _dev(offsets, "offsets", torch.int64)
+    dA = _dev(dA, "dA", torch.float32)
+    n_env = offsets.numel() - 1
+    dpos = torch.empty_like(pos)
+    L.ace_pool_A_grad(pos.data_ptr(), offsets.data_ptr(), n_env, pos.shape[0], rc, nmin, nmax, lmax,
+                      dA.data_ptr(), dpos.data_ptr(), _stream())
+    return dpos
+
+
+def energy_and_forces(dag: Dag, pos: torch.Tensor, offsets: torch.Tensor, c: torch.Tensor, nmin: int, nmax: int,
+                      lmax: int, rc: float, readout: str = "plain"):
+    """Full pipeline: pooling -> fused forward+adjoint -> pooling adjoint.  Returns (phi, F = -dphi/dr)."""
+    A = pool_A(pos, offsets, nmin, nmax, lmax, rc)
+    phi, dA = dag.evaluate_grad(A, c, None, readout)
+    dpos = pool_A_grad(pos, offsets, dA, nmin, nmax, lmax, rc)
+    return phi, -dpos

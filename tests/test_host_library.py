@@ -1,0 +1,241 @@
+"""Host side of libace (no GPU): exported symbols, index set and graph bit-exact against the oracle,
+and the evaluation plan checked by emulating the fused kernel's arithmetic on the CPU."""
+import hashlib
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle.basis import index_set, o3_basis, so2_basis, torus_basis, workload_index_set
+from oracle.dag import build_dag
+from oracle.evaluate import error_scale, grad_error_scale, grad_naive, phi_naive
+import workloads as W
+from tests.metrics import normalized_error
+
+L = pytest.importorskip("paper_2202_04140_gb300.ace")
+from paper_2202_04140_gb300.torch_api import Dag, Spec  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = json.load(open(os.path.join(ROOT, "tests", "golden", "dag_summaries.json")))
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "ace.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ace_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = header_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L._lib, n), n
+    assert sorted(L.EXPORTED) == names
+    assert L.ace_abi_version() == 1
+
+
+def spec_of(basis_kind, **kw):
+    if basis_kind == "O3":
+        return Spec("O3", kw["nmin"], kw["nmax"], kw["lmax"], kw["nu"], kw["D"], kw["wn"], kw["wl"],
+                    kw.get("p", 1), True)
+    if basis_kind == "SO2":
+        return Spec("SO2", kw["nmin"], kw["nmax"], kw["mmax"], kw["nu"], kw["D"], 1, 1, 1, False)
+    return Spec("T", 0, 0, kw["mmax"], kw["nu"], kw["D"], 1, 1, 1, False)
+
+
+CASES = [
+    ("O3", dict(nmin=1, nmax=4, lmax=3, nu=3, D=10, wn=1, wl=2), lambda: o3_basis(1, 4, 3, 1, 2)),
+    ("O3", dict(nmin=1, nmax=3, lmax=3, nu=4, D=9, wn=1, wl=1), lambda: o3_basis(1, 3, 3, 1, 1)),
+    ("O3", dict(nmin=1, nmax=3, lmax=2, nu=3, D=5, wn=1, wl=1, p=2), lambda: o3_basis(1, 3, 2, 1, 1)),
+    ("O3", dict(nmin=1, nmax=3, lmax=2, nu=3, D=3, wn=1, wl=1, p=0), lambda: o3_basis(1, 3, 2, 1, 1)),
+    ("SO2", dict(nmin=1, nmax=3, mmax=4, nu=4, D=8), lambda: so2_basis(1, 3, 4)),
+    ("T", dict(mmax=10, nu=5, D=10), lambda: torus_basis(10)),
+]
+
+
+@pytest.mark.parametrize("kind,kw,ob", CASES)
+def test_spec_matches_oracle(kind, kw, ob):
+    s = spec_of(kind, **kw)
+    p = {1: 1, 2: 2, 0: np.inf}[kw.get("p", 1)]
+    o = index_set(ob(), kw["nu"], kw["D"], p=p)
+    t, d = s.tuples()
+    assert np.array_equal(t, o.tuples.astype(np.int32))
+    assert np.array_equal(d, o.deg.astype(np.int32))
+
+
+@pytest.mark.parametrize("kind,kw,ob", [c for c in CASES if c[1].get("p", 1) == 1])
+@pytest.mark.parametrize("algo,rule", [(1, "balanced"), (1, "peel"), (2, "balanced")])
+def test_dag_matches_oracle(kind, kw, ob, algo, rule):
+    s = spec_of(kind, **kw)
+    o = index_set(ob(), kw["nu"], kw["D"])
+    od = build_dag(o, algo=algo, rule=rule, n_split=2)
+    d = Dag(s, algo=algo, rule=rule, n_split=2)
+    ex = d.export()
+    assert d.n_nodes == od.n_nodes and d.n_aux == od.n_aux
+    assert np.array_equal(ex["left"], od.left.astype(np.int32))
+    assert np.array_equal(ex["right"], od.right.astype(np.int32))
+    assert np.array_equal(ex["is_aux"], od.is_aux.astype(np.uint8))
+    assert np.array_equal(ex["basis_node"], od.basis_node.astype(np.int32))
+    assert np.array_equal(ex["level"], od.order.astype(np.int32))
+
+
+@pytest.mark.parametrize("name", sorted(GOLDEN))
+def test_workload_digests(name):
+    """Bit-exact against the oracle's digests (written by tests/golden/make_golden.py)."""
+    g = GOLDEN[name]
+    s = Spec.from_workload(W.WORKLOADS[name])
+    t, d = s.tuples()
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(t, "<i4").tobytes())
+    h.update(np.ascontiguousarray(d, "<i4").tobytes())
+    assert s.n_basis == g["n_basis"] and list(s.counts_per_nu) == g["counts_per_nu"]
+    assert h.hexdigest() == g["spec_sha256"]
+    for rule, rec in g["rules"].items():
+        dag = Dag(s, rule=rule)
+        ex = dag.export()
+        h = hashlib.sha256()
+        h.update(np.ascontiguousarray(ex["left"], "<i4").tobytes())
+        h.update(np.ascontiguousarray(ex["right"], "<i4").tobytes())
+        h.update(np.ascontiguousarray(ex["is_aux"], "u1").tobytes())
+        h.update(np.ascontiguousarray(ex["basis_node"], "<i4").tobytes())
+        assert dag.n_aux == rec["n_aux"] and dag.n_nodes == rec["n_nodes"]
+        assert dag.n_operands == rec["n_operands"]
+        assert h.hexdigest() == rec["dag_sha256"]
+
+
+# ---- plan emulation: the fused kernel's arithmetic, in FP64 numpy, on the exported plan -----
+
+def plan_arrays(dag, mode):
+    P = {k: L.ace_dag_plan_array(dag.handle, k) for k in
+         ["slot_node", "slot_basis", "n_g", "fwd_slot", "fwd_l", "fwd_r", "fwd_off", "rev_slot", "rev_l", "rev_r",
+          "rev_off"]}
+    for k in ["tasks", "slice_off", "slice_steps", "col", "ebasis", "ew2"]:
+        P[k] = L.ace_dag_plan_array(dag.handle, f"{mode}_{k}")
+    P["tasks"] = P["tasks"].reshape(-1, 4)
+    return P
+
+
+def emulate(dag, mode, A, c, phibar=None):
+    P = plan_arrays(dag, mode)
+    n_env, K = A.shape
+    n_slots = len(P["slot_node"])
+    n_g = int(P["n_g"][0])
+    c = c.reshape(dag.n_basis, -1)
+    AA = np.zeros((n_env, n_slots))
+    AA[:, :K] = A
+    off = P["fwd_off"]
+    for lv in range(len(off) - 1):
+        s = slice(off[lv], off[lv + 1])
+        AA[:, P["fwd_slot"][s]] = AA[:, P["fwd_l"][s]] * AA[:, P["fwd_r"][s]]
+    eb = P["ebasis"]
+    vals = np.where(eb[:, None] >= 0, c[np.maximum(eb, 0)], 0.0) * np.where(P["ew2"] > 0, 2.0, 1.0)[:, None]
+    lin = np.where(P["slot_basis"][:, None] >= 0, c[np.maximum(P["slot_basis"], 0)], 0.0)
+    n_tasks = P["tasks"].shape[0]
+    task_of = np.zeros(len(eb), dtype=np.int64)
+    for s_ in range(len(P["slice_steps"])):
+        o, st = P["slice_off"][s_], P["slice_steps"][s_]
+        idx = o + np.arange(32 * st)
+        task_of[idx] = s_ * 32 + (np.arange(32 * st) % 32)
+    u = np.zeros((n_env, n_tasks, c.shape[1]))
+    for ch in range(c.shape[1]):
+        M = sp.csr_matrix((vals[:, ch], (task_of, np.arange(len(eb)))), shape=(n_tasks, len(eb)))
+        u[:, :, ch] = (M @ AA[:, P["col"]].T).T
+    T = P["tasks"]
+    valid = T[:, 0] >= 0
+    row, first, top = T[:, 0], (T[:, 1] & 1) > 0, (T[:, 1] & 2) > 0
+    linr = np.where((valid & first)[:, None], lin[np.maximum(row, 0)], 0.0)
+    half = 0.5 if mode == "sym" else 1.0
+    ap = AA[:, np.maximum(row, 0)]
+    phi = np.einsum("et,etc->ec", ap * valid, linr[None] + half * u)
+    if mode == "one":
+        return phi, None
+    pb = np.ones((n_env, c.shape[1])) if phibar is None else phibar
+    g = np.einsum("ec,etc->et", pb, linr[None] + u) * valid
+    G = np.zeros((n_env, n_g))
+    gt = g[:, top]
+    pl, pr = T[top, 2], T[top, 3]
+    np.add.at(G.T, pl, (gt * AA[:, pr]).T)
+    np.add.at(G.T, pr, (gt * AA[:, pl]).T)
+    np.add.at(G.T, row[valid & ~top], g[:, valid & ~top].T)
+    off = P["rev_off"]
+    for lv in range(len(off) - 1):
+        s = slice(off[lv], off[lv + 1])
+        gs = G[:, P["rev_slot"][s]]
+        np.add.at(G.T, P["rev_l"][s], (gs * AA[:, P["rev_r"][s]]).T)
+        np.add.at(G.T, P["rev_r"][s], (gs * AA[:, P["rev_l"][s]]).T)
+    return phi, G[:, :K]
+
+
+@pytest.mark.parametrize("name,n_out,rule", [("plain_fp64_k64", 1, "balanced"), ("fwd_grad_k392", 1, "balanced"),
+                                             ("fwd_grad_k392", 3, "peel"), ("uneven_16ch_k392", 16, "balanced")])
+def test_plan_emulation_matches_oracle(name, n_out, rule):
+    w = W.WORKLOADS[name]
+    o = workload_index_set(w)
+    s = Spec.from_workload(w)
+    dag = Dag(s, rule=rule)
+    A = W.draw_A(4, s.K, env_scale=w.env_scale)
+    c = W.draw_c(o.deg, n_out)
+    pb = np.random.default_rng(9).standard_normal((4, n_out))
+    ref = phi_naive(A, o, c)
+    scale = error_scale(A, o, c)
+    for mode in ["one", "sym"]:
+        phi, _ = emulate(dag, mode, A, c, pb)
+        assert normalized_error(phi, ref, scale) < 1e-12
+    _, dA = emulate(dag, "sym", A, c, pb)
+    gref = grad_naive(A, o, c, pb)
+    gscale = grad_error_scale(A, o, c, pb)
+    assert normalized_error(dA, gref, gscale) < 1e-12
+
+
+def test_plan_emulation_stress_sample():
+    """Largest workload (K = 810, nu <= 6): plan arithmetic against the oracle on 2 environments."""
+    w = W.WORKLOADS["stress_k810"]
+    s = Spec.from_workload(w)
+    dag = Dag(s)
+    t, d = s.tuples()
+    from oracle.basis import IndexSet
+    o = IndexSet(o3_basis(1, 10, 8, 1, 2), 6, 24, t.astype(np.int64), (t >= 0).sum(1).astype(np.int64),
+                 d.astype(np.int64))
+    A = W.draw_A(2, s.K)
+    c = W.draw_c(d, 1)
+    phi, dA = emulate(dag, "sym", A, c)
+    ref = phi_naive(A, o, c)
+    assert normalized_error(phi, ref, error_scale(A, o, c)) < 1e-12
+    gref = grad_naive(A, o, c)
+    assert normalized_error(dA, gref, grad_error_scale(A, o, c)) < 1e-12
+
+
+def test_plan_tasks_cover_every_sink_once():
+    s = Spec.from_workload(W.WORKLOADS["fwd_grad_k392"])
+    dag = Dag(s)
+    for mode, per_sink in [("one", 1), ("sym", 2)]:
+        P = plan_arrays(dag, mode)
+        eb = P["ebasis"]
+        real = eb >= 0
+        counts = np.bincount(eb[real], weights=np.where(P["ew2"][real] > 0, 2, 1), minlength=s.n_basis)
+        sink_basis = np.unique(eb[real])
+        assert np.all(counts[sink_basis] == per_sink)
+        assert np.all(P["col"] < len(P["slot_node"])) and np.all(P["col"] >= 0)
+
+
+def test_invalid_arguments_fail_cleanly():
+    with pytest.raises(L.AceError) as e:
+        L.ace_build_spec(L.ACE_GROUP_O3, 1, 2, 1, 9, 5)          # nu_max > 8
+    assert e.value.status == -1
+    with pytest.raises(L.AceError):
+        L.ace_build_spec(7, 1, 2, 1, 2, 5)                         # unknown group
+    s = Spec("O3", 1, 2, 1, 2, 5, 1, 1)
+    with pytest.raises(L.AceError):
+        L.ace_build_dag(s.handle, 3, 0, 2)                         # unknown algorithm
+    d = Dag(s)
+    with pytest.raises(L.AceError):
+        L.ace_dag_plan_array(d.handle, "nonsense")
+    with pytest.raises(L.AceError):                                # n_out out of range, before any CUDA call
+        L.ace_eval(d.handle, 0, 0, 1, 17, L.ACE_F32, 0, 0)
+    with pytest.raises(L.AceError):                                # misaligned A
+        L.ace_eval(d.handle, 8, 0, 1, 1, L.ACE_F32, 0, 16)
+    with pytest.raises(L.AceError):
+        L.ace_pool_A(0, 0, 1, 0, 5.0, 1, 8, 9, 0)                  # lmax > 8 unsupported
