@@ -1,0 +1,429 @@
+#!/usr/bin/env python3
+"""Benchmark: environments per second for phi + dphi/dA through the recursive contraction graph.
+
+Default workload: K = 810 one-particle functions (n <= 10, l <= 8), nu <= 6,
+total degree <= 24 (deg = n + 2l), 213,525 basis functions, 16,384 environments,
+FP32 forward + adjoint in one fused kernel per step (the largest configuration,
+on which the roofline target is stated).  Inputs are synthetic (seeded draws,
+see workloads/), resident in HBM; successive steps rotate over buffer sets
+larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU; every rank processes its own full
+batch (independent environments, no collective on the data path: weak scaling);
+the timed region is bracketed by a barrier and a device synchronisation and the
+maximum time over ranks is reported.  ``--impl reference`` times the FP64 CPU
+oracle (the only reference this method has) on the host cores.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")   # the CPU oracle legs run single-threaded; "cores" reports 1
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+import workloads as W  # noqa: E402
+
+METRIC = "env/s, phi+dphi/dA: batched FP32 vs plain FP64 (GB300, rel err<=1e-5); % roofline"
+TOL32 = 1e-5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="stress_k810", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--readout", default="compensated", choices=["plain", "compensated", "fp64"])
+    ap.add_argument("--no-baselines", action="store_true", help="skip the plain-FP64 GPU and CPU oracle legs")
+    ap.add_argument("--n-env", type=int, default=None, help="override the environment count (small profiling cases)")
+    return ap.parse_args()
+
+
+# ---- algorithmic work (FMA-pipe operations per environment) ---------------------------------
+
+def algorithmic_ops(w, n_nodes_ge2: int, n_basis: int, mode: str) -> float:
+    """Forward: one product per node of order >= 2 plus one readout FMA per basis function and
+    channel; adjoint: two FMAs per node of order >= 2 plus the seed per basis function."""
+    fwd = n_nodes_ge2 + n_basis * w.n_out
+    adj = 2 * n_nodes_ge2 + n_basis * w.n_out
+    return float(fwd + (adj if mode != "forward" else 0))
+
+
+# ---- clocks ---------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---- the CPU oracle legs ------------------------------------------------------------------------
+
+def oracle_setup(w):
+    from oracle.basis import workload_index_set
+    t0 = time.time()
+    o = workload_index_set(w)
+    return o, time.time() - t0
+
+
+def oracle_step(o, A, c):
+    from oracle.evaluate import grad_naive, phi_naive
+    phi = phi_naive(A, o, c)
+    dA = grad_naive(A, o, c)
+    return phi, dA
+
+
+def cpu_baseline(w, o, budget_s=15.0, max_envs=256):
+    """Time the oracle (naive term-by-term phi + product-rule gradient) on a bounded env sample."""
+    c = W.round_to(W.draw_c(o.deg, w.n_out), w.dtype)
+    n = 2
+    A = W.round_to(W.draw_A(n, o.basis.K, env_scale=w.env_scale), w.dtype)
+    t0 = time.perf_counter()
+    oracle_step(o, A, c)
+    per_env = (time.perf_counter() - t0) / n
+    n = int(max(2, min(max_envs, budget_s / max(per_env, 1e-6))))
+    A = W.round_to(W.draw_A(n, o.basis.K, env_scale=w.env_scale), w.dtype)
+    t0 = time.perf_counter()
+    oracle_step(o, A, c)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "env/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} environments of {w.name} (naive FP64 phi + product-rule dphi/dA, numpy, 1 thread)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = W.WORKLOADS[args.workload]
+    o, _ = oracle_setup(w)
+    c = W.round_to(W.draw_c(o.deg, w.n_out), w.dtype)
+    A1 = W.round_to(W.draw_A(2, o.basis.K, env_scale=w.env_scale), w.dtype)
+    t0 = time.perf_counter()
+    oracle_step(o, A1, c)
+    per_env = (time.perf_counter() - t0) / 2
+    budget = 120.0 / max(1, args.steps + args.warmup)           # whole run within about two minutes
+    n = int(max(1, min(256, budget / max(per_env, 1e-6))))
+    A = W.round_to(W.draw_A(n, o.basis.K, env_scale=w.env_scale), w.dtype)
+    for _ in range(args.warmup):
+        oracle_step(o, A, c)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(o, A, c)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": "env/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "n_env_per_step": n, "n_env_full": w.n_env,
+                       "description": w.description},
+            "cpu_baseline": {"value": value, "unit": "env/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n} environments per step of {w.name} (naive FP64 oracle, 1 thread)"},
+            "e2e": {"value": value, "unit": "env/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our path ------------------------------------------------------------------------------------
+
+class Step:
+    """One step of the workload on device-resident inputs (all compute in libace)."""
+
+    def __init__(self, w, dag, torch, dev, n_sets, readout):
+        self.w, self.dag, self.torch, self.readout = w, dag, torch, readout
+        t = torch
+        self.c = t.tensor(W.round_to(W.draw_c(dag.spec.deg, w.n_out), "f32"), dtype=t.float32, device=dev)
+        self.sets = []
+        if w.pooling:
+            offsets, P = W.draw_neighbours(w.n_env, rc=w.rc, j_range=w.j_range)
+            self.offsets = t.tensor(offsets, device=dev)
+            self.n_pairs = P.shape[0]
+            for i in range(n_sets):
+                Pi = P if i == 0 else P[np.random.default_rng(100 + i).permutation(P.shape[0])]
+                self.sets.append(t.tensor(W.round_to(Pi, "f32"), dtype=t.float32, device=dev))
+            self.in_bytes = P.shape[0] * 12 + (w.n_env + 1) * 8
+            self.out_bytes = w.n_env * 4 + P.shape[0] * 12
+        else:
+            A = W.round_to(W.draw_A(w.n_env, dag.K, env_scale=w.env_scale), "f32")
+            for i in range(n_sets):
+                Ai = A if i == 0 else A[np.random.default_rng(100 + i).permutation(A.shape[0])]
+                self.sets.append(t.tensor(Ai, dtype=t.float32, device=dev))
+            self.in_bytes = w.n_env * dag.K * 4
+            self.out_bytes = w.n_env * w.n_out * 4 + (w.n_env * dag.K * 4 if w.grad else 0)
+        self.A0 = self.sets[0]
+
+    def __call__(self, i):
+        from paper_2202_04140_gb300.torch_api import energy_and_forces
+        x = self.sets[i % len(self.sets)]
+        w = self.w
+        if w.pooling:
+            return energy_and_forces(self.dag, x, self.offsets, self.c, w.nmin, w.nmax, w.lmax, w.rc, self.readout)
+        if w.grad:
+            return self.dag.evaluate_grad(x, self.c, None, self.readout)
+        return self.dag.evaluate(x, self.c, self.readout), None
+
+    def launches_per_step(self):
+        return 3 if self.w.pooling else 1
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2202_04140_gb300 import ace as L
+    from paper_2202_04140_gb300.torch_api import Dag, Spec
+
+    w = W.workload(args.workload, **({"n_env": args.n_env} if args.n_env else {}))
+    spec = Spec.from_workload(w)
+    dag = Dag(spec)
+    n_ge2 = dag.n_nodes - dag.K
+    mode = "forward" if not w.grad else "forward+adjoint"
+    ops_env = algorithmic_ops(w, n_ge2, dag.n_basis, mode)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    l2 = 129e6
+    step = Step(w, dag, torch, dev, 1, args.readout)
+    per_set = step.in_bytes + step.out_bytes
+    n_sets = max(1, int(np.ceil(2.5 * l2 / per_set)))
+    step = Step(w, dag, torch, dev, n_sets, args.readout)
+
+    for i in range(args.warmup):
+        step(i)
+    barrier()
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        barrier()
+        ev0.record(st)
+        for i in range(args.steps):
+            step(i)
+        ev1.record(st)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / args.steps
+    value = world * w.n_env * args.steps / (ms / 1e3)
+
+    # dominant kernel: the fused forward+adjoint kernel, timed alone on the same stream
+    if w.pooling:
+        A_dev = None
+    kernel_ms = None
+    if not w.pooling:
+        barrier()
+        ev0.record(st)
+        for i in range(args.steps):
+            step(i)
+        ev1.record(st)
+        barrier()
+        kernel_ms = ev0.elapsed_time(ev1) / args.steps
+    else:
+        from paper_2202_04140_gb300.torch_api import pool_A
+        A_dev = pool_A(step.A0, step.offsets, w.nmin, w.nmax, w.lmax, w.rc)
+        barrier()
+        ev0.record(st)
+        for i in range(args.steps):
+            dag.evaluate_grad(A_dev, step.c, None, args.readout)
+        ev1.record(st)
+        barrier()
+        kernel_ms = ev0.elapsed_time(ev1) / args.steps
+
+    sms, smem, ccmaj, ccmin = L.ace_device_info()
+    peak_flops = sms * 128 * 2 * 2070e6                 # FP32 lanes x FLOP per FMA x max SM clock
+    achieved = 2.0 * ops_env * w.n_env / (kernel_ms / 1e3)
+    probe_ms, probe_fma = L.ace_fma_peak(200000)
+    probe_tflops = 2.0 * probe_fma / (probe_ms / 1e3) / 1e12
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not w.pooling:
+        A_host = step.A0.cpu().pin_memory()
+        dA_host = torch.empty_like(A_host).pin_memory() if w.grad else None
+        phi_host = torch.empty((w.n_env, w.n_out), dtype=torch.float32).pin_memory()
+        n_e2e = max(3, min(args.steps, 50))
+        for _ in range(2):
+            x = A_host.to(dev, non_blocking=True)
+            phi, dA = dag.evaluate_grad(x, step.c, None, args.readout) if w.grad else (dag.evaluate(x, step.c), None)
+        barrier()
+        ev0.record(st)
+        for _ in range(n_e2e):
+            x = A_host.to(dev, non_blocking=True)
+            if w.grad:
+                phi, dA = dag.evaluate_grad(x, step.c, None, args.readout)
+                dA_host.copy_(dA, non_blocking=True)
+            else:
+                phi = dag.evaluate(x, step.c, args.readout)
+            phi_host.copy_(phi, non_blocking=True)
+        ev1.record(st)
+        barrier()
+        e_ms = ev0.elapsed_time(ev1)
+        e2e = {"value": w.n_env * n_e2e / (e_ms / 1e3), "unit": "env/s", "h2d_bytes_per_step": step.in_bytes,
+               "d2h_bytes_per_step": step.out_bytes, "steps": n_e2e}
+    else:
+        from paper_2202_04140_gb300.torch_api import energy_and_forces
+        P_host = step.A0.cpu().pin_memory()
+        off_host = step.offsets.cpu().pin_memory()
+        F_host = torch.empty_like(P_host).pin_memory()
+        phi_host = torch.empty((w.n_env, 1), dtype=torch.float32).pin_memory()
+        n_e2e = max(3, min(args.steps, 50))
+        barrier()
+        ev0.record(st)
+        for _ in range(n_e2e):
+            P = P_host.to(dev, non_blocking=True)
+            off = off_host.to(dev, non_blocking=True)
+            phi, F = energy_and_forces(dag, P, off, step.c, w.nmin, w.nmax, w.lmax, w.rc, args.readout)
+            F_host.copy_(F, non_blocking=True)
+            phi_host.copy_(phi, non_blocking=True)
+        ev1.record(st)
+        barrier()
+        e_ms = ev0.elapsed_time(ev1)
+        e2e = {"value": w.n_env * n_e2e / (e_ms / 1e3), "unit": "env/s", "h2d_bytes_per_step": step.in_bytes,
+               "d2h_bytes_per_step": step.out_bytes, "steps": n_e2e}
+    if world > 1:
+        tt = torch.tensor([e2e["value"]], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MIN)
+        e2e["value"] = float(tt.item()) * world
+
+    extra = {}
+    if rank == 0 and not args.no_baselines and not w.pooling:
+        # plain FP64 GPU graph walk on the same environments (the comparison the method is measured against)
+        A64 = step.A0.double()
+        c64 = step.c.double()
+        need = L.ace_eval_plain_workspace_bytes(dag.handle, w.n_env, w.grad)
+        free = torch.cuda.mem_get_info(dev)[0]
+        n_plain = w.n_env if need < 0.6 * free else max(1, int(w.n_env * 0.6 * free / need))
+        ws = torch.empty(L.ace_eval_plain_workspace_bytes(dag.handle, n_plain, w.grad), dtype=torch.uint8,
+                         device=dev)
+        dag.evaluate_plain_f64(A64[:n_plain], c64, grad=w.grad, workspace=ws)
+        torch.cuda.synchronize()
+        reps = 3
+        ev0.record(st)
+        for _ in range(reps):
+            dag.evaluate_plain_f64(A64[:n_plain], c64, grad=w.grad, workspace=ws)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        p_ms = ev0.elapsed_time(ev1) / reps
+        del ws
+        extra["plain_fp64_gpu"] = {"value": n_plain / (p_ms / 1e3), "unit": "env/s", "ms_per_call": p_ms,
+                                   "n_env": n_plain}
+        # accuracy of this run's configuration on sampled environments, against the oracle
+        o, t_setup = oracle_setup(w)
+        idx = np.array([0, 1, w.n_env // 2, w.n_env - 1])
+        A_s = step.A0[idx].double().cpu().numpy()
+        c_s = step.c.double().cpu().numpy()
+        phi, dA = step(0)
+        from oracle.evaluate import error_scale, grad_error_scale
+        ref_phi, ref_dA = oracle_step(o, A_s, c_s)
+        def nerr(x, r, s):
+            d = np.abs(x - r)
+            return float(np.max(np.where(s > 0, d / np.where(s > 0, s, 1), d)))
+        err = {"phi": nerr(phi.double().cpu().numpy()[idx], ref_phi, error_scale(A_s, o, c_s)), "sample": len(idx)}
+        if dA is not None:
+            err["dphi_dA"] = nerr(dA.double().cpu().numpy()[idx], ref_dA, grad_error_scale(A_s, o, c_s))
+        extra["error_vs_oracle"] = err
+        extra["cpu_baseline"] = cpu_baseline(w, o)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "env/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "description": w.description, "n_env_per_gpu": w.n_env,
+                       "K": dag.K, "nu_max": w.nu_max, "deg_max": w.deg_max, "n_basis": dag.n_basis,
+                       "n_nodes": dag.n_nodes, "n_aux": dag.n_aux, "n_operands": dag.n_operands,
+                       "n_sinks": dag.n_sinks, "mode": mode, "readout": args.readout,
+                       "l2": f"inputs larger than L2: {n_sets} rotating buffer sets of {per_set / 1e6:.0f} MB"},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / peak_flops, "traffic": None,
+                         "kernel": "fused forward+adjoint (ace_eval_grad)", "kernel_ms": kernel_ms,
+                         "ops_per_env": ops_env, "fma_probe_tflops": probe_tflops},
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "gpu_launches": step.launches_per_step() * args.steps,
+        }
+        line.update({k: v for k, v in extra.items()})
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

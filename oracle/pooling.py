@@ -32,11 +32,13 @@ def lm_index(l: int, m: int) -> int:
     return l * l + l + m
 
 
-def real_sph_harm(P: np.ndarray, lmax: int, with_grad: bool = False):
+def real_sph_harm(P: np.ndarray, lmax: int, with_grad: bool = False, bound: bool = False):
     """Y (n, (lmax+1)^2) at the directions of the rows of P (not necessarily unit), and dY/dP (n, L, 3).
 
     The value depends on the direction only, so the gradient is the gradient of
-    Y(r / |r|) with respect to r.
+    Y(r / |r|) with respect to r.  With bound=True the gradient returned is the
+    same expression with every product term replaced by its absolute value (an
+    error scale for finite-precision evaluations, not a derivative).
     """
     P = np.asarray(P, dtype=np.float64)
     x, y, z = P[:, 0], P[:, 1], P[:, 2]
@@ -73,15 +75,20 @@ def real_sph_harm(P: np.ndarray, lmax: int, with_grad: bool = False):
             for mm, fac, g, dg in parts:
                 idx = lm_index(l, mm)
                 Y[:, idx] = fac * Q * g * h
-                if with_grad:
+                if with_grad and not bound:
                     dY[:, idx, :] = fac * (dQ[:, None] * grad_u * (g * h)[:, None]
                                            + Q[:, None] * dg * h[:, None]
                                            + (Q * g)[:, None] * grad_h)
+                elif with_grad:
+                    dY[:, idx, :] = fac * (np.abs(dQ[:, None] * grad_u * (g * h)[:, None])
+                                           + np.abs(Q[:, None] * dg * h[:, None])
+                                           + np.abs((Q * g)[:, None] * grad_h))
     return Y, dY
 
 
-def radial(r: np.ndarray, nmin: int, nmax: int, rc: float, with_grad: bool = False):
-    """R_n(r) = T_n(2r/rc - 1)(1 - r/rc)^2 for n = nmin..nmax, and dR_n/dr."""
+def radial(r: np.ndarray, nmin: int, nmax: int, rc: float, with_grad: bool = False, bound: bool = False):
+    """R_n(r) = T_n(2r/rc - 1)(1 - r/rc)^2 for n = nmin..nmax, and dR_n/dr (or, with bound=True,
+    the derivative's two product terms in absolute value)."""
     r = np.asarray(r, dtype=np.float64)
     x = 2.0 * r / rc - 1.0
     env = (1.0 - r / rc) ** 2
@@ -95,7 +102,8 @@ def radial(r: np.ndarray, nmin: int, nmax: int, rc: float, with_grad: bool = Fal
         R[:, i] = T * env
         if with_grad:
             dT = C.chebval(x, C.chebder(coef))
-            dR[:, i] = dT * (2.0 / rc) * env + T * denv
+            dR[:, i] = (np.abs(dT * (2.0 / rc) * env) + np.abs(T * denv)) if bound else \
+                dT * (2.0 / rc) * env + T * denv
     return R, dR
 
 
@@ -113,6 +121,22 @@ def one_particle(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float, with
     g = (dR[:, :, None, None] * Y[:, None, :, None] * rhat[:, None, None, :]
          + R[:, :, None, None] * dY[:, None, :, :])
     return phi, g.reshape(P.shape[0], nR * nL, 3)
+
+
+def one_particle_grad_bound(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float) -> np.ndarray:
+    """(n, K, 3): grad phi_k written as in ``one_particle`` with every product term in absolute value.
+
+    Used as the scale of the force error: |F_hat - F| / sum_k |G_k| bound_k is the
+    force analogue of |phi_hat - phi| / sum_k |c_k| |AA_k|.
+    """
+    P = np.asarray(P, dtype=np.float64)
+    r = np.linalg.norm(P, axis=1)
+    Y, dYb = real_sph_harm(P, lmax, True, bound=True)
+    R, dRb = radial(r, nmin, nmax, rc, True, bound=True)
+    rhat = np.abs(P / r[:, None])
+    g = (dRb[:, :, None, None] * np.abs(Y)[:, None, :, None] * rhat[:, None, None, :]
+         + np.abs(R)[:, :, None, None] * dYb[:, None, :, :])
+    return g.reshape(P.shape[0], R.shape[1] * Y.shape[1], 3)
 
 
 def pool_A(P: np.ndarray, offsets: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float) -> np.ndarray:

@@ -49,6 +49,7 @@ struct DevTaskSet {
   size_t vals_bytes = 0;
   void* lin = nullptr;
   size_t lin_bytes = 0;
+  int2* ent = nullptr;  // packed entries (FP32, one channel)
   bool bound = false;
   int bound_dtype = -1, bound_nout = -1;
 };
@@ -126,6 +127,8 @@ ace_status validate_plan(const Plan& p) {
       if (!in(t.row, p.n_slots)) return fail(ACE_ERR_BOUNDS, "plan: task row out of range");
       if ((t.flags & 2) && (!in(t.pl, p.n_g) || !in(t.pr, p.n_g)))
         return fail(ACE_ERR_BOUNDS, "plan: task factor out of range");
+      if (ts == &p.sym && !(t.flags & 2) && !in(t.row, p.n_g))
+        return fail(ACE_ERR_BOUNDS, "plan: adjoint row out of range");
     }
   }
   return ACE_OK;
@@ -196,8 +199,14 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
     if ((e = cudaMalloc(&dt.lin, lb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     dt.lin_bytes = lb;
   }
+  if (dtype == ACE_F32 && npad == 1 && !dt.ent) {
+    void* p = nullptr;
+    if ((e = cudaMalloc(&p, std::max<size_t>((size_t)dt.n_pad * sizeof(int2), 16))) != cudaSuccess)
+      return cuda_fail(e, "cudaMalloc");
+    dt.ent = static_cast<int2*>(p);
+  }
   e = launch_bind(dtype, c, n_out, npad, dt.ebasis, dt.ew2, dt.n_pad, dt.vals, d->slot_basis, d->plan.n_slots,
-                  dt.lin, st);
+                  dt.lin, dt.col, dt.ent, st);
   if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
   dt.bound = true;
   dt.bound_dtype = dtype;
@@ -300,6 +309,8 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     a.slice_steps = dt.slice_steps;
     a.n_slices = dt.n_slices;
     a.col = dt.col;
+    a.ent = dt.ent;
+    a.gs = dev::g_stride(p.n_g);
     a.vals = static_cast<const TT*>(dt.vals);
     a.lin = static_cast<const TT*>(dt.lin);
     a.check = checked_mode() ? 1 : 0;
@@ -494,6 +505,7 @@ void ace_dag_free(ace_dag* dag) {
     for (DevTaskSet* t : {&dag->sym, &dag->one}) {
       if (t->vals) cudaFree(t->vals);
       if (t->lin) cudaFree(t->lin);
+      if (t->ent) cudaFree(t->ent);
     }
     cudaSetDevice(cur);
   }

@@ -31,13 +31,128 @@ struct Entry {
   uint8_t w2;
 };
 
+// Slices of 32 tasks (one per lane).  Tasks are taken longest first.  In the
+// adjoint form every task adds into one "A" target (its row, or the first
+// factor of a top operand), combined across lanes by a segmented warp
+// reduction (lanes are ordered by A target), and top-operand tasks also add
+// into a "B" target (their second factor) with one shared-memory atomic per
+// lane; a task joins the slice being filled only if its B target falls in a
+// bank (slot mod 32, the accumulators being stored environment-major) not yet
+// used by another lane.  The search looks at most `kWindow` tasks ahead; a
+// slice that cannot be completed without a collision takes the next tasks.
+constexpr int kWindow = 512;
+
+void form_slices(const std::vector<Task>& tasks, const std::vector<int32_t>& order, bool atomics,
+                 std::vector<std::vector<int32_t>>& slices) {
+  std::vector<uint8_t> taken(order.size(), 0);
+  size_t head = 0;
+  while (true) {
+    while (head < order.size() && taken[head]) ++head;
+    if (head >= order.size()) break;
+    std::vector<int32_t> sl;
+    uint32_t used_b = 0;
+    size_t scanned = 0;
+    for (size_t i = head; i < order.size() && sl.size() < 32 && scanned < (size_t)kWindow; ++i) {
+      if (taken[i]) continue;
+      ++scanned;
+      const Task& t = tasks[order[i]];
+      if (atomics && (t.flags & 2)) {
+        uint32_t b = 1u << (t.pr & 31);
+        if (used_b & b) continue;
+        used_b |= b;
+      }
+      taken[i] = 1;
+      sl.push_back(order[i]);
+    }
+    for (size_t i = head; i < order.size() && sl.size() < 32; ++i) {
+      if (taken[i]) continue;
+      taken[i] = 1;
+      sl.push_back(order[i]);
+    }
+    if (atomics) {  // lanes ordered by A target so that equal targets are contiguous
+      std::stable_sort(sl.begin(), sl.end(), [&](int32_t a, int32_t b) {
+        const int32_t ka = (tasks[a].flags & 2) ? tasks[a].pl : tasks[a].row;
+        const int32_t kb = (tasks[b].flags & 2) ? tasks[b].pl : tasks[b].row;
+        return ka < kb;
+      });
+    }
+    slices.push_back(std::move(sl));
+  }
+}
+
+// Interleave the entries of one slice step by step.  At every step each lane
+// takes, among its remaining entries, one whose column falls in a shared-memory
+// bank group not yet used by the lanes of its phase (bank group = column mod
+// `bank_mod`; a phase is `phase_lanes` consecutive lanes, as in one vector
+// shared-memory load of E values per lane).  Lanes without entries left read a
+// zero coefficient at a column chosen to avoid the used groups.
+void interleave(const std::vector<const std::vector<Entry>*>& lane_entries, int32_t steps, int phase_lanes,
+                int bank_mod, int32_t n_slots, int64_t off, TaskSet& ts) {
+  const int nl = (int)lane_entries.size();
+  std::vector<std::vector<std::vector<int32_t>>> buckets(nl, std::vector<std::vector<int32_t>>(bank_mod));
+  for (int j = 0; j < nl; ++j) {
+    const auto& v = *lane_entries[j];
+    for (int32_t q = (int32_t)v.size() - 1; q >= 0; --q) buckets[j][v[q].col % bank_mod].push_back(q);
+  }
+  std::vector<int32_t> left(nl);
+  for (int j = 0; j < nl; ++j) left[j] = (int32_t)lane_entries[j]->size();
+  for (int32_t k = 0; k < steps; ++k) {
+    for (int p0 = 0; p0 < 32; p0 += phase_lanes) {
+      std::vector<uint8_t> used(bank_mod, 0);
+      std::vector<int> pending;
+      for (int j = p0; j < p0 + phase_lanes; ++j) {
+        const int64_t idx = off + (int64_t)k * 32 + j;
+        if (j >= nl || left[j] == 0) {
+          pending.push_back(j);
+          continue;
+        }
+        int chosen = -1;
+        for (int b = 0; b < bank_mod; ++b) {
+          int bb = (b + j) % bank_mod;
+          if (!used[bb] && !buckets[j][bb].empty()) {
+            chosen = bb;
+            break;
+          }
+        }
+        if (chosen < 0)
+          for (int b = 0; b < bank_mod; ++b)
+            if (!buckets[j][b].empty()) {
+              chosen = b;
+              break;
+            }
+        const int32_t q = buckets[j][chosen].back();
+        buckets[j][chosen].pop_back();
+        --left[j];
+        used[chosen] = 1;
+        const Entry& e = (*lane_entries[j])[q];
+        ts.col[idx] = e.col;
+        ts.ebasis[idx] = e.basis;
+        ts.ew2[idx] = e.w2;
+      }
+      for (int j : pending) {  // padding: zero coefficient, unused bank group if any
+        const int64_t idx = off + (int64_t)k * 32 + j;
+        int32_t c = 0;
+        for (int b = 0; b < bank_mod && b < n_slots; ++b)
+          if (!used[b]) {
+            c = b;
+            used[b] = 1;
+            break;
+          }
+        ts.col[idx] = c;
+        ts.ebasis[idx] = -1;
+        ts.ew2[idx] = 0;
+      }
+    }
+  }
+}
+
 void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<int32_t>& slot_basis,
                  int32_t n_g, bool sym, const std::vector<int32_t>& slot_l, const std::vector<int32_t>& slot_r,
                  int task_len, TaskSet& ts) {
   struct Proto {
-    Task t;
     int32_t begin, len;
   };
+  std::vector<Task> tasks;
   std::vector<Proto> protos;
   const int32_t n_slots = (int32_t)rows.size();
   for (int32_t s = 0; s < n_slots; ++s) {
@@ -45,26 +160,26 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
     const bool lin = slot_basis[s] >= 0;
     if (r.empty() && !lin) continue;
     const bool top = sym && s >= n_g;
-    int32_t n = (int32_t)r.size();
-    int32_t begin = 0;
-    bool first = true;
-    do {
-      int32_t len = std::min<int32_t>(task_len, n - begin);
-      Proto p;
-      p.t.row = s;
-      p.t.flags = (first ? 1 : 0) | (top ? 2 : 0);
-      p.t.pl = top ? slot_l[s] : -1;
-      p.t.pr = top ? slot_r[s] : -1;
-      p.begin = begin;
-      p.len = len;
-      protos.push_back(p);
-      begin += len;
-      first = false;
-    } while (begin < n);
+    const int32_t n = (int32_t)r.size();
+    // equal pieces of at most task_len entries
+    const int32_t pieces = std::max<int32_t>(1, (n + task_len - 1) / task_len);
+    for (int32_t p = 0; p < pieces; ++p) {
+      const int32_t b = (int32_t)((int64_t)n * p / pieces), e = (int32_t)((int64_t)n * (p + 1) / pieces);
+      Task t;
+      t.row = s;
+      t.flags = (p == 0 ? 1 : 0) | (top ? 2 : 0);
+      t.pl = top ? slot_l[s] : -1;
+      t.pr = top ? slot_r[s] : -1;
+      tasks.push_back(t);
+      protos.push_back({b, e - b});
+    }
   }
-  std::stable_sort(protos.begin(), protos.end(), [](const Proto& a, const Proto& b) { return a.len > b.len; });
-  const int32_t n_tasks = (int32_t)protos.size();
-  const int32_t n_slices = (n_tasks + 31) / 32;
+  std::vector<int32_t> order(tasks.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return protos[a].len > protos[b].len; });
+  std::vector<std::vector<int32_t>> slices;
+  form_slices(tasks, order, sym, slices);
+  const int32_t n_slices = (int32_t)slices.size();
   ts = TaskSet();
   ts.tasks.resize((size_t)n_slices * 32, Task{-1, 0, -1, -1});
   ts.slice_off.assign(n_slices + 1, 0);
@@ -72,10 +187,7 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
   int64_t off = 0;
   for (int32_t s = 0; s < n_slices; ++s) {
     int32_t steps = 0;
-    for (int j = 0; j < 32; ++j) {
-      int32_t ti = s * 32 + j;
-      if (ti < n_tasks) steps = std::max(steps, protos[ti].len);
-    }
+    for (int32_t ti : slices[s]) steps = std::max(steps, protos[ti].len);
     ts.slice_off[s] = (int32_t)off;
     ts.slice_steps[s] = steps;
     off += (int64_t)steps * 32;
@@ -85,22 +197,18 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
   ts.ebasis.assign(off, -1);
   ts.ew2.assign(off, 0);
   ts.n_entries = 0;
+  std::vector<std::vector<Entry>> lane_store(32);
   for (int32_t s = 0; s < n_slices; ++s) {
-    for (int j = 0; j < 32; ++j) {
-      int32_t ti = s * 32 + j;
-      if (ti >= n_tasks) continue;
-      const Proto& p = protos[ti];
-      ts.tasks[ti] = p.t;
-      const auto& r = rows[p.t.row];
-      for (int32_t k = 0; k < p.len; ++k) {
-        const Entry& e = r[p.begin + k];
-        int64_t idx = (int64_t)ts.slice_off[s] + (int64_t)k * 32 + j;
-        ts.col[idx] = e.col;
-        ts.ebasis[idx] = e.basis;
-        ts.ew2[idx] = e.w2;
-      }
-      ts.n_entries += p.len;
+    std::vector<const std::vector<Entry>*> lanes;
+    for (size_t j = 0; j < slices[s].size(); ++j) {
+      const int32_t ti = slices[s][j];
+      ts.tasks[(size_t)s * 32 + j] = tasks[ti];
+      const auto& r = rows[tasks[ti].row];
+      lane_store[j].assign(r.begin() + protos[ti].begin, r.begin() + protos[ti].begin + protos[ti].len);
+      lanes.push_back(&lane_store[j]);
+      ts.n_entries += protos[ti].len;
     }
+    interleave(lanes, ts.slice_steps[s], 16, 16, n_slots, ts.slice_off[s], ts);
   }
 }
 

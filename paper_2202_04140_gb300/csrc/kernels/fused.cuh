@@ -40,6 +40,7 @@ struct FusedArgs {
   int64_t n_env;
   int64_t n_tiles;
   int32_t K, n_slots, n_g, n_out;
+  int32_t gs;  // stride between environments in G (n_g rounded up to 32)
   const int32_t* fwd_slot;
   const int32_t* fwd_l;
   const int32_t* fwd_r;
@@ -54,6 +55,7 @@ struct FusedArgs {
   const int32_t* slice_steps;
   int32_t n_slices;
   const int32_t* col;
+  const int2* ent;  // packed {column, coefficient bits} (FP32, one channel)
   const T* vals;  // [entries][NOUT]
   const T* lin;   // [n_slots][NOUT]
   int32_t check;
@@ -61,7 +63,9 @@ struct FusedArgs {
 };
 
 // Byte offsets of the shared-memory regions of one CTA (each 16-byte aligned):
-// AA [n_slots][E], G [n_g][E] (adjoint only), phibar [E][NOUT], phi partials
+// AA [n_slots][E] (slot-major: the E values of one slot are one vector load),
+// G [E][gs] (adjoint only, environment-major: the bank of an accumulator is
+// its slot mod 32, gs = n_g rounded up to 32), phibar [E][NOUT], phi partials
 // [warps][E][NOUT] in FP64.
 struct SmemLayout {
   size_t g, pb, red, total;
@@ -69,11 +73,13 @@ struct SmemLayout {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+__host__ __device__ inline int g_stride(int n_g) { return (n_g + 31) & ~31; }
+
 __host__ __device__ inline SmemLayout smem_layout(int E, int NOUT, bool grad, int n_slots, int n_g, int NT,
                                                   int tsize) {
   SmemLayout L;
   L.g = align16((size_t)n_slots * E * tsize);
-  L.pb = L.g + (grad ? align16((size_t)n_g * E * tsize) : 0);
+  L.pb = L.g + (grad ? align16((size_t)g_stride(n_g) * E * tsize) : 0);
   L.red = L.pb + align16((size_t)E * NOUT * tsize);
   L.total = L.red + (size_t)(NT / 32) * E * NOUT * sizeof(double);
   return L;
@@ -83,11 +89,6 @@ __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fma
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // ---- vector helpers ---------------------------------------------------------------
-
-template <typename T, int E>
-struct Vec {
-  T v[E];
-};
 
 template <typename T, int E>
 __device__ __forceinline__ void load_slot(const T* __restrict__ p, T (&x)[E]) {
@@ -205,12 +206,87 @@ struct Acc<double, kReadPlain> : AccD<double> {};
 
 // ---- the kernel ------------------------------------------------------------------------
 
+// Entries of one lane's task, software-pipelined: the (column, coefficient)
+// pairs of the next kBatch steps are loaded while the current kBatch are used.
+constexpr int kBatch = 8;
+
+template <typename T, int E, int NOUT, bool CHECK>
+__device__ __forceinline__ void task_entries(const FusedArgs<T>& a, const T* __restrict__ AA, int32_t off,
+                                             int steps, int lane, T (&acc)[E][NOUT]) {
+  constexpr bool kPacked = sizeof(T) == 4 && NOUT == 1;
+  if constexpr (kPacked) {
+    const int2* ep = a.ent + off + lane;
+    int2 cur[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) cur[u] = u < steps ? __ldg(ep + u * 32) : make_int2(0, 0);
+    for (int k = 0; k < steps; k += kBatch) {
+      int2 nxt[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u)
+        nxt[u] = (k + kBatch + u < steps) ? __ldg(ep + (size_t)(k + kBatch + u) * 32) : make_int2(0, 0);
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        if (k + u < steps) {
+          int j = cur[u].x;
+          if constexpr (CHECK) {
+            if ((unsigned)j >= (unsigned)a.n_slots) {
+              atomicOr(a.status, kStatusBounds);
+              j = 0;
+            }
+          }
+          T x[E];
+          load_slot<T, E>(AA + (size_t)j * E, x);
+          const T v = __int_as_float(cur[u].y);
+#pragma unroll
+          for (int e = 0; e < E; ++e) acc[e][0] = fma_t(v, x[e], acc[e][0]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) cur[u] = nxt[u];
+    }
+  } else {
+    const int32_t* colp = a.col + off + lane;
+    const T* valp = a.vals + ((size_t)off + lane) * NOUT;
+    int cur[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) cur[u] = u < steps ? __ldg(colp + u * 32) : 0;
+    for (int k = 0; k < steps; k += kBatch) {
+      int nxt[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) nxt[u] = (k + kBatch + u < steps) ? __ldg(colp + (size_t)(k + kBatch + u) * 32) : 0;
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        if (k + u < steps) {
+          int j = cur[u];
+          if constexpr (CHECK) {
+            if ((unsigned)j >= (unsigned)a.n_slots) {
+              atomicOr(a.status, kStatusBounds);
+              j = 0;
+            }
+          }
+          T v[NOUT];
+          load_vals<T, NOUT>(valp + (size_t)(k + u) * 32 * NOUT, v);
+          T x[E];
+          load_slot<T, E>(AA + (size_t)j * E, x);
+#pragma unroll
+          for (int e = 0; e < E; ++e)
+#pragma unroll
+            for (int c = 0; c < NOUT; ++c) acc[e][c] = fma_t(v[c], x[e], acc[e][c]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) cur[u] = nxt[u];
+    }
+  }
+}
+
 template <typename T, int E, int NOUT, bool GRAD, int RO, int NT, bool CHECK>
 __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
                                           const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT]) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
+  const int gs = a.gs;
   for (int sl = warp; sl < a.n_slices; sl += NW) {
     const int4 task = __ldg(a.tasks + (size_t)sl * 32 + lane);
     const int steps = __ldg(a.slice_steps + sl);
@@ -220,70 +296,73 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
     for (int e = 0; e < E; ++e)
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) acc[e][c] = T(0);
-    const int32_t* colp = a.col + off + lane;
-    const T* valp = a.vals + ((size_t)off + lane) * NOUT;
-#pragma unroll 4
-    for (int k = 0; k < steps; ++k) {
-      int32_t j = __ldg(colp + (size_t)k * 32);
-      T v[NOUT];
-      load_vals<T, NOUT>(valp + (size_t)k * 32 * NOUT, v);
-      if constexpr (CHECK) {
-        if ((unsigned)j >= (unsigned)a.n_slots) {
-          atomicOr(a.status, kStatusBounds);
-          continue;
-        }
-      }
-      T x[E];
-      load_slot<T, E>(AA + (size_t)j * E, x);
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-#pragma unroll
-        for (int c = 0; c < NOUT; ++c) acc[e][c] = fma_t(v[c], x[e], acc[e][c]);
-    }
-    const int row = task.x;
-    if (row < 0) continue;
+    task_entries<T, E, NOUT, CHECK>(a, AA, off, steps, lane, acc);
+    const bool top = (task.y & 2) != 0;
+    bool valid = task.x >= 0;
     if constexpr (CHECK) {
-      bool bad = (unsigned)row >= (unsigned)a.n_slots;
-      if (GRAD && (task.y & 2)) bad |= (unsigned)task.z >= (unsigned)a.n_g || (unsigned)task.w >= (unsigned)a.n_g;
-      if (GRAD && !(task.y & 2)) bad |= (unsigned)row >= (unsigned)a.n_g;
+      bool bad = valid && (unsigned)task.x >= (unsigned)a.n_slots;
+      if (GRAD && valid && top) bad |= (unsigned)task.z >= (unsigned)a.n_g || (unsigned)task.w >= (unsigned)a.n_g;
+      if (GRAD && valid && !top) bad |= (unsigned)task.x >= (unsigned)a.n_g;
       if (bad) {
         atomicOr(a.status, kStatusBounds);
-        continue;
+        valid = false;
       }
     }
+    const int row = valid ? task.x : 0;
     T lin[NOUT];
 #pragma unroll
     for (int c = 0; c < NOUT; ++c) lin[c] = T(0);
-    if (task.y & 1) load_vals<T, NOUT>(a.lin + (size_t)row * NOUT, lin);
+    if (valid && (task.y & 1)) load_vals<T, NOUT>(a.lin + (size_t)row * NOUT, lin);
     T ap[E];
     load_slot<T, E>(AA + (size_t)row * E, ap);
     const T half = GRAD ? T(0.5) : T(1);
+    if (valid) {
 #pragma unroll
-    for (int e = 0; e < E; ++e)
+      for (int e = 0; e < E; ++e)
 #pragma unroll
-      for (int c = 0; c < NOUT; ++c) phiacc[e][c].add(ap[e] * fma_t(half, acc[e][c], lin[c]));
+        for (int c = 0; c < NOUT; ++c) phiacc[e][c].add(ap[e] * fma_t(half, acc[e][c], lin[c]));
+    }
     if constexpr (GRAD) {
+      // g = phibar . (c_s + u): the adjoint of this task's stored value
       T g[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         T s = T(0);
 #pragma unroll
         for (int c = 0; c < NOUT; ++c) s = fma_t(pb[e * NOUT + c], acc[e][c] + lin[c], s);
-        g[e] = s;
+        g[e] = valid ? s : T(0);
       }
-      if (task.y & 2) {
-        const int pl = task.z, pr = task.w;
-        T xl[E], xr[E];
-        load_slot<T, E>(AA + (size_t)pl * E, xl);
-        load_slot<T, E>(AA + (size_t)pr * E, xr);
+      const int pl = (valid && top) ? task.z : 0, pr = (valid && top) ? task.w : 0;
+      T xl[E], xr[E];
+      load_slot<T, E>(AA + (size_t)pl * E, xl);
+      load_slot<T, E>(AA + (size_t)pr * E, xr);
+      // "A" target: the row itself, or the first factor of a top operand.  Lanes
+      // are ordered by A target, so equal targets form runs; a segmented suffix
+      // sum leaves each run's total in its first lane, which does one atomic.
+      int key = valid ? (top ? pl : row) : -1 - lane;
+      T va[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) va[e] = top ? g[e] * xr[e] : g[e];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int k2 = __shfl_down_sync(0xffffffffu, key, d);
+        const bool same = (lane + d < 32) && (k2 == key);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          atomicAdd(G + (size_t)pl * E + e, g[e] * xr[e]);
-          atomicAdd(G + (size_t)pr * E + e, g[e] * xl[e]);
+          const T y = __shfl_down_sync(0xffffffffu, va[e], d);
+          if (same) va[e] += y;
         }
-      } else {
+      }
+      const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+      const bool head = lane == 0 || kprev != key;
+      if (valid && head) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)row * E + e, g[e]);
+        for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * gs + key, va[e]);
+      }
+      // "B" target: the second factor of a top operand, one atomic per lane
+      if (valid && top) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * gs + pr, g[e] * xl[e]);
       }
     }
   }
@@ -311,7 +390,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
       AA[(size_t)k * E + e] = env < a.n_env ? a.A[env * K + k] : T(0);
     }
     if constexpr (GRAD) {
-      for (int i = tid; i < a.n_g * E; i += NT) G[i] = T(0);
+      for (int i = tid; i < a.gs * E; i += NT) G[i] = T(0);
       for (int i = tid; i < E * NOUT; i += NT) {
         const int e = i / NOUT, c = i - e * NOUT;
         const int64_t env = env0 + e;
@@ -356,14 +435,14 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
             atomicOr(a.status, kStatusBounds);
             continue;
           }
-          T g[E], xl[E], xr[E];
-          load_slot<T, E>(G + (size_t)s * E, g);
+          T xl[E], xr[E];
           load_slot<T, E>(AA + (size_t)l * E, xl);
           load_slot<T, E>(AA + (size_t)r * E, xr);
 #pragma unroll
           for (int e = 0; e < E; ++e) {
-            atomicAdd(G + (size_t)l * E + e, g[e] * xr[e]);
-            atomicAdd(G + (size_t)r * E + e, g[e] * xl[e]);
+            const T g = G[(size_t)e * a.gs + s];
+            atomicAdd(G + (size_t)e * a.gs + l, g * xr[e]);
+            atomicAdd(G + (size_t)e * a.gs + r, g * xl[e]);
           }
         }
         __syncthreads();
@@ -371,7 +450,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
       for (int i = tid; i < E * K; i += NT) {
         const int e = i / K, k = i - e * K;
         const int64_t env = env0 + e;
-        if (env < a.n_env) a.dA[env * K + k] = G[(size_t)k * E + e];
+        if (env < a.n_env) a.dA[env * K + k] = G[(size_t)e * a.gs + k];
       }
     }
     // 5. phi: warp reduction, then the warps in fixed order

@@ -4,10 +4,16 @@
 
 namespace ace {
 
-const void* fused_ptr_f64_n16_fwd(int E, int ro) {
+const void* fused_ptr_f64_n16_fwd(int E, int ro, int* nt) {
   using namespace dev;
-  if (E == 1 && ro == 0) return (const void*)&fused_kernel<double, 1, 16, false, 0, 256>;
-  if (E == 2 && ro == 0) return (const void*)&fused_kernel<double, 2, 16, false, 0, 256>;
+  if (E == 1 && ro == 0) {
+    *nt = 256;
+    return (const void*)&fused_kernel<double, 1, 16, false, 0, 256>;
+  }
+  if (E == 2 && ro == 0) {
+    *nt = 256;
+    return (const void*)&fused_kernel<double, 2, 16, false, 0, 256>;
+  }
   return nullptr;
 }
 

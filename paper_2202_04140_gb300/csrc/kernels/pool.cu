@@ -40,6 +40,29 @@ __constant__ float c_dfac[kPoolLmax + 2];               // (2m-1)!!
 
 __device__ __forceinline__ int qidx(int l, int m) { return l * (l + 1) / 2 + m; }
 
+// Neighbour geometry.  r, 2r/rc - 1 and 1 - r/rc are formed in FP64 from the
+// exact FP32 coordinates, so that 1 - r/rc keeps full FP32 relative accuracy
+// next to the cutoff (in FP32 it loses digits to cancellation there).
+struct Geo {
+  bool ok;
+  float ir, xh, yh, u, t, w;
+};
+
+__device__ __forceinline__ void geometry(float x, float y, float z, float rc, Geo& g) {
+  const double xd = x, yd = y, zd = z;
+  const double r2 = xd * xd + yd * yd + zd * zd;
+  const double r = sqrt(r2);
+  const double rcd = rc;
+  g.ok = r > 0.0 && r < rcd;
+  const double ir = g.ok ? 1.0 / r : 0.0;
+  g.ir = (float)ir;
+  g.xh = (float)(xd * ir);
+  g.yh = (float)(yd * ir);
+  g.u = (float)(zd * ir);
+  g.t = (float)(2.0 * r / rcd - 1.0);
+  g.w = (float)(1.0 - r / rcd);
+}
+
 // Q[qidx(l,m)] = Q_l^m(u) for 0 <= m <= l <= lmax.
 template <int LMAX>
 __device__ __forceinline__ void legendre_q(float u, float (&Q)[kPoolQ]) {
@@ -78,14 +101,11 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
       const int cnt = (int)((j1 - jb) < kPoolChunk ? (j1 - jb) : kPoolChunk);
       if (lane < cnt) {
         const float x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
-        const float r = sqrtf(x * x + y * y + z * z);
-        const bool ok = r > 0.f && r < rc;
-        const float ir = ok ? 1.f / r : 0.f;
-        const float xh = x * ir, yh = y * ir, u = z * ir;
-        // radial
-        const float t = 2.f * r / rc - 1.f;
-        const float w = (1.f - r / rc);
-        const float env2 = ok ? w * w : 0.f;
+        Geo g;
+        geometry(x, y, z, rc, g);
+        const bool ok = g.ok;
+        const float xh = g.xh, yh = g.yh, u = g.u, t = g.t;
+        const float env2 = ok ? g.w * g.w : 0.f;
         float Tm1 = 1.f, T = t;
         for (int n = 1; n <= nmax; ++n) {
           if (n >= nmin) sR[warp][lane][n - nmin] = T * env2;
@@ -162,17 +182,17 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
     const int64_t j0 = offsets[env], j1 = offsets[env + 1];
     for (int64_t j = j0 + lane; j < j1; j += 32) {
       const float x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
-      const float r = sqrtf(x * x + y * y + z * z);
-      if (!(r > 0.f && r < rc)) {
+      Geo geo;
+      geometry(x, y, z, rc, geo);
+      if (!geo.ok) {
         dpos[3 * j] = 0.f;
         dpos[3 * j + 1] = 0.f;
         dpos[3 * j + 2] = 0.f;
         continue;
       }
-      const float ir = 1.f / r;
-      const float xh = x * ir, yh = y * ir, u = z * ir;
-      const float t = 2.f * r / rc - 1.f;
-      const float w = 1.f - r / rc;
+      const float ir = geo.ir;
+      const float xh = geo.xh, yh = geo.yh, u = geo.u, t = geo.t;
+      const float w = geo.w;
       const float env2 = w * w, denv = -2.f * w / rc;
       float R[kPoolMaxR], dR[kPoolMaxR];
       {

@@ -1,0 +1,143 @@
+"""GPU parity of the pooling kernels and the full forces pipeline against the FP64 oracle (C ABI).
+
+A is gated by |A - ref| / sum_j |R_n Y_lm|; forces by |F - ref| / (the oracle's
+forces assembled from |G| and |grad phi_k|); phi by the usual normaliser.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.basis import workload_index_set
+from oracle.evaluate import error_scale, grad_naive, phi_naive
+from oracle.pooling import forces, one_particle, one_particle_grad_bound, pool_A
+from tests.metrics import normalized_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def abs_pool(P, offsets, w):
+    phi, _ = one_particle(P, w.nmin, w.nmax, w.lmax, w.rc)
+    A = np.zeros((len(offsets) - 1, phi.shape[1]))
+    for e in range(A.shape[0]):
+        A[e] = np.abs(phi[offsets[e]:offsets[e + 1]]).sum(axis=0)
+    return A
+
+
+def force_scale(P, offsets, G, w):
+    g = one_particle_grad_bound(P, w.nmin, w.nmax, w.lmax, w.rc)
+    S = np.zeros((P.shape[0], 3))
+    for e in range(len(offsets) - 1):
+        a, b = offsets[e], offsets[e + 1]
+        S[a:b] = np.einsum("k,jkd->jd", np.abs(G[e]), np.abs(g[a:b]))
+    return S
+
+
+def inputs(n_env, seed=3, j_range=(10, 60)):
+    w = W.WORKLOADS["forces_k392"]
+    offsets, P = W.draw_neighbours(n_env, seed=seed, rc=w.rc, j_range=j_range)
+    return w, offsets, W.round_to(P, "f32")
+
+
+def test_pool_matches_oracle(dev):
+    from paper_2202_04140_gb300.torch_api import pool_A as gpu_pool
+    w, offsets, P = inputs(200)
+    A = gpu_pool(torch.tensor(P, dtype=torch.float32, device=dev), torch.tensor(offsets, device=dev),
+                 w.nmin, w.nmax, w.lmax, w.rc).cpu().numpy()
+    ref = pool_A(P, offsets, w.nmin, w.nmax, w.lmax, w.rc)
+    assert normalized_error(A, ref, abs_pool(P, offsets, w)) < TOL32
+
+
+@pytest.mark.parametrize("lmax,nmin,nmax", [(0, 1, 3), (3, 0, 5), (8, 1, 16)])
+def test_pool_other_shapes(dev, lmax, nmin, nmax):
+    from paper_2202_04140_gb300.torch_api import pool_A as gpu_pool, pool_A_grad
+    offsets, P = W.draw_neighbours(9, seed=8, rc=5.0, j_range=(0, 40))
+    P = W.round_to(P, "f32")
+    Pt, ot = torch.tensor(P, dtype=torch.float32, device=dev), torch.tensor(offsets, device=dev)
+    A = gpu_pool(Pt, ot, nmin, nmax, lmax, 5.0).cpu().numpy()
+    ref = pool_A(P, offsets, nmin, nmax, lmax, 5.0)
+    phi, _ = one_particle(P, nmin, nmax, lmax, 5.0)
+    g = one_particle_grad_bound(P, nmin, nmax, lmax, 5.0)
+    scale = np.zeros_like(ref)
+    for e in range(len(offsets) - 1):
+        scale[e] = np.abs(phi[offsets[e]:offsets[e + 1]]).sum(axis=0)
+    assert normalized_error(A, ref, scale) < TOL32
+    G = np.random.default_rng(2).standard_normal(ref.shape)
+    dpos = pool_A_grad(Pt, ot, torch.tensor(G, dtype=torch.float32, device=dev), nmin, nmax, lmax, 5.0)
+    Fref = -forces(P, offsets, G, nmin, nmax, lmax, 5.0)
+    S = np.zeros_like(Fref)
+    for e in range(len(offsets) - 1):
+        a, b = offsets[e], offsets[e + 1]
+        S[a:b] = np.einsum("k,jkd->jd", np.abs(G[e]), np.abs(g[a:b]))
+    assert normalized_error(dpos.cpu().numpy(), Fref, S) < TOL32
+
+
+def test_forces_pipeline_small_batch(dev):
+    """pooling -> fused forward + adjoint -> pooling adjoint, against the oracle's chain rule."""
+    from paper_2202_04140_gb300.torch_api import Dag, Spec, energy_and_forces
+    w, offsets, P = inputs(96)
+    o = workload_index_set(w)
+    s = Spec.from_workload(w)
+    d = Dag(s)
+    c = W.round_to(W.draw_c(o.deg, 1), "f32")
+    phi, F = energy_and_forces(d, torch.tensor(P, dtype=torch.float32, device=dev),
+                               torch.tensor(offsets, device=dev), torch.tensor(c, dtype=torch.float32, device=dev),
+                               w.nmin, w.nmax, w.lmax, w.rc)
+    A = pool_A(P, offsets, w.nmin, w.nmax, w.lmax, w.rc)
+    ref = phi_naive(A, o, c)
+    Aabs = abs_pool(P, offsets, w)
+    assert normalized_error(phi.cpu().numpy(), ref, error_scale(Aabs, o, c)) < TOL32
+    G = grad_naive(A, o, c)
+    Fref = forces(P, offsets, G, w.nmin, w.nmax, w.lmax, w.rc)
+    Gabs = grad_naive(Aabs, o, np.abs(c))
+    assert normalized_error(F.cpu().numpy(), Fref, force_scale(P, offsets, Gabs, w)) < TOL32
+
+
+def test_forces_permutation_invariance(dev):
+    from paper_2202_04140_gb300.torch_api import Dag, Spec, energy_and_forces
+    w, offsets, P = inputs(8)
+    s = Spec.from_workload(w)
+    d = Dag(s)
+    c = torch.tensor(W.round_to(W.draw_c(s.deg, 1), "f32"), dtype=torch.float32, device=dev)
+    perm = np.arange(P.shape[0])
+    for e in range(len(offsets) - 1):
+        a, b = offsets[e], offsets[e + 1]
+        perm[a:b] = a + np.random.default_rng(e).permutation(b - a)
+    ot = torch.tensor(offsets, device=dev)
+    phi1, F1 = energy_and_forces(d, torch.tensor(P, dtype=torch.float32, device=dev), ot, c,
+                                 w.nmin, w.nmax, w.lmax, w.rc)
+    phi2, F2 = energy_and_forces(d, torch.tensor(P[perm], dtype=torch.float32, device=dev), ot, c,
+                                 w.nmin, w.nmax, w.lmax, w.rc)
+    assert torch.allclose(phi1, phi2, rtol=1e-5, atol=1e-6)
+    assert torch.allclose(F1[torch.tensor(perm, device=dev)], F2, rtol=1e-4, atol=1e-6)
+
+
+def test_forces_full_size_sampled(dev):
+    """50k environments in one pipeline call; sampled environments against the oracle."""
+    from paper_2202_04140_gb300.torch_api import Dag, Spec, energy_and_forces
+    w, offsets, P = inputs(w_n := W.WORKLOADS["forces_k392"].n_env)
+    o = workload_index_set(w)
+    d = Dag(Spec.from_workload(w))
+    c = W.round_to(W.draw_c(o.deg, 1), "f32")
+    phi, F = energy_and_forces(d, torch.tensor(P, dtype=torch.float32, device=dev),
+                               torch.tensor(offsets, device=dev), torch.tensor(c, dtype=torch.float32, device=dev),
+                               w.nmin, w.nmax, w.lmax, w.rc)
+    phi, F = phi.cpu().numpy(), F.cpu().numpy()
+    for e in [0, 12345, w_n - 1]:
+        a, b = offsets[e], offsets[e + 1]
+        Pe, oe = P[a:b], np.array([0, b - a])
+        A = pool_A(Pe, oe, w.nmin, w.nmax, w.lmax, w.rc)
+        Aabs = abs_pool(Pe, oe, w)
+        assert normalized_error(phi[e:e + 1], phi_naive(A, o, c), error_scale(Aabs, o, c)) < TOL32
+        G = grad_naive(A, o, c)
+        Gabs = grad_naive(Aabs, o, np.abs(c))
+        Fref = forces(Pe, oe, G, w.nmin, w.nmax, w.lmax, w.rc)
+        assert normalized_error(F[a:b], Fref, force_scale(Pe, oe, Gabs, w)) < TOL32

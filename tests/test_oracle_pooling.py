@@ -108,3 +108,12 @@ def test_pooling_forces_permutation_and_fd():
             fp = phi_naive(pool_A(Pp, offsets, 1, 3, 2, rc), s, c).sum()
             fm = phi_naive(pool_A(Pm, offsets, 1, 3, 2, rc), s, c).sum()
             assert abs(-(fp - fm) / (2 * h) - F[j, d]) < 1e-7 * max(1.0, abs(F[j, d]))
+
+
+def test_gradient_bound_dominates_gradient():
+    """The force error scale is at least the magnitude of the gradient it bounds, term by term."""
+    from oracle.pooling import one_particle_grad_bound
+    P = unit(9, 6) * np.random.default_rng(8).uniform(0.2, 4.9, 9)[:, None]
+    _, g = one_particle(P, 1, 8, LMAX, 5.0, with_grad=True)
+    b = one_particle_grad_bound(P, 1, 8, LMAX, 5.0)
+    assert np.all(b >= np.abs(g) * (1 - 1e-12) - 1e-300)
