@@ -196,6 +196,29 @@ ace_status ace_eval_plain_f64(ace_dag* dag, const double* A, const double* c, co
                               int64_t n_env, int32_t n_out, double* phi, double* dA, void* workspace,
                               size_t workspace_bytes, void* stream);
 
+/* The same plain FP64 graph walk without any device allocation.
+ * The paper has no counterpart to this entry point.  It exists for callers that
+ * must not call cudaMalloc: code that runs where the device heap is owned by
+ * another allocator (a framework's caching allocator reserving the memory),
+ * code on latency-critical paths where an allocation call, which may
+ * synchronise the device, is not acceptable, and hosts that only hand out
+ * input and output buffers.  Its scratch is one array of 32 MiB that lives in
+ * the library image on every GPU that loads libace, until the process exits.
+ * Inside it go the graph (three int32 arrays of n_nodes, copied from host
+ * memory on each call) and the node values (n_nodes x n_env doubles, twice that
+ * when dA != NULL).  A request larger than the array fails with
+ * ACE_ERR_INVALID_ARG and a message giving the bytes needed; nothing is
+ * truncated or split.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  Every call on a device shares the array and the kernel
+ * writes each scratch value before reading it, so nothing is cleared between
+ * calls; calls whose work overlaps on the GPU (other streams, other threads)
+ * race on the array and must be serialised by the caller.  The graph handle is
+ * used on the host only (no upload).  Arguments and results are those of
+ * ace_eval_plain_f64, minus the workspace. */
+ace_status ace_eval_plain_f64_static(ace_dag* dag, const double* A, const double* c, const double* phi_bar,
+                                     int64_t n_env, int32_t n_out, double* phi, double* dA, void* stream);
+
 /* ---- neighbour pooling (device, O(3) only) ------------------------------------ */
 
 /* A[e][id(n,l,m)] = sum_{j in env e} R_n(|r_j|) Y_lm(r_j/|r_j|)   (Eq. 2, section 2.4)

@@ -32,7 +32,7 @@ EXPORTED = [
     "ace_last_error", "ace_abi_version", "ace_build_spec", "ace_spec_info", "ace_spec_tuples",
     "ace_spec_free", "ace_build_dag", "ace_dag_info", "ace_dag_export", "ace_dag_plan_info",
     "ace_dag_plan_array", "ace_dag_free", "ace_dag_upload", "ace_eval", "ace_eval_grad", "ace_eval_plain_workspace_bytes",
-    "ace_eval_plain_f64", "ace_pool_A", "ace_pool_A_grad", "ace_stream_status", "ace_device_info",
+    "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_stream_status", "ace_device_info",
     "ace_fma_peak",
 ]
 
@@ -73,6 +73,7 @@ _SIG = {
     "ace_eval_grad": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _i32, _i32, _p, _p, _p]),
     "ace_eval_plain_workspace_bytes": (C.c_int, [_p, _i64, _i32, _P(_sz)]),
     "ace_eval_plain_f64": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _p, _p, _p, _sz, _p]),
+    "ace_eval_plain_f64_static": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _p, _p, _p]),
     "ace_pool_A": (C.c_int, [_p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _p, _p]),
     "ace_pool_A_grad": (C.c_int, [_p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _p, _p, _p]),
     "ace_stream_status": (C.c_int, [_p, _p]),
@@ -198,6 +199,12 @@ def ace_eval_plain_workspace_bytes(dag, n_env, with_grad) -> int:
 def ace_eval_plain_f64(dag, A, c, phi_bar, n_env, n_out, phi, dA, workspace, workspace_bytes, stream=0):
     _check(_lib.ace_eval_plain_f64(dag, A, c, phi_bar, n_env, n_out, phi, dA, workspace, workspace_bytes, stream),
            "ace_eval_plain_f64")
+
+
+def ace_eval_plain_f64_static(dag, A, c, phi_bar, n_env, n_out, phi, dA, stream=0):
+    """Plain FP64 graph walk with the library's fixed 32 MiB device scratch: allocates nothing."""
+    _check(_lib.ace_eval_plain_f64_static(dag, A, c, phi_bar, n_env, n_out, phi, dA, stream),
+           "ace_eval_plain_f64_static")
 
 
 def ace_pool_A(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, A, stream=0):

@@ -571,6 +571,44 @@ ace_status ace_eval_plain_f64(ace_dag* dag, const double* A, const double* c, co
   return ACE_OK;
 }
 
+ace_status ace_eval_plain_f64_static(ace_dag* dag, const double* A, const double* c, const double* phi_bar,
+                                     int64_t n_env, int32_t n_out, double* phi, double* dA, void* stream) {
+  ace_status s = check_eval_args(dag, A, n_env, n_out, ACE_F64, 0);
+  if (s != ACE_OK) return s;
+  if (n_env == 0) return ACE_OK;
+  if (!c) return fail(ACE_ERR_INVALID_ARG, "c is NULL");
+  if (!phi && !dA) return fail(ACE_ERR_INVALID_ARG, "nothing to compute: phi and dA are NULL");
+  const int64_t N = dag->g.n_nodes();
+  const size_t graph_bytes = (size_t(3) * (size_t)N * sizeof(int32_t) + 255) & ~size_t(255);
+  const size_t value_bytes = (size_t)N * (size_t)n_env * sizeof(double) * (dA ? 2 : 1);
+  const size_t cap = static_scratch_bytes();
+  if (graph_bytes + value_bytes > cap)
+    return fail(ACE_ERR_INVALID_ARG, "ace_eval_plain_f64_static needs " + std::to_string(graph_bytes + value_bytes) +
+                                         " bytes of scratch; the static scratch holds " + std::to_string(cap) +
+                                         " bytes (at most " +
+                                         std::to_string((cap - std::min(cap, graph_bytes)) /
+                                                        ((size_t)N * sizeof(double) * (dA ? 2 : 1))) +
+                                         " environments for this graph)");
+  void* base = nullptr;
+  cudaError_t e = static_scratch_ptr(&base);
+  if (e != cudaSuccess) return cuda_fail(e, "static scratch lookup");
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* left = static_cast<int32_t*>(base);
+  int32_t* right = left + N;
+  int32_t* nbasis = right + N;
+  double* AA = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + graph_bytes);
+  double* abar = dA ? AA + (size_t)N * n_env : nullptr;
+  if ((e = cudaMemcpyAsync(left, dag->g.left.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(right, dag->g.right.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(nbasis, dag->g.node_basis.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess)
+    return cuda_fail(e, "graph copy into the static scratch");
+  e = launch_plain_f64(A, c, phi_bar, n_env, n_out, dag->K, N, left, right, nbasis, phi, dA, AA, abar, st);
+  if (e != cudaSuccess) return cuda_fail(e, "plain kernel launch");
+  return ACE_OK;
+}
+
 static ace_status check_pool_args(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
                                   int32_t nmin, int32_t nmax, int32_t lmax) {
   if (n_env < 0 || n_pairs < 0) return fail(ACE_ERR_INVALID_ARG, "sizes must be >= 0");

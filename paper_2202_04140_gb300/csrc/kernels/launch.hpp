@@ -21,6 +21,10 @@ cudaError_t launch_plain_f64(const double* A, const double* c, const double* phi
                              int64_t n_nodes, const int32_t* left, const int32_t* right, const int32_t* node_basis,
                              double* phi, double* dA, double* AA, double* abar, cudaStream_t st);
 
+// Fixed device scratch of ace_eval_plain_f64_static (plain_static.cu).
+size_t static_scratch_bytes();
+cudaError_t static_scratch_ptr(void** out);
+
 cudaError_t launch_fma_probe(int64_t iters, int blocks, int threads, float* out, cudaStream_t st);
 
 cudaError_t launch_pool(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
