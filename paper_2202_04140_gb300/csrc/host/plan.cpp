@@ -42,8 +42,8 @@ struct Entry {
 // slice that cannot be completed without a collision takes the next tasks.
 constexpr int kWindow = 512;
 
-void form_slices(const std::vector<Task>& tasks, const std::vector<int32_t>& order, bool atomics,
-                 std::vector<std::vector<int32_t>>& slices) {
+void form_slices(const std::vector<Task>& tasks, const std::vector<int32_t>& order, const std::vector<int32_t>& len,
+                 bool atomics, std::vector<std::vector<int32_t>>& slices) {
   std::vector<uint8_t> taken(order.size(), 0);
   size_t head = 0;
   while (true) {
@@ -52,8 +52,11 @@ void form_slices(const std::vector<Task>& tasks, const std::vector<int32_t>& ord
     std::vector<int32_t> sl;
     uint32_t used_b = 0;
     size_t scanned = 0;
+    // candidates stay within a length band of the slice's longest task (padding stays small)
+    const int32_t band = len[order[head]] - std::max<int32_t>(1, len[order[head]] / 16);
     for (size_t i = head; i < order.size() && sl.size() < 32 && scanned < (size_t)kWindow; ++i) {
       if (taken[i]) continue;
+      if (len[order[i]] < band) break;
       ++scanned;
       const Task& t = tasks[order[i]];
       if (atomics && (t.flags & 2)) {
@@ -80,67 +83,98 @@ void form_slices(const std::vector<Task>& tasks, const std::vector<int32_t>& ord
   }
 }
 
-// Interleave the entries of one slice step by step.  At every step each lane
-// takes, among its remaining entries, one whose column falls in a shared-memory
-// bank group not yet used by the lanes of its phase (bank group = column mod
-// `bank_mod`; a phase is `phase_lanes` consecutive lanes, as in one vector
-// shared-memory load of E values per lane).  Lanes without entries left read a
-// zero coefficient at a column chosen to avoid the used groups.
+// Interleave the entries of one slice step by step.  At every step the lanes of
+// each phase (`phase_lanes` consecutive lanes, as served by one vector
+// shared-memory load of E values per lane) are matched to distinct bank groups
+// (bank group = column mod `bank_mod`) by a maximum bipartite matching between
+// lanes and the groups in which they still have entries: the most constrained
+// lanes are matched first, and a lane tries its most abundant groups first
+// (ties rotated by lane and step) so that choice remains for later steps.  A lane the matching cannot place takes
+// an entry from its most abundant group (a conflict); lanes without entries
+// left read a zero coefficient at a column in a group nobody uses.
+struct LaneBanks {
+  std::vector<std::vector<int32_t>> by_bank;  // entry indices per bank group
+  int32_t left = 0;
+};
+
+bool augment(int lane, const std::vector<LaneBanks>& lb, const std::vector<int>& lanes_in_phase,
+             std::vector<int>& bank_owner, std::vector<uint8_t>& seen, const std::vector<std::vector<int>>& pref) {
+  for (int b : pref[lane]) {
+    if (seen[b]) continue;
+    seen[b] = 1;
+    if (bank_owner[b] < 0 || augment(bank_owner[b], lb, lanes_in_phase, bank_owner, seen, pref)) {
+      bank_owner[b] = lane;
+      return true;
+    }
+  }
+  return false;
+}
+
 void interleave(const std::vector<const std::vector<Entry>*>& lane_entries, int32_t steps, int phase_lanes,
                 int bank_mod, int32_t n_slots, int64_t off, TaskSet& ts) {
   const int nl = (int)lane_entries.size();
-  std::vector<std::vector<std::vector<int32_t>>> buckets(nl, std::vector<std::vector<int32_t>>(bank_mod));
+  std::vector<LaneBanks> lb(32);
   for (int j = 0; j < nl; ++j) {
+    lb[j].by_bank.assign(bank_mod, {});
     const auto& v = *lane_entries[j];
-    for (int32_t q = (int32_t)v.size() - 1; q >= 0; --q) buckets[j][v[q].col % bank_mod].push_back(q);
+    for (int32_t q = (int32_t)v.size() - 1; q >= 0; --q) lb[j].by_bank[v[q].col % bank_mod].push_back(q);
+    lb[j].left = (int32_t)v.size();
   }
-  std::vector<int32_t> left(nl);
-  for (int j = 0; j < nl; ++j) left[j] = (int32_t)lane_entries[j]->size();
+  std::vector<std::vector<int>> pref(32);
   for (int32_t k = 0; k < steps; ++k) {
     for (int p0 = 0; p0 < 32; p0 += phase_lanes) {
+      std::vector<int> active;
+      for (int j = p0; j < p0 + phase_lanes; ++j)
+        if (j < nl && lb[j].left > 0) {
+          active.push_back(j);
+          pref[j].clear();
+          for (int b = 0; b < bank_mod; ++b)
+            if (!lb[j].by_bank[b].empty()) pref[j].push_back(b);
+          const int rot = (j + k) % bank_mod;  // ties: lane j at step k prefers group (j + k) mod n first
+          std::stable_sort(pref[j].begin(), pref[j].end(), [&](int x, int y) {
+            if (lb[j].by_bank[x].size() != lb[j].by_bank[y].size())
+              return lb[j].by_bank[x].size() > lb[j].by_bank[y].size();
+            return (x - rot + bank_mod) % bank_mod < (y - rot + bank_mod) % bank_mod;
+          });
+        }
+      std::stable_sort(active.begin(), active.end(), [&](int x, int y) { return pref[x].size() < pref[y].size(); });
+      std::vector<int> bank_owner(bank_mod, -1);
+      std::vector<uint8_t> seen(bank_mod);
+      for (int j : active) {
+        std::fill(seen.begin(), seen.end(), 0);
+        augment(j, lb, active, bank_owner, seen, pref);
+      }
+      std::vector<int> lane_bank(32, -1);
       std::vector<uint8_t> used(bank_mod, 0);
-      std::vector<int> pending;
+      for (int b = 0; b < bank_mod; ++b)
+        if (bank_owner[b] >= 0) {
+          lane_bank[bank_owner[b]] = b;
+          used[b] = 1;
+        }
       for (int j = p0; j < p0 + phase_lanes; ++j) {
         const int64_t idx = off + (int64_t)k * 32 + j;
-        if (j >= nl || left[j] == 0) {
-          pending.push_back(j);
-          continue;
-        }
-        int chosen = -1;
-        for (int b = 0; b < bank_mod; ++b) {
-          int bb = (b + j) % bank_mod;
-          if (!used[bb] && !buckets[j][bb].empty()) {
-            chosen = bb;
-            break;
-          }
-        }
-        if (chosen < 0)
-          for (int b = 0; b < bank_mod; ++b)
-            if (!buckets[j][b].empty()) {
-              chosen = b;
+        if (j < nl && lb[j].left > 0) {
+          int b = lane_bank[j];
+          if (b < 0) b = pref[j][0];  // no free group: take the most abundant one
+          const int32_t q = lb[j].by_bank[b].back();
+          lb[j].by_bank[b].pop_back();
+          --lb[j].left;
+          const Entry& e = (*lane_entries[j])[q];
+          ts.col[idx] = e.col;
+          ts.ebasis[idx] = e.basis;
+          ts.ew2[idx] = e.w2;
+        } else {  // padding: zero coefficient, in a group nobody uses if one is left
+          int32_t c = 0;
+          for (int b = 0; b < bank_mod && b < n_slots; ++b)
+            if (!used[b]) {
+              c = b;
+              used[b] = 1;
               break;
             }
-        const int32_t q = buckets[j][chosen].back();
-        buckets[j][chosen].pop_back();
-        --left[j];
-        used[chosen] = 1;
-        const Entry& e = (*lane_entries[j])[q];
-        ts.col[idx] = e.col;
-        ts.ebasis[idx] = e.basis;
-        ts.ew2[idx] = e.w2;
-      }
-      for (int j : pending) {  // padding: zero coefficient, unused bank group if any
-        const int64_t idx = off + (int64_t)k * 32 + j;
-        int32_t c = 0;
-        for (int b = 0; b < bank_mod && b < n_slots; ++b)
-          if (!used[b]) {
-            c = b;
-            used[b] = 1;
-            break;
-          }
-        ts.col[idx] = c;
-        ts.ebasis[idx] = -1;
-        ts.ew2[idx] = 0;
+          ts.col[idx] = c;
+          ts.ebasis[idx] = -1;
+          ts.ew2[idx] = 0;
+        }
       }
     }
   }
@@ -178,7 +212,9 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return protos[a].len > protos[b].len; });
   std::vector<std::vector<int32_t>> slices;
-  form_slices(tasks, order, sym, slices);
+  std::vector<int32_t> lens(protos.size());
+  for (size_t i = 0; i < protos.size(); ++i) lens[i] = protos[i].len;
+  form_slices(tasks, order, lens, sym, slices);
   const int32_t n_slices = (int32_t)slices.size();
   ts = TaskSet();
   ts.tasks.resize((size_t)n_slices * 32, Task{-1, 0, -1, -1});
