@@ -62,6 +62,7 @@ struct Task {
   int32_t row;    // slot whose sparse row this task covers (-1: padding)
   int32_t flags;  // bit0: first task of its row (adds the row's own coefficient)
                   // bit1: row is a top operand (push to its factors) else G row
+                  // bit2: the row's stored value is a basis function (has a coefficient)
   int32_t pl, pr; // factor slots of a top operand row, else -1
 };
 

@@ -40,6 +40,7 @@ struct DevTaskSet {
   int32_t* slice_off = nullptr;
   int32_t* slice_steps = nullptr;
   int32_t* col = nullptr;
+  uint16_t* col16 = nullptr;  // columns as uint16 when every slot index fits
   int32_t* ebasis = nullptr;
   uint8_t* ew2 = nullptr;
   int32_t n_slices = 0;
@@ -49,7 +50,6 @@ struct DevTaskSet {
   size_t vals_bytes = 0;
   void* lin = nullptr;
   size_t lin_bytes = 0;
-  int2* ent = nullptr;  // packed entries (FP32, one channel)
   bool bound = false;
   int bound_dtype = -1, bound_nout = -1;
 };
@@ -69,6 +69,7 @@ struct ace_dag {
   DevTaskSet sym, one;
   uint32_t* status = nullptr;
   std::vector<void*> allocations;
+  std::vector<std::vector<uint16_t>> staging16;  // host copies kept alive until the upload completes
 };
 
 namespace {
@@ -103,6 +104,10 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   if ((s = upload_vec(d, ts.slice_off, &dt.slice_off, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.slice_steps, &dt.slice_steps, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.col, &dt.col, st)) != ACE_OK) return s;
+  if (d->plan.n_slots <= 65535) {
+    d->staging16.emplace_back(ts.col.begin(), ts.col.end());
+    if ((s = upload_vec(d, d->staging16.back(), &dt.col16, st)) != ACE_OK) return s;
+  }
   if ((s = upload_vec(d, ts.ebasis, &dt.ebasis, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.ew2, &dt.ew2, st)) != ACE_OK) return s;
   dt.n_slices = ts.n_slices();
@@ -199,14 +204,8 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
     if ((e = cudaMalloc(&dt.lin, lb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     dt.lin_bytes = lb;
   }
-  if (dtype == ACE_F32 && npad == 1 && !dt.ent) {
-    void* p = nullptr;
-    if ((e = cudaMalloc(&p, std::max<size_t>((size_t)dt.n_pad * sizeof(int2), 16))) != cudaSuccess)
-      return cuda_fail(e, "cudaMalloc");
-    dt.ent = static_cast<int2*>(p);
-  }
   e = launch_bind(dtype, c, n_out, npad, dt.ebasis, dt.ew2, dt.n_pad, dt.vals, d->slot_basis, d->plan.n_slots,
-                  dt.lin, dt.col, dt.ent, st);
+                  dt.lin, st);
   if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
   dt.bound = true;
   dt.bound_dtype = dtype;
@@ -263,6 +262,7 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
   DevTaskSet& dt = grad ? d->sym : d->one;
   ace_status s = bind(d, dt, c, n_out, dtype, st);
   if (s != ACE_OK) return s;
+  if (!dt.col16) return fail(ACE_ERR_UNSUPPORTED, "more than 65535 stored values per environment");
   const int npad = nout_pad_of(n_out);
   int E = 0, nt = 0;
   size_t smem = 0;
@@ -308,8 +308,7 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     a.slice_off = dt.slice_off;
     a.slice_steps = dt.slice_steps;
     a.n_slices = dt.n_slices;
-    a.col = dt.col;
-    a.ent = dt.ent;
+    a.col16 = dt.col16;
     a.gs = dev::g_stride(p.n_g);
     a.vals = static_cast<const TT*>(dt.vals);
     a.lin = static_cast<const TT*>(dt.lin);
@@ -505,7 +504,6 @@ void ace_dag_free(ace_dag* dag) {
     for (DevTaskSet* t : {&dag->sym, &dag->one}) {
       if (t->vals) cudaFree(t->vals);
       if (t->lin) cudaFree(t->lin);
-      if (t->ent) cudaFree(t->ent);
     }
     cudaSetDevice(cur);
   }

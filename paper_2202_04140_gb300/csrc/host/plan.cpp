@@ -201,7 +201,7 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
       const int32_t b = (int32_t)((int64_t)n * p / pieces), e = (int32_t)((int64_t)n * (p + 1) / pieces);
       Task t;
       t.row = s;
-      t.flags = (p == 0 ? 1 : 0) | (top ? 2 : 0);
+      t.flags = (p == 0 ? 1 : 0) | (top ? 2 : 0) | (lin ? 4 : 0);
       t.pl = top ? slot_l[s] : -1;
       t.pr = top ? slot_r[s] : -1;
       tasks.push_back(t);

@@ -11,13 +11,10 @@ namespace dev {
 // vals[e][ch] = w(e) * c[basis(e)][ch] (w = 2 on the diagonal of the symmetric
 // sink form), 0 for padding entries and for ch >= n_out; lin[s][ch] likewise for
 // the stored value of slot s.
-// With `ent` (FP32, one channel) the coefficient is also packed next to its
-// column as one 8-byte {column, coefficient bits} entry.
 template <typename T>
 __global__ void bind_kernel(const T* __restrict__ c, int n_out, int nout_pad, const int32_t* __restrict__ ebasis,
                             const uint8_t* __restrict__ ew2, int64_t n_entries, T* __restrict__ vals,
-                            const int32_t* __restrict__ slot_basis, int64_t n_slots, T* __restrict__ lin,
-                            const int32_t* __restrict__ col, int2* __restrict__ ent) {
+                            const int32_t* __restrict__ slot_basis, int64_t n_slots, T* __restrict__ lin) {
   const int64_t total_e = n_entries * nout_pad;
   const int64_t total = total_e + n_slots * nout_pad;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -28,7 +25,6 @@ __global__ void bind_kernel(const T* __restrict__ c, int n_out, int nout_pad, co
       T v = T(0);
       if (b >= 0 && ch < n_out) v = c[(int64_t)b * n_out + ch] * (ew2[e] ? T(2) : T(1));
       vals[i] = v;
-      if (ent) ent[e] = make_int2(col[e], __float_as_int((float)v));
     } else {
       const int64_t j = i - total_e;
       const int64_t s = j / nout_pad;
@@ -111,18 +107,16 @@ __global__ void fma_probe_kernel(int64_t iters, float* out) {
 
 cudaError_t launch_bind(int dtype, const void* c, int n_out, int nout_pad, const int32_t* ebasis, const uint8_t* ew2,
                         int64_t n_entries, void* vals, const int32_t* slot_basis, int64_t n_slots, void* lin,
-                        const int32_t* col, int2* ent, cudaStream_t st) {
+                        cudaStream_t st) {
   const int64_t total = (n_entries + n_slots) * nout_pad;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
   if (blocks < 1) blocks = 1;
   if (dtype == ACE_F32)
     dev::bind_kernel<float><<<blocks, 256, 0, st>>>((const float*)c, n_out, nout_pad, ebasis, ew2, n_entries,
-                                                    (float*)vals, slot_basis, n_slots, (float*)lin, col,
-                                                    nout_pad == 1 ? ent : nullptr);
+                                                    (float*)vals, slot_basis, n_slots, (float*)lin);
   else
     dev::bind_kernel<double><<<blocks, 256, 0, st>>>((const double*)c, n_out, nout_pad, ebasis, ew2, n_entries,
-                                                     (double*)vals, slot_basis, n_slots, (double*)lin, col,
-                                                     nullptr);
+                                                     (double*)vals, slot_basis, n_slots, (double*)lin);
   return cudaGetLastError();
 }
 

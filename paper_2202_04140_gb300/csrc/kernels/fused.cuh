@@ -54,8 +54,7 @@ struct FusedArgs {
   const int32_t* slice_off;
   const int32_t* slice_steps;
   int32_t n_slices;
-  const int32_t* col;
-  const int2* ent;  // packed {column, coefficient bits} (FP32, one channel)
+  const uint16_t* col16;    // entry columns (slot indices)
   const T* vals;  // [entries][NOUT]
   const T* lin;   // [n_slots][NOUT]
   int32_t check;
@@ -75,6 +74,7 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t
 
 __host__ __device__ inline int g_stride(int n_g) { return (n_g + 31) & ~31; }
 
+
 __host__ __device__ inline SmemLayout smem_layout(int E, int NOUT, bool grad, int n_slots, int n_g, int NT,
                                                   int tsize) {
   SmemLayout L;
@@ -86,7 +86,12 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int NOUT, bool grad, in
 }
 
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Shared-memory float addition has no native atomic instruction on this GPU
+// (atomicAdd(float*) on shared memory is a compare-and-swap loop, about a
+// quarter of the throughput of an integer atomic): the kernel keeps the number
+// of such updates low (segmented warp reduction of equal targets) and spreads
+// concurrent ones over distinct banks (environment-major accumulators).
 
 // ---- vector helpers ---------------------------------------------------------------
 
@@ -208,76 +213,85 @@ struct Acc<double, kReadPlain> : AccD<double> {};
 
 // Entries of one lane's task, software-pipelined: the (column, coefficient)
 // pairs of the next kBatch steps are loaded while the current kBatch are used.
-constexpr int kBatch = 8;
+constexpr int kBatch = 4;
+
+template <typename T, int E, int NOUT, bool CHECK>
+__device__ __forceinline__ void use_entry(const FusedArgs<T>& a, const T* __restrict__ AA, int j, const T (&v)[NOUT],
+                                          T (&acc)[E][NOUT]) {
+  if constexpr (CHECK) {
+    if ((unsigned)j >= (unsigned)a.n_slots) {
+      atomicOr(a.status, kStatusBounds);
+      j = 0;
+    }
+  }
+  T x[E];
+  load_slot<T, E>(AA + (size_t)j * E, x);
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) acc[e][c] = fma_t(v[c], x[e], acc[e][c]);
+}
+
+template <typename T, int E, int NOUT, bool CHECK, typename C>
+__device__ __forceinline__ void task_entries_impl(const FusedArgs<T>& a, const T* __restrict__ AA,
+                                                  const C* __restrict__ colp, const T* __restrict__ valp, int steps,
+                                                  T (&acc)[E][NOUT]) {
+  // colp / valp point at this lane's first entry; entry k is 32 k further on.
+  // Whole batches of kBatch entries run without per-entry guards, the loads of
+  // batch b + 1 in flight while batch b is used; the last steps % kBatch
+  // entries follow one by one.
+  const int nb = steps / kBatch;
+  if (nb > 0) {
+    int cur[kBatch];
+    T vc[kBatch][NOUT];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      cur[u] = (int)__ldg(colp + u * 32);
+      if constexpr (NOUT == 1) vc[u][0] = __ldg(valp + u * 32);
+    }
+    for (int b = 0; b < nb; ++b) {
+      int nxt[kBatch];
+      T vn[kBatch][NOUT];
+      if (b + 1 < nb) {
+        const C* cp = colp + (size_t)(b + 1) * kBatch * 32;
+        const T* vp = valp + (size_t)(b + 1) * kBatch * 32 * NOUT;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          nxt[u] = (int)__ldg(cp + u * 32);
+          if constexpr (NOUT == 1) vn[u][0] = __ldg(vp + u * 32);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        if constexpr (NOUT > 1) load_vals<T, NOUT>(valp + ((size_t)b * kBatch + u) * 32 * NOUT, vc[u]);
+        use_entry<T, E, NOUT, CHECK>(a, AA, cur[u], vc[u], acc);
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        cur[u] = nxt[u];
+        if constexpr (NOUT == 1) vc[u][0] = vn[u][0];
+      }
+    }
+  }
+  const int done = nb * kBatch;
+#pragma unroll
+  for (int u = 0; u < kBatch - 1; ++u) {
+    if (done + u < steps) {
+      const int j = (int)__ldg(colp + (size_t)(done + u) * 32);
+      T v[NOUT];
+      load_vals<T, NOUT>(valp + (size_t)(done + u) * 32 * NOUT, v);
+      use_entry<T, E, NOUT, CHECK>(a, AA, j, v, acc);
+    }
+  }
+}
 
 template <typename T, int E, int NOUT, bool CHECK>
 __device__ __forceinline__ void task_entries(const FusedArgs<T>& a, const T* __restrict__ AA, int32_t off,
                                              int steps, int lane, T (&acc)[E][NOUT]) {
-  constexpr bool kPacked = sizeof(T) == 4 && NOUT == 1;
-  if constexpr (kPacked) {
-    const int2* ep = a.ent + off + lane;
-    int2 cur[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) cur[u] = u < steps ? __ldg(ep + u * 32) : make_int2(0, 0);
-    for (int k = 0; k < steps; k += kBatch) {
-      int2 nxt[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u)
-        nxt[u] = (k + kBatch + u < steps) ? __ldg(ep + (size_t)(k + kBatch + u) * 32) : make_int2(0, 0);
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        if (k + u < steps) {
-          int j = cur[u].x;
-          if constexpr (CHECK) {
-            if ((unsigned)j >= (unsigned)a.n_slots) {
-              atomicOr(a.status, kStatusBounds);
-              j = 0;
-            }
-          }
-          T x[E];
-          load_slot<T, E>(AA + (size_t)j * E, x);
-          const T v = __int_as_float(cur[u].y);
-#pragma unroll
-          for (int e = 0; e < E; ++e) acc[e][0] = fma_t(v, x[e], acc[e][0]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) cur[u] = nxt[u];
-    }
-  } else {
-    const int32_t* colp = a.col + off + lane;
-    const T* valp = a.vals + ((size_t)off + lane) * NOUT;
-    int cur[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) cur[u] = u < steps ? __ldg(colp + u * 32) : 0;
-    for (int k = 0; k < steps; k += kBatch) {
-      int nxt[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) nxt[u] = (k + kBatch + u < steps) ? __ldg(colp + (size_t)(k + kBatch + u) * 32) : 0;
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        if (k + u < steps) {
-          int j = cur[u];
-          if constexpr (CHECK) {
-            if ((unsigned)j >= (unsigned)a.n_slots) {
-              atomicOr(a.status, kStatusBounds);
-              j = 0;
-            }
-          }
-          T v[NOUT];
-          load_vals<T, NOUT>(valp + (size_t)(k + u) * 32 * NOUT, v);
-          T x[E];
-          load_slot<T, E>(AA + (size_t)j * E, x);
-#pragma unroll
-          for (int e = 0; e < E; ++e)
-#pragma unroll
-            for (int c = 0; c < NOUT; ++c) acc[e][c] = fma_t(v[c], x[e], acc[e][c]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) cur[u] = nxt[u];
-    }
-  }
+  // 16-bit columns: a graph whose stored values per environment exceed 65535
+  // could not hold one environment in shared memory anyway.
+  const T* valp = a.vals + ((size_t)off + lane) * NOUT;
+  task_entries_impl<T, E, NOUT, CHECK>(a, AA, a.col16 + off + lane, valp, steps, acc);
 }
 
 template <typename T, int E, int NOUT, bool GRAD, int RO, int NT, bool CHECK>
@@ -312,9 +326,20 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
     T lin[NOUT];
 #pragma unroll
     for (int c = 0; c < NOUT; ++c) lin[c] = T(0);
-    if (valid && (task.y & 1)) load_vals<T, NOUT>(a.lin + (size_t)row * NOUT, lin);
-    T ap[E];
-    load_slot<T, E>(AA + (size_t)row * E, ap);
+    if (valid && (task.y & 5) == 5) load_vals<T, NOUT>(a.lin + (size_t)row * NOUT, lin);
+    // factors of a top operand (adjoint form); AA of the row is their product
+    const int pl = (GRAD && valid && top) ? task.z : 0, pr = (GRAD && valid && top) ? task.w : 0;
+    T xl[E], xr[E], ap[E];
+    if (GRAD && top) {
+      load_slot<T, E>(AA + (size_t)pl * E, xl);
+      load_slot<T, E>(AA + (size_t)pr * E, xr);
+#pragma unroll
+      for (int e = 0; e < E; ++e) ap[e] = xl[e] * xr[e];
+    } else {
+      load_slot<T, E>(AA + (size_t)row * E, ap);
+#pragma unroll
+      for (int e = 0; e < E; ++e) xl[e] = xr[e] = T(0);
+    }
     const T half = GRAD ? T(0.5) : T(1);
     if (valid) {
 #pragma unroll
@@ -332,10 +357,6 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
         for (int c = 0; c < NOUT; ++c) s = fma_t(pb[e * NOUT + c], acc[e][c] + lin[c], s);
         g[e] = valid ? s : T(0);
       }
-      const int pl = (valid && top) ? task.z : 0, pr = (valid && top) ? task.w : 0;
-      T xl[E], xr[E];
-      load_slot<T, E>(AA + (size_t)pl * E, xl);
-      load_slot<T, E>(AA + (size_t)pr * E, xr);
       // "A" target: the row itself, or the first factor of a top operand.  Lanes
       // are ordered by A target, so equal targets form runs; a segmented suffix
       // sum leaves each run's total in its first lane, which does one atomic.

@@ -15,7 +15,7 @@ const void* fused_kernel_ptr(int dtype, int E, int nout, bool grad, int readout,
 
 cudaError_t launch_bind(int dtype, const void* c, int n_out, int nout_pad, const int32_t* ebasis, const uint8_t* ew2,
                         int64_t n_entries, void* vals, const int32_t* slot_basis, int64_t n_slots, void* lin,
-                        const int32_t* col, int2* ent, cudaStream_t st);
+                        cudaStream_t st);
 
 cudaError_t launch_plain_f64(const double* A, const double* c, const double* phibar, int64_t n_env, int n_out, int K,
                              int64_t n_nodes, const int32_t* left, const int32_t* right, const int32_t* node_basis,
