@@ -143,7 +143,8 @@ ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_si
  * one of: "slot_node", "slot_basis", "n_g", "fwd_slot", "fwd_l", "fwd_r",
  * "fwd_off", "rev_slot", "rev_l", "rev_r", "rev_off", and for the symmetric
  * ("sym_") and one-sided ("one_") sink forms: "tasks" (4 int32 per task: row,
- * flags, factor slots), "slice_off", "slice_steps", "col", "ebasis", "ew2".
+ * flags, factor slots), "slice_off", "slice_steps", "col", "ebasis", "ew2", and
+ * their row-major copies "rm_tasks", "rm_off", "rm_col", "rm_ebasis", "rm_ew2".
  * Every array is exported as int32.  *count receives the number of int32
  * values; out (host) may be NULL to query the size.  Errors: INVALID_ARG for an
  * unknown name. */

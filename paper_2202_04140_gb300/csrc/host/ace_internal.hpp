@@ -76,6 +76,13 @@ struct TaskSet {
   std::vector<int32_t> ebasis;        // [n_entries_padded] basis index (-1 padding)
   std::vector<uint8_t> ew2;           // [n_entries_padded] 1: weight 2 (diagonal of the symmetric form)
   int64_t n_entries = 0;              // real (unpadded) entries
+  // The same tasks with their entries contiguous (for the kernel in which a
+  // whole warp works on one task, one environment per lane); every task's
+  // entry count is padded to an even number (entries are read in pairs).
+  std::vector<Task> rm_tasks;         // [n_rm] in slice order, padding tasks dropped
+  std::vector<int32_t> rm_off;        // [n_rm + 1]
+  std::vector<int32_t> rm_col, rm_ebasis;
+  std::vector<uint8_t> rm_ew2;
   int32_t n_slices() const { return (int32_t)slice_steps.size(); }
 };
 

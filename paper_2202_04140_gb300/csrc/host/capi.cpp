@@ -45,6 +45,16 @@ struct DevTaskSet {
   uint8_t* ew2 = nullptr;
   int32_t n_slices = 0;
   int64_t n_pad = 0;
+  // row-major copy of the tasks (one-environment-per-lane kernel)
+  int4* rm_tasks = nullptr;
+  int32_t* rm_off = nullptr;
+  int32_t* rm_col = nullptr;
+  int32_t* rm_ebasis = nullptr;
+  uint8_t* rm_ew2 = nullptr;
+  int32_t n_rm = 0;
+  int64_t n_rm_ent = 0;
+  int2* rm_ent = nullptr;     // bound {column, coefficient} entries (FP32, one channel)
+  bool rm_bound = false;
   // coefficients bound into this task set
   void* vals = nullptr;
   size_t vals_bytes = 0;
@@ -70,6 +80,7 @@ struct ace_dag {
   uint32_t* status = nullptr;
   std::vector<void*> allocations;
   std::vector<std::vector<uint16_t>> staging16;  // host copies kept alive until the upload completes
+  std::vector<std::vector<int4>> staging_int4;
 };
 
 namespace {
@@ -99,8 +110,9 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   std::vector<int4> t4(ts.tasks.size());
   for (size_t i = 0; i < ts.tasks.size(); ++i)
     t4[i] = make_int4(ts.tasks[i].row, ts.tasks[i].flags, ts.tasks[i].pl, ts.tasks[i].pr);
+  d->staging_int4.push_back(std::move(t4));
   ace_status s;
-  if ((s = upload_vec(d, t4, &dt.tasks, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, d->staging_int4.back(), &dt.tasks, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.slice_off, &dt.slice_off, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.slice_steps, &dt.slice_steps, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.col, &dt.col, st)) != ACE_OK) return s;
@@ -112,6 +124,17 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   if ((s = upload_vec(d, ts.ew2, &dt.ew2, st)) != ACE_OK) return s;
   dt.n_slices = ts.n_slices();
   dt.n_pad = (int64_t)ts.col.size();
+  std::vector<int4> r4(ts.rm_tasks.size());
+  for (size_t i = 0; i < ts.rm_tasks.size(); ++i)
+    r4[i] = make_int4(ts.rm_tasks[i].row, ts.rm_tasks[i].flags, ts.rm_tasks[i].pl, ts.rm_tasks[i].pr);
+  d->staging_int4.push_back(std::move(r4));
+  if ((s = upload_vec(d, d->staging_int4.back(), &dt.rm_tasks, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.rm_off, &dt.rm_off, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.rm_col, &dt.rm_col, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.rm_ebasis, &dt.rm_ebasis, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.rm_ew2, &dt.rm_ew2, st)) != ACE_OK) return s;
+  dt.n_rm = (int32_t)ts.rm_tasks.size();
+  dt.n_rm_ent = (int64_t)ts.rm_col.size();
   return ACE_OK;
 }
 
@@ -134,6 +157,19 @@ ace_status validate_plan(const Plan& p) {
         return fail(ACE_ERR_BOUNDS, "plan: task factor out of range");
       if (ts == &p.sym && !(t.flags & 2) && !in(t.row, p.n_g))
         return fail(ACE_ERR_BOUNDS, "plan: adjoint row out of range");
+    }
+    for (int32_t c : ts->rm_col)
+      if (!in(c, p.n_slots)) return fail(ACE_ERR_BOUNDS, "plan: row-major entry column out of range");
+    if (ts->rm_off.size() != ts->rm_tasks.size() + 1 || ts->rm_off.back() != (int32_t)ts->rm_col.size())
+      return fail(ACE_ERR_BOUNDS, "plan: row-major offsets inconsistent");
+    for (size_t i = 0; i < ts->rm_tasks.size(); ++i) {
+      const Task& t = ts->rm_tasks[i];
+      if ((ts->rm_off[i] & 1) || ts->rm_off[i + 1] < ts->rm_off[i]) return fail(ACE_ERR_BOUNDS, "plan: odd offset");
+      if (!in(t.row, p.n_slots)) return fail(ACE_ERR_BOUNDS, "plan: row-major task row out of range");
+      if ((t.flags & 2) && (!in(t.pl, p.n_g) || !in(t.pr, p.n_g)))
+        return fail(ACE_ERR_BOUNDS, "plan: row-major task factor out of range");
+      if (ts == &p.sym && !(t.flags & 2) && !in(t.row, p.n_g))
+        return fail(ACE_ERR_BOUNDS, "plan: row-major adjoint row out of range");
     }
   }
   return ACE_OK;
@@ -207,6 +243,18 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
   e = launch_bind(dtype, c, n_out, npad, dt.ebasis, dt.ew2, dt.n_pad, dt.vals, d->slot_basis, d->plan.n_slots,
                   dt.lin, st);
   if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
+  dt.rm_bound = false;
+  if (dtype == ACE_F32 && n_out == 1) {
+    if (!dt.rm_ent) {
+      void* p = nullptr;
+      if ((e = cudaMalloc(&p, std::max<size_t>((size_t)dt.n_rm_ent * sizeof(int2), 16))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc");
+      dt.rm_ent = static_cast<int2*>(p);
+    }
+    e = launch_bind_rm(static_cast<const float*>(c), dt.rm_col, dt.rm_ebasis, dt.rm_ew2, dt.n_rm_ent, dt.rm_ent, st);
+    if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
+    dt.rm_bound = true;
+  }
   dt.bound = true;
   dt.bound_dtype = dtype;
   dt.bound_nout = n_out;
@@ -257,11 +305,74 @@ ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t
               "kernel)");
 }
 
+// Which fused kernel: ACE_KERNEL=lon|loe forces one (tests), otherwise the
+// one-environment-per-lane kernel whenever 32 environments fit in shared memory.
+int kernel_choice() {
+  const char* v = std::getenv("ACE_KERNEL");
+  if (v && std::strcmp(v, "lon") == 0) return 1;
+  if (v && std::strcmp(v, "loe") == 0) return 2;
+  return 0;
+}
+
+ace_status run_loe(ace_dag* d, DevTaskSet& dt, const void* A, const void* phibar, int64_t n_env, int readout,
+                   void* phi, void* dA, bool grad, cudaStream_t st) {
+  int nt = 0;
+  const void* k = loe_kernel_ptr(grad, readout, &nt);
+  if (!k) return fail(ACE_ERR_UNSUPPORTED, "no kernel for this readout mode");
+  const size_t smem = loe_smem(d->plan.n_slots, d->plan.n_g, grad, nt);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  int bps = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, nt, smem)) != cudaSuccess)
+    return cuda_fail(e, "occupancy query");
+  if (bps < 1) return fail(ACE_ERR_UNSUPPORTED, "one-environment-per-lane kernel cannot be resident");
+  const Plan& p = d->plan;
+  dev::LoeArgs a{};
+  a.A = static_cast<const float*>(A);
+  a.phibar = static_cast<const float*>(phibar);
+  a.phi = static_cast<float*>(phi);
+  a.dA = static_cast<float*>(dA);
+  a.n_env = n_env;
+  a.n_tiles = (n_env + 31) / 32;
+  a.K = p.K;
+  a.n_slots = p.n_slots;
+  a.n_g = p.n_g;
+  a.fwd_slot = d->fwd_slot;
+  a.fwd_l = d->fwd_l;
+  a.fwd_r = d->fwd_r;
+  a.rev_slot = d->rev_slot;
+  a.rev_l = d->rev_l;
+  a.rev_r = d->rev_r;
+  a.n_fwd_levels = (int32_t)p.fwd.off.size() - 1;
+  a.n_rev_levels = (int32_t)p.rev.off.size() - 1;
+  for (int i = 0; i <= dev::kMaxLevels; ++i) {
+    a.fwd_off[i] = i < (int)p.fwd.off.size() ? p.fwd.off[i] : 0;
+    a.rev_off[i] = i < (int)p.rev.off.size() ? p.rev.off[i] : 0;
+  }
+  a.tasks = dt.rm_tasks;
+  a.toff = dt.rm_off;
+  a.n_tasks = dt.n_rm;
+  a.ent = reinterpret_cast<const int4*>(dt.rm_ent);
+  a.lin = static_cast<const float*>(dt.lin);
+  a.check = checked_mode() ? 1 : 0;
+  a.status = d->status;
+  const int64_t grid = std::min<int64_t>(a.n_tiles, (int64_t)d->sm_count * bps);
+  void* args[] = {&a};
+  e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(nt), args, smem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  return ACE_OK;
+}
+
 ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phibar, int64_t n_env, int n_out,
                      int dtype, int readout, void* phi, void* dA, bool grad, cudaStream_t st) {
   DevTaskSet& dt = grad ? d->sym : d->one;
   ace_status s = bind(d, dt, c, n_out, dtype, st);
   if (s != ACE_OK) return s;
+  const int choice = kernel_choice();
+  const bool loe_ok = dtype == ACE_F32 && n_out == 1 && dt.rm_bound &&
+                      loe_smem(d->plan.n_slots, d->plan.n_g, grad, 1024) <= (size_t)d->smem_optin;
+  if (choice == 2 && !loe_ok) return fail(ACE_ERR_UNSUPPORTED, "ACE_KERNEL=loe: graph or request does not fit");
+  if (loe_ok && choice != 1) return run_loe(d, dt, A, phibar, n_env, readout, phi, dA, grad, st);
   if (!dt.col16) return fail(ACE_ERR_UNSUPPORTED, "more than 65535 stored values per environment");
   const int npad = nout_pad_of(n_out);
   int E = 0, nt = 0;
@@ -467,6 +578,15 @@ ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out
     else if (field == "ew2") {
       tmp.assign(ts.ew2.begin(), ts.ew2.end());
       v = &tmp;
+    } else if (field == "rm_tasks") {
+      for (const Task& t : ts.rm_tasks) tmp.insert(tmp.end(), {t.row, t.flags, t.pl, t.pr});
+      v = &tmp;
+    } else if (field == "rm_off") v = &ts.rm_off;
+    else if (field == "rm_col") v = &ts.rm_col;
+    else if (field == "rm_ebasis") v = &ts.rm_ebasis;
+    else if (field == "rm_ew2") {
+      tmp.assign(ts.rm_ew2.begin(), ts.rm_ew2.end());
+      v = &tmp;
     } else return false;
     return true;
   };
@@ -504,6 +624,7 @@ void ace_dag_free(ace_dag* dag) {
     for (DevTaskSet* t : {&dag->sym, &dag->one}) {
       if (t->vals) cudaFree(t->vals);
       if (t->lin) cudaFree(t->lin);
+      if (t->rm_ent) cudaFree(t->rm_ent);
     }
     cudaSetDevice(cur);
   }

@@ -246,6 +246,24 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
     }
     interleave(lanes, ts.slice_steps[s], 16, 16, n_slots, ts.slice_off[s], ts);
   }
+  // row-major copy (same tasks, same order)
+  ts.rm_off.push_back(0);
+  for (int32_t s = 0; s < n_slices; ++s)
+    for (int32_t ti : slices[s]) {
+      ts.rm_tasks.push_back(tasks[ti]);
+      const auto& r = rows[tasks[ti].row];
+      for (int32_t q = protos[ti].begin; q < protos[ti].begin + protos[ti].len; ++q) {
+        ts.rm_col.push_back(r[q].col);
+        ts.rm_ebasis.push_back(r[q].basis);
+        ts.rm_ew2.push_back(r[q].w2);
+      }
+      if (protos[ti].len % 2) {
+        ts.rm_col.push_back(0);
+        ts.rm_ebasis.push_back(-1);
+        ts.rm_ew2.push_back(0);
+      }
+      ts.rm_off.push_back((int32_t)ts.rm_col.size());
+    }
 }
 
 }  // namespace

@@ -61,6 +61,32 @@ struct FusedArgs {
   uint32_t* status;
 };
 
+// Arguments of the one-environment-per-lane variant (loe.cu).
+struct LoeArgs {
+  const float* A;
+  const float* phibar;
+  float* phi;
+  float* dA;
+  int64_t n_env, n_tiles;
+  int32_t K, n_slots, n_g;
+  const int32_t* fwd_slot;
+  const int32_t* fwd_l;
+  const int32_t* fwd_r;
+  const int32_t* rev_slot;
+  const int32_t* rev_l;
+  const int32_t* rev_r;
+  int32_t fwd_off[kMaxLevels + 1];
+  int32_t rev_off[kMaxLevels + 1];
+  int32_t n_fwd_levels, n_rev_levels;
+  const int4* tasks;
+  const int32_t* toff;
+  int32_t n_tasks;
+  const int4* ent;  // entry pairs {col0, coef0 bits, col1, coef1 bits}
+  const float* lin;
+  int32_t check;
+  uint32_t* status;
+};
+
 // Byte offsets of the shared-memory regions of one CTA (each 16-byte aligned):
 // AA [n_slots][E] (slot-major: the E values of one slot are one vector load),
 // G [E][gs] (adjoint only, environment-major: the bank of an accumulator is
@@ -85,7 +111,14 @@ __host__ __device__ inline SmemLayout smem_layout(int E, int NOUT, bool grad, in
   return L;
 }
 
-__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// Fused multiply-add in the arithmetic type T (no implicit conversions: a call
+// with mixed types does not compile).
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "fma_t: float or double");
+  if constexpr (sizeof(T) == 4) return __fmaf_rn(a, b, c);
+  else return __fma_rn(a, b, c);
+}
 
 // Shared-memory float addition has no native atomic instruction on this GPU
 // (atomicAdd(float*) on shared memory is a compare-and-swap loop, about a

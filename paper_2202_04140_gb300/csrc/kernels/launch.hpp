@@ -13,6 +13,12 @@ namespace ace {
 // nullptr when that combination is not compiled; *nt receives its block size.
 const void* fused_kernel_ptr(int dtype, int E, int nout, bool grad, int readout, int* nt);
 
+// One-environment-per-lane variant (loe.cu): kernel, shared memory, entry binding.
+const void* loe_kernel_ptr(bool grad, int readout, int* nt);
+size_t loe_smem(int n_slots, int n_g, bool grad, int nt);
+cudaError_t launch_bind_rm(const float* c, const int32_t* col, const int32_t* ebasis, const uint8_t* ew2, int64_t n,
+                           int2* ent, cudaStream_t st);
+
 cudaError_t launch_bind(int dtype, const void* c, int n_out, int nout_pad, const int32_t* ebasis, const uint8_t* ew2,
                         int64_t n_entries, void* vals, const int32_t* slot_basis, int64_t n_slots, void* lin,
                         cudaStream_t st);

@@ -1,0 +1,188 @@
+// Fused forward + adjoint for small graphs, one environment per lane.
+//
+// Same arithmetic as fused.cuh (section 2.6, Eq. 4; sinks folded into the
+// symmetric sink matrix, adjoint pushed back through the operand nodes), laid
+// out the other way round: a CTA holds 32 environments, lane e of every warp
+// owns environment e, and a whole warp works on one task at a time.  The
+// stored values of the tile are AA[slot][e] with a row stride of 33 floats, so
+// that a warp reading slot j touches 32 consecutive banks (no conflicts) and
+// the transposed copies of A in and dA out hit distinct banks too.  Entries
+// {column, coefficient} are read two at a time with one warp-uniform 16-byte
+// load (a broadcast), so metadata costs half a shared-memory-pipe wavefront per
+// entry and 32 environments; the gather is one conflict-free wavefront.  Used
+// when 32 environments of stored values (and adjoints) fit in shared memory.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fused.cuh"
+#include "launch.hpp"
+
+namespace ace {
+namespace dev {
+
+constexpr int kLoeStride = 33;
+
+
+__host__ __device__ inline size_t loe_smem_bytes(int n_slots, int n_g, bool grad, int nt) {
+  size_t b = align16((size_t)n_slots * kLoeStride * 4);
+  if (grad) b += align16((size_t)n_g * kLoeStride * 4);
+  b += 32 * 4;
+  b += (size_t)(nt / 32) * 32 * sizeof(double);
+  return b;
+}
+
+template <bool GRAD, int RO, int NT>
+__global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NW = NT / 32;
+  constexpr int S = kLoeStride;
+  float* AA = reinterpret_cast<float*>(smem_raw);
+  float* G = reinterpret_cast<float*>(smem_raw + align16((size_t)a.n_slots * S * 4));
+  float* pb = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(G) +
+                                       (GRAD ? align16((size_t)a.n_g * S * 4) : 0));
+  double* red = reinterpret_cast<double*>(pb + 32);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K = a.K;
+  for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int64_t env0 = tile * 32;
+    const int n_here = (a.n_env - env0) < 32 ? (int)(a.n_env - env0) : 32;
+    // 1. leaves: the tile's rows of A are one contiguous block
+    for (int i = tid; i < 32 * K; i += NT) {
+      const int e = i / K, k = i - e * K;
+      AA[k * S + e] = e < n_here ? a.A[env0 * K + i] : 0.f;
+    }
+    if constexpr (GRAD) {
+      for (int i = tid; i < a.n_g * S; i += NT) G[i] = 0.f;
+      if (tid < 32) pb[tid] = tid < n_here ? (a.phibar ? a.phibar[env0 + tid] : 1.f) : 0.f;
+    }
+    __syncthreads();
+    // 2. operand nodes, order ascending (Eq. 4): one node per warp, one environment per lane
+    for (int lv = 0; lv < a.n_fwd_levels; ++lv) {
+      for (int i = a.fwd_off[lv] + warp; i < a.fwd_off[lv + 1]; i += NW) {
+        const int s = __ldg(a.fwd_slot + i), l = __ldg(a.fwd_l + i), r = __ldg(a.fwd_r + i);
+        if (a.check && ((unsigned)s >= (unsigned)a.n_slots || (unsigned)l >= (unsigned)a.n_slots ||
+                        (unsigned)r >= (unsigned)a.n_slots)) {
+          if (lane == 0) atomicOr(a.status, kStatusBounds);
+          continue;
+        }
+        AA[s * S + lane] = AA[l * S + lane] * AA[r * S + lane];
+      }
+      __syncthreads();
+    }
+    // 3. tasks: one task per warp
+    Acc<float, RO> phiacc;
+    const float half = GRAD ? 0.5f : 1.f;
+    const float pbl = GRAD ? pb[lane] : 0.f;
+    for (int t = warp; t < a.n_tasks; t += NW) {
+      const int4 task = __ldg(a.tasks + t);
+      const int q0 = __ldg(a.toff + t), q1 = __ldg(a.toff + t + 1);
+      float acc0 = 0.f, acc1 = 0.f;
+      for (int q = q0; q < q1; q += 2) {
+        const int4 p = __ldg(a.ent + (q >> 1));
+        int j0 = p.x, j1 = p.z;
+        if (a.check && ((unsigned)j0 >= (unsigned)a.n_slots || (unsigned)j1 >= (unsigned)a.n_slots)) {
+          if (lane == 0) atomicOr(a.status, kStatusBounds);
+          j0 = j1 = 0;
+        }
+        acc0 = __fmaf_rn(__int_as_float(p.y), AA[j0 * S + lane], acc0);
+        acc1 = __fmaf_rn(__int_as_float(p.w), AA[j1 * S + lane], acc1);
+      }
+      const float acc = acc0 + acc1;
+      const int row = task.x;
+      const bool top = (task.y & 2) != 0;
+      if (a.check && (unsigned)row >= (unsigned)a.n_slots) {
+        if (lane == 0) atomicOr(a.status, kStatusBounds);
+        continue;
+      }
+      const float lin = (task.y & 5) == 5 ? __ldg(a.lin + row) : 0.f;
+      float ap, xl = 0.f, xr = 0.f;
+      if (GRAD && top) {
+        xl = AA[task.z * S + lane];
+        xr = AA[task.w * S + lane];
+        ap = xl * xr;
+      } else {
+        ap = AA[row * S + lane];
+      }
+      phiacc.add(ap * __fmaf_rn(half, acc, lin));
+      if constexpr (GRAD) {
+        const float g = pbl * (acc + lin);
+        if (top) {
+          atomicAdd(G + task.z * S + lane, g * xr);
+          atomicAdd(G + task.w * S + lane, g * xl);
+        } else {
+          atomicAdd(G + row * S + lane, g);
+        }
+      }
+    }
+    __syncthreads();
+    // 4. adjoint through the inner operand nodes, order descending
+    if constexpr (GRAD) {
+      for (int lv = 0; lv < a.n_rev_levels; ++lv) {
+        for (int i = a.rev_off[lv] + warp; i < a.rev_off[lv + 1]; i += NW) {
+          const int s = __ldg(a.rev_slot + i), l = __ldg(a.rev_l + i), r = __ldg(a.rev_r + i);
+          if (a.check && ((unsigned)s >= (unsigned)a.n_g || (unsigned)l >= (unsigned)a.n_g ||
+                          (unsigned)r >= (unsigned)a.n_g)) {
+            if (lane == 0) atomicOr(a.status, kStatusBounds);
+            continue;
+          }
+          const float g = G[s * S + lane];
+          atomicAdd(G + l * S + lane, g * AA[r * S + lane]);
+          atomicAdd(G + r * S + lane, g * AA[l * S + lane]);
+        }
+        __syncthreads();
+      }
+      for (int i = tid; i < 32 * K; i += NT) {
+        const int e = i / K, k = i - e * K;
+        if (e < n_here) a.dA[env0 * K + i] = G[k * S + e];
+      }
+    }
+    // 5. phi: per-lane partials of every warp, summed in FP64 in warp order
+    red[warp * 32 + lane] = phiacc.value();
+    __syncthreads();
+    if (tid < 32 && tid < n_here && a.phi) {
+      double s = 0.0;
+      for (int w = 0; w < NW; ++w) s += red[w * 32 + tid];
+      a.phi[env0 + tid] = (float)s;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace dev
+
+const void* loe_kernel_ptr(bool grad, int readout, int* nt) {
+  *nt = 1024;
+  using namespace dev;
+  if (grad) {
+    if (readout == 0) return (const void*)&loe_kernel<true, 0, 1024>;
+    if (readout == 1) return (const void*)&loe_kernel<true, 1, 1024>;
+    if (readout == 2) return (const void*)&loe_kernel<true, 2, 1024>;
+  } else {
+    if (readout == 0) return (const void*)&loe_kernel<false, 0, 1024>;
+    if (readout == 1) return (const void*)&loe_kernel<false, 1, 1024>;
+    if (readout == 2) return (const void*)&loe_kernel<false, 2, 1024>;
+  }
+  return nullptr;
+}
+
+size_t loe_smem(int n_slots, int n_g, bool grad, int nt) { return dev::loe_smem_bytes(n_slots, n_g, grad, nt); }
+
+__global__ void bind_rm_kernel(const float* __restrict__ c, const int32_t* __restrict__ col,
+                               const int32_t* __restrict__ ebasis, const uint8_t* __restrict__ ew2, int64_t n,
+                               int2* __restrict__ ent) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = ebasis[i];
+    const float v = b >= 0 ? c[b] * (ew2[i] ? 2.f : 1.f) : 0.f;
+    ent[i] = make_int2(col[i], __float_as_int(v));
+  }
+}
+
+cudaError_t launch_bind_rm(const float* c, const int32_t* col, const int32_t* ebasis, const uint8_t* ew2, int64_t n,
+                           int2* ent, cudaStream_t st) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  if (blocks < 1) blocks = 1;
+  bind_rm_kernel<<<blocks, 256, 0, st>>>(c, col, ebasis, ew2, n, ent);
+  return cudaGetLastError();
+}
+
+}  // namespace ace

@@ -190,6 +190,71 @@ def test_plan_emulation_matches_oracle(name, n_out, rule):
     assert normalized_error(dA, gref, gscale) < 1e-12
 
 
+def emulate_row_major(dag, mode, A, c, phibar=None):
+    """The one-environment-per-lane kernel's arithmetic on the row-major task copy (one channel)."""
+    P = plan_arrays(dag, mode)
+    R = {k: L.ace_dag_plan_array(dag.handle, f"{mode}_rm_{k}") for k in ["tasks", "off", "col", "ebasis", "ew2"]}
+    T = R["tasks"].reshape(-1, 4)
+    n_env, K = A.shape
+    n_g = int(P["n_g"][0])
+    c = c.reshape(-1)
+    AA = np.zeros((n_env, len(P["slot_node"])))
+    AA[:, :K] = A
+    off = P["fwd_off"]
+    for lv in range(len(off) - 1):
+        s = slice(off[lv], off[lv + 1])
+        AA[:, P["fwd_slot"][s]] = AA[:, P["fwd_l"][s]] * AA[:, P["fwd_r"][s]]
+    eb = R["ebasis"]
+    vals = np.where(eb >= 0, c[np.maximum(eb, 0)], 0.0) * np.where(R["ew2"] > 0, 2.0, 1.0)
+    lin = np.where(P["slot_basis"] >= 0, c[np.maximum(P["slot_basis"], 0)], 0.0)
+    phi = np.zeros(n_env)
+    G = np.zeros((n_env, n_g))
+    pb = np.ones(n_env) if phibar is None else phibar.reshape(-1)
+    for t, (row, flags, pl, pr) in enumerate(T):
+        q = slice(R["off"][t], R["off"][t + 1])
+        u = AA[:, R["col"][q]] @ vals[q]
+        li = lin[row] if (flags & 5) == 5 else 0.0
+        top = (flags & 2) > 0 and mode == "sym"
+        ap = AA[:, pl] * AA[:, pr] if top else AA[:, row]
+        phi += ap * (li + (0.5 if mode == "sym" else 1.0) * u)
+        if mode == "sym":
+            g = pb * (u + li)
+            if top:
+                G[:, pl] += g * AA[:, pr]
+                G[:, pr] += g * AA[:, pl]
+            else:
+                G[:, row] += g
+    if mode == "one":
+        return phi, None
+    off = P["rev_off"]
+    for lv in range(len(off) - 1):
+        for i in range(off[lv], off[lv + 1]):
+            s_, l_, r_ = P["rev_slot"][i], P["rev_l"][i], P["rev_r"][i]
+            gs = G[:, s_].copy()
+            G[:, l_] += gs * AA[:, r_]
+            G[:, r_] += gs * AA[:, l_]
+    return phi, G[:, :K]
+
+
+@pytest.mark.parametrize("name", ["plain_fp64_k64", "fwd_grad_k392"])
+def test_row_major_plan_emulation_matches_oracle(name):
+    w = W.WORKLOADS[name]
+    o = workload_index_set(w)
+    s = Spec.from_workload(w)
+    dag = Dag(s)
+    A = W.draw_A(3, s.K)
+    c = W.draw_c(o.deg, 1)
+    pb = np.random.default_rng(3).standard_normal((3, 1))
+    ref = phi_naive(A, o, c)
+    for mode in ["one", "sym"]:
+        phi, _ = emulate_row_major(dag, mode, A, c, pb)
+        assert normalized_error(phi[:, None], ref, error_scale(A, o, c)) < 1e-12
+    _, dA = emulate_row_major(dag, "sym", A, c, pb)
+    assert normalized_error(dA, grad_naive(A, o, c, pb), grad_error_scale(A, o, c, pb)) < 1e-12
+    R = L.ace_dag_plan_array(dag.handle, "sym_rm_off")
+    assert np.all(R % 2 == 0)
+
+
 def test_plan_emulation_stress_sample():
     """Largest workload (K = 810, nu <= 6): plan arithmetic against the oracle on 2 environments."""
     w = W.WORKLOADS["stress_k810"]
