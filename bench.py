@@ -64,6 +64,32 @@ def algorithmic_ops(w, n_nodes_ge2: int, n_basis: int, mode: str) -> float:
     return float(fwd + (adj if mode != "forward" else 0))
 
 
+# ---- ranks ----------------------------------------------------------------------------------
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """Largest value over all ranks (the timed region's duration is the slowest rank's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def min_over_ranks(x: float, dist=None, device=None) -> float:
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return float(t.item())
+
+
+def weak_scaling_value(n_env_per_rank: int, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job throughput: every rank processes its own batch of n_env_per_rank environments per step."""
+    return world * n_env_per_rank * steps / (max_ms / 1e3)
+
+
 # ---- clocks ---------------------------------------------------------------------------------
 
 class ClockSampler:
@@ -275,13 +301,9 @@ def main():
             step(i)
         ev1.record(st)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_step = ms / args.steps
-    value = world * w.n_env * args.steps / (ms / 1e3)
+    value = weak_scaling_value(w.n_env, args.steps, ms, world)
 
     # dominant kernel: the fused forward+adjoint kernel, timed alone on the same stream
     if w.pooling:
@@ -357,10 +379,7 @@ def main():
         e_ms = ev0.elapsed_time(ev1)
         e2e = {"value": w.n_env * n_e2e / (e_ms / 1e3), "unit": "env/s", "h2d_bytes_per_step": step.in_bytes,
                "d2h_bytes_per_step": step.out_bytes, "steps": n_e2e}
-    if world > 1:
-        tt = torch.tensor([e2e["value"]], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MIN)
-        e2e["value"] = float(tt.item()) * world
+    e2e["value"] = min_over_ranks(e2e["value"], dist, dev) * world
 
     extra = {}
     if rank == 0 and not args.no_baselines and not w.pooling:

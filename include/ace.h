@@ -234,12 +234,12 @@ ace_status ace_eval_plain_f64_static(ace_dag* dag, const double* A, const double
 ace_status ace_pool_A(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs,
                       float rc, int32_t nmin, int32_t nmax, int32_t lmax, float* A, void* stream);
 
-/* Adjoint of ace_pool_A: dpos[j] = sum_k dA[e(j)][k] grad_{r_j} (R_n Y_lm)(r_j).
- * Forces are F_j = -dpos[j] when dA = dphi/dA.
+/* Adjoint of ace_pool_A: dpos[j] = alpha * sum_k dA[e(j)][k] grad_{r_j} (R_n Y_lm)(r_j).
+ * With dA = dphi/dA and alpha = -1 this writes the forces F_j = -dphi/dr_j.
  *  dA   : dev float [n_env][K];  dpos : dev float [n_pairs][3], written. */
 ace_status ace_pool_A_grad(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs,
                            float rc, int32_t nmin, int32_t nmax, int32_t lmax, const float* dA,
-                           float* dpos, void* stream);
+                           float alpha, float* dpos, void* stream);
 
 /* ---- status / utilities --------------------------------------------------------- */
 

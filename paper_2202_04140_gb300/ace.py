@@ -75,7 +75,7 @@ _SIG = {
     "ace_eval_plain_f64": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _p, _p, _p, _sz, _p]),
     "ace_eval_plain_f64_static": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _p, _p, _p]),
     "ace_pool_A": (C.c_int, [_p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _p, _p]),
-    "ace_pool_A_grad": (C.c_int, [_p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _p, _p, _p]),
+    "ace_pool_A_grad": (C.c_int, [_p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _p, _f32, _p, _p]),
     "ace_stream_status": (C.c_int, [_p, _p]),
     "ace_device_info": (C.c_int, [_P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
     "ace_fma_peak": (C.c_int, [_i64, _P(C.c_double), _P(C.c_double), _p]),
@@ -211,8 +211,8 @@ def ace_pool_A(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, A, stream=0):
     _check(_lib.ace_pool_A(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, A, stream), "ace_pool_A")
 
 
-def ace_pool_A_grad(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, dA, dpos, stream=0):
-    _check(_lib.ace_pool_A_grad(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, dA, dpos, stream),
+def ace_pool_A_grad(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, dA, alpha, dpos, stream=0):
+    _check(_lib.ace_pool_A_grad(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, dA, alpha, dpos, stream),
            "ace_pool_A_grad")
 
 

@@ -54,6 +54,7 @@ struct DevTaskSet {
   int32_t n_rm = 0;
   int64_t n_rm_ent = 0;
   int2* rm_ent = nullptr;     // bound {column, coefficient} entries (FP32, one channel)
+  int4* rm_thdr = nullptr;    // bound per-task header {first, end, row coefficient, 0}
   bool rm_bound = false;
   // coefficients bound into this task set
   void* vals = nullptr;
@@ -250,8 +251,12 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
       if ((e = cudaMalloc(&p, std::max<size_t>((size_t)dt.n_rm_ent * sizeof(int2), 16))) != cudaSuccess)
         return cuda_fail(e, "cudaMalloc");
       dt.rm_ent = static_cast<int2*>(p);
+      if ((e = cudaMalloc(&p, std::max<size_t>((size_t)dt.n_rm * sizeof(int4), 16))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc");
+      dt.rm_thdr = static_cast<int4*>(p);
     }
-    e = launch_bind_rm(static_cast<const float*>(c), dt.rm_col, dt.rm_ebasis, dt.rm_ew2, dt.n_rm_ent, dt.rm_ent, st);
+    e = launch_bind_rm(static_cast<const float*>(c), dt.rm_col, dt.rm_ebasis, dt.rm_ew2, dt.n_rm_ent, dt.rm_ent,
+                       dt.rm_tasks, dt.rm_off, d->slot_basis, dt.n_rm, dt.rm_thdr, st);
     if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
     dt.rm_bound = true;
   }
@@ -350,10 +355,9 @@ ace_status run_loe(ace_dag* d, DevTaskSet& dt, const void* A, const void* phibar
     a.rev_off[i] = i < (int)p.rev.off.size() ? p.rev.off[i] : 0;
   }
   a.tasks = dt.rm_tasks;
-  a.toff = dt.rm_off;
+  a.thdr = dt.rm_thdr;
   a.n_tasks = dt.n_rm;
   a.ent = reinterpret_cast<const int4*>(dt.rm_ent);
-  a.lin = static_cast<const float*>(dt.lin);
   a.check = checked_mode() ? 1 : 0;
   a.status = d->status;
   const int64_t grid = std::min<int64_t>(a.n_tiles, (int64_t)d->sm_count * bps);
@@ -625,6 +629,7 @@ void ace_dag_free(ace_dag* dag) {
       if (t->vals) cudaFree(t->vals);
       if (t->lin) cudaFree(t->lin);
       if (t->rm_ent) cudaFree(t->rm_ent);
+      if (t->rm_thdr) cudaFree(t->rm_thdr);
     }
     cudaSetDevice(cur);
   }
@@ -753,12 +758,13 @@ ace_status ace_pool_A(const float* pos, const int64_t* offsets, int64_t n_env, i
 }
 
 ace_status ace_pool_A_grad(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
-                           int32_t nmin, int32_t nmax, int32_t lmax, const float* dA, float* dpos, void* stream) {
+                           int32_t nmin, int32_t nmax, int32_t lmax, const float* dA, float alpha, float* dpos,
+                           void* stream) {
   ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax);
   if (s != ACE_OK) return s;
   if (n_env == 0) return ACE_OK;
   if (!dA || (!dpos && n_pairs > 0)) return fail(ACE_ERR_INVALID_ARG, "dA or dpos is NULL");
-  cudaError_t e = launch_pool_grad(pos, offsets, n_env, rc, nmin, nmax, lmax, dA, dpos, (cudaStream_t)stream);
+  cudaError_t e = launch_pool_grad(pos, offsets, n_env, rc, nmin, nmax, lmax, dA, alpha, dpos, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "pooling adjoint launch");
   return ACE_OK;
 }

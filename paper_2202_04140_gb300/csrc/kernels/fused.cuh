@@ -78,11 +78,10 @@ struct LoeArgs {
   int32_t fwd_off[kMaxLevels + 1];
   int32_t rev_off[kMaxLevels + 1];
   int32_t n_fwd_levels, n_rev_levels;
-  const int4* tasks;
-  const int32_t* toff;
+  const int4* tasks;  // {row, flags, factor slots}
+  const int4* thdr;   // {first entry, end entry, row coefficient bits (first task only), 0}
   int32_t n_tasks;
-  const int4* ent;  // entry pairs {col0, coef0 bits, col1, coef1 bits}
-  const float* lin;
+  const int4* ent;    // entry pairs {col0, coef0 bits, col1, coef1 bits}
   int32_t check;
   uint32_t* status;
 };

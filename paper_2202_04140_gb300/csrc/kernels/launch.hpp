@@ -17,7 +17,8 @@ const void* fused_kernel_ptr(int dtype, int E, int nout, bool grad, int readout,
 const void* loe_kernel_ptr(bool grad, int readout, int* nt);
 size_t loe_smem(int n_slots, int n_g, bool grad, int nt);
 cudaError_t launch_bind_rm(const float* c, const int32_t* col, const int32_t* ebasis, const uint8_t* ew2, int64_t n,
-                           int2* ent, cudaStream_t st);
+                           int2* ent, const int4* tasks, const int32_t* toff, const int32_t* slot_basis,
+                           int32_t n_tasks, int4* thdr, cudaStream_t st);
 
 cudaError_t launch_bind(int dtype, const void* c, int n_out, int nout_pad, const int32_t* ebasis, const uint8_t* ew2,
                         int64_t n_entries, void* vals, const int32_t* slot_basis, int64_t n_slots, void* lin,
@@ -37,6 +38,6 @@ cudaError_t launch_pool(const float* pos, const int64_t* offsets, int64_t n_env,
                         int lmax, float* A, cudaStream_t st);
 
 cudaError_t launch_pool_grad(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
-                             int lmax, const float* dA, float* dpos, cudaStream_t st);
+                             int lmax, const float* dA, float alpha, float* dpos, cudaStream_t st);
 
 }  // namespace ace

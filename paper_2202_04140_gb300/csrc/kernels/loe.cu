@@ -21,6 +21,8 @@ namespace ace {
 namespace dev {
 
 constexpr int kLoeStride = 33;
+constexpr int kPairBatch = 4;  // entry pairs loaded together per warp
+constexpr int kNodeBatch = 4;  // operand nodes whose indices are loaded together per warp
 
 
 __host__ __device__ inline size_t loe_smem_bytes(int n_slots, int n_g, bool grad, int nt) {
@@ -47,9 +49,9 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
     const int64_t env0 = tile * 32;
     const int n_here = (a.n_env - env0) < 32 ? (int)(a.n_env - env0) : 32;
     // 1. leaves: the tile's rows of A are one contiguous block
-    for (int i = tid; i < 32 * K; i += NT) {
-      const int e = i / K, k = i - e * K;
-      AA[k * S + e] = e < n_here ? a.A[env0 * K + i] : 0.f;
+    for (int e = warp; e < 32; e += NW) {
+      const float* row = a.A + (env0 + e) * K;
+      for (int k = lane; k < K; k += 32) AA[k * S + e] = e < n_here ? row[k] : 0.f;
     }
     if constexpr (GRAD) {
       for (int i = tid; i < a.n_g * S; i += NT) G[i] = 0.f;
@@ -58,14 +60,26 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
     __syncthreads();
     // 2. operand nodes, order ascending (Eq. 4): one node per warp, one environment per lane
     for (int lv = 0; lv < a.n_fwd_levels; ++lv) {
-      for (int i = a.fwd_off[lv] + warp; i < a.fwd_off[lv + 1]; i += NW) {
-        const int s = __ldg(a.fwd_slot + i), l = __ldg(a.fwd_l + i), r = __ldg(a.fwd_r + i);
-        if (a.check && ((unsigned)s >= (unsigned)a.n_slots || (unsigned)l >= (unsigned)a.n_slots ||
-                        (unsigned)r >= (unsigned)a.n_slots)) {
-          if (lane == 0) atomicOr(a.status, kStatusBounds);
-          continue;
+      // kNodeBatch nodes per warp at a time: their indices are loaded together
+      for (int i0 = a.fwd_off[lv] + warp * kNodeBatch; i0 < a.fwd_off[lv + 1]; i0 += NW * kNodeBatch) {
+        int s[kNodeBatch], l[kNodeBatch], r[kNodeBatch];
+#pragma unroll
+        for (int u = 0; u < kNodeBatch; ++u) {
+          const bool in = i0 + u < a.fwd_off[lv + 1];
+          s[u] = in ? __ldg(a.fwd_slot + i0 + u) : -1;
+          l[u] = in ? __ldg(a.fwd_l + i0 + u) : 0;
+          r[u] = in ? __ldg(a.fwd_r + i0 + u) : 0;
         }
-        AA[s * S + lane] = AA[l * S + lane] * AA[r * S + lane];
+#pragma unroll
+        for (int u = 0; u < kNodeBatch; ++u) {
+          if (s[u] < 0) continue;
+          if (a.check && ((unsigned)s[u] >= (unsigned)a.n_slots || (unsigned)l[u] >= (unsigned)a.n_slots ||
+                          (unsigned)r[u] >= (unsigned)a.n_slots)) {
+            if (lane == 0) atomicOr(a.status, kStatusBounds);
+            continue;
+          }
+          AA[s[u] * S + lane] = AA[l[u] * S + lane] * AA[r[u] * S + lane];
+        }
       }
       __syncthreads();
     }
@@ -73,67 +87,121 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
     Acc<float, RO> phiacc;
     const float half = GRAD ? 0.5f : 1.f;
     const float pbl = GRAD ? pb[lane] : 0.f;
-    for (int t = warp; t < a.n_tasks; t += NW) {
-      const int4 task = __ldg(a.tasks + t);
-      const int q0 = __ldg(a.toff + t), q1 = __ldg(a.toff + t + 1);
+    // The header of the warp's next task is loaded while the current task runs.
+    int t = warp;
+    int4 task = make_int4(-1, 0, 0, 0);
+    int q0 = 0, q1 = 0;
+    float lin = 0.f;
+    if (t < a.n_tasks) {
+      task = __ldg(a.tasks + t);
+      const int4 h = __ldg(a.thdr + t);
+      q0 = h.x;
+      q1 = h.y;
+      lin = __int_as_float(h.z);
+    }
+    while (t < a.n_tasks) {
+      const int tn = t + NW;
+      int4 task_n = make_int4(-1, 0, 0, 0);
+      int q0n = 0, q1n = 0;
+      float lin_n = 0.f;
+      if (tn < a.n_tasks) {
+        task_n = __ldg(a.tasks + tn);
+        const int4 h = __ldg(a.thdr + tn);
+        q0n = h.x;
+        q1n = h.y;
+        lin_n = __int_as_float(h.z);
+      }
+      // entry pairs in batches of kPairBatch, the next batch loading while this one is used
+      const int4* ep = a.ent + (q0 >> 1);
+      const int np = (q1 - q0) >> 1;
       float acc0 = 0.f, acc1 = 0.f;
-      for (int q = q0; q < q1; q += 2) {
-        const int4 p = __ldg(a.ent + (q >> 1));
-        int j0 = p.x, j1 = p.z;
-        if (a.check && ((unsigned)j0 >= (unsigned)a.n_slots || (unsigned)j1 >= (unsigned)a.n_slots)) {
-          if (lane == 0) atomicOr(a.status, kStatusBounds);
-          j0 = j1 = 0;
+      int4 cur[kPairBatch];
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u) cur[u] = u < np ? __ldg(ep + u) : make_int4(0, 0, 0, 0);
+      for (int b = 0; b < np; b += kPairBatch) {
+        int4 nxt[kPairBatch];
+#pragma unroll
+        for (int u = 0; u < kPairBatch; ++u)
+          nxt[u] = b + kPairBatch + u < np ? __ldg(ep + b + kPairBatch + u) : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < kPairBatch; ++u) {
+          if (b + u >= np) break;
+          int j0 = cur[u].x, j1 = cur[u].z;
+          if (a.check && ((unsigned)j0 >= (unsigned)a.n_slots || (unsigned)j1 >= (unsigned)a.n_slots)) {
+            if (lane == 0) atomicOr(a.status, kStatusBounds);
+            j0 = j1 = 0;
+          }
+          acc0 = __fmaf_rn(__int_as_float(cur[u].y), AA[j0 * S + lane], acc0);
+          acc1 = __fmaf_rn(__int_as_float(cur[u].w), AA[j1 * S + lane], acc1);
         }
-        acc0 = __fmaf_rn(__int_as_float(p.y), AA[j0 * S + lane], acc0);
-        acc1 = __fmaf_rn(__int_as_float(p.w), AA[j1 * S + lane], acc1);
+#pragma unroll
+        for (int u = 0; u < kPairBatch; ++u) cur[u] = nxt[u];
       }
       const float acc = acc0 + acc1;
       const int row = task.x;
       const bool top = (task.y & 2) != 0;
+      bool ok = true;
       if (a.check && (unsigned)row >= (unsigned)a.n_slots) {
         if (lane == 0) atomicOr(a.status, kStatusBounds);
-        continue;
+        ok = false;
       }
-      const float lin = (task.y & 5) == 5 ? __ldg(a.lin + row) : 0.f;
-      float ap, xl = 0.f, xr = 0.f;
-      if (GRAD && top) {
-        xl = AA[task.z * S + lane];
-        xr = AA[task.w * S + lane];
-        ap = xl * xr;
-      } else {
-        ap = AA[row * S + lane];
-      }
-      phiacc.add(ap * __fmaf_rn(half, acc, lin));
-      if constexpr (GRAD) {
-        const float g = pbl * (acc + lin);
-        if (top) {
-          atomicAdd(G + task.z * S + lane, g * xr);
-          atomicAdd(G + task.w * S + lane, g * xl);
+      if (ok) {
+        float ap, xl = 0.f, xr = 0.f;
+        if (GRAD && top) {
+          xl = AA[task.z * S + lane];
+          xr = AA[task.w * S + lane];
+          ap = xl * xr;
         } else {
-          atomicAdd(G + row * S + lane, g);
+          ap = AA[row * S + lane];
+        }
+        phiacc.add(ap * __fmaf_rn(half, acc, lin));
+        if constexpr (GRAD) {
+          const float g = pbl * (acc + lin);
+          if (top) {
+            atomicAdd(G + task.z * S + lane, g * xr);
+            atomicAdd(G + task.w * S + lane, g * xl);
+          } else {
+            atomicAdd(G + row * S + lane, g);
+          }
         }
       }
+      t = tn;
+      task = task_n;
+      q0 = q0n;
+      q1 = q1n;
+      lin = lin_n;
     }
     __syncthreads();
     // 4. adjoint through the inner operand nodes, order descending
     if constexpr (GRAD) {
       for (int lv = 0; lv < a.n_rev_levels; ++lv) {
-        for (int i = a.rev_off[lv] + warp; i < a.rev_off[lv + 1]; i += NW) {
-          const int s = __ldg(a.rev_slot + i), l = __ldg(a.rev_l + i), r = __ldg(a.rev_r + i);
-          if (a.check && ((unsigned)s >= (unsigned)a.n_g || (unsigned)l >= (unsigned)a.n_g ||
-                          (unsigned)r >= (unsigned)a.n_g)) {
-            if (lane == 0) atomicOr(a.status, kStatusBounds);
-            continue;
+        for (int i0 = a.rev_off[lv] + warp * kNodeBatch; i0 < a.rev_off[lv + 1]; i0 += NW * kNodeBatch) {
+          int s[kNodeBatch], l[kNodeBatch], r[kNodeBatch];
+#pragma unroll
+          for (int u = 0; u < kNodeBatch; ++u) {
+            const bool in = i0 + u < a.rev_off[lv + 1];
+            s[u] = in ? __ldg(a.rev_slot + i0 + u) : -1;
+            l[u] = in ? __ldg(a.rev_l + i0 + u) : 0;
+            r[u] = in ? __ldg(a.rev_r + i0 + u) : 0;
           }
-          const float g = G[s * S + lane];
-          atomicAdd(G + l * S + lane, g * AA[r * S + lane]);
-          atomicAdd(G + r * S + lane, g * AA[l * S + lane]);
+#pragma unroll
+          for (int u = 0; u < kNodeBatch; ++u) {
+            if (s[u] < 0) continue;
+            if (a.check && ((unsigned)s[u] >= (unsigned)a.n_g || (unsigned)l[u] >= (unsigned)a.n_g ||
+                            (unsigned)r[u] >= (unsigned)a.n_g)) {
+              if (lane == 0) atomicOr(a.status, kStatusBounds);
+              continue;
+            }
+            const float g = G[s[u] * S + lane];
+            atomicAdd(G + l[u] * S + lane, g * AA[r[u] * S + lane]);
+            atomicAdd(G + r[u] * S + lane, g * AA[l[u] * S + lane]);
+          }
         }
         __syncthreads();
       }
-      for (int i = tid; i < 32 * K; i += NT) {
-        const int e = i / K, k = i - e * K;
-        if (e < n_here) a.dA[env0 * K + i] = G[k * S + e];
+      for (int e = warp; e < n_here; e += NW) {
+        float* row = a.dA + (env0 + e) * K;
+        for (int k = lane; k < K; k += 32) row[k] = G[k * S + e];
       }
     }
     // 5. phi: per-lane partials of every warp, summed in FP64 in warp order
@@ -177,11 +245,28 @@ __global__ void bind_rm_kernel(const float* __restrict__ c, const int32_t* __res
   }
 }
 
+// thdr[t] = {first entry, end entry, coefficient bits, 0}: the coefficient is c of
+// task t's row when t is the row's first task and the row is a basis function, else 0
+__global__ void bind_thdr_kernel(const float* __restrict__ c, const int4* __restrict__ tasks,
+                                 const int32_t* __restrict__ toff, const int32_t* __restrict__ slot_basis, int32_t n,
+                                 int4* __restrict__ thdr) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int4 t = tasks[i];
+    const int32_t b = slot_basis[t.x];
+    const float lin = ((t.y & 5) == 5 && b >= 0) ? c[b] : 0.f;
+    thdr[i] = make_int4(toff[i], toff[i + 1], __float_as_int(lin), 0);
+  }
+}
+
 cudaError_t launch_bind_rm(const float* c, const int32_t* col, const int32_t* ebasis, const uint8_t* ew2, int64_t n,
-                           int2* ent, cudaStream_t st) {
+                           int2* ent, const int4* tasks, const int32_t* toff, const int32_t* slot_basis,
+                           int32_t n_tasks, int4* thdr, cudaStream_t st) {
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
   if (blocks < 1) blocks = 1;
   bind_rm_kernel<<<blocks, 256, 0, st>>>(c, col, ebasis, ew2, n, ent);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || n_tasks == 0) return e;
+  bind_thdr_kernel<<<(n_tasks + 255) / 256, 256, 0, st>>>(c, tasks, toff, slot_basis, n_tasks, thdr);
   return cudaGetLastError();
 }
 

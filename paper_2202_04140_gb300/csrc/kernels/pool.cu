@@ -168,7 +168,7 @@ template <int LMAX>
 __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float* __restrict__ pos,
                                                                     const int64_t* __restrict__ offsets,
                                                                     int64_t n_env, float rc, int nmin, int nmax,
-                                                                    const float* __restrict__ dA,
+                                                                    const float* __restrict__ dA, float alpha,
                                                                     float* __restrict__ dpos) {
   constexpr int NL = (LMAX + 1) * (LMAX + 1);
   __shared__ float sG[kPoolWarps][kPoolMaxR * NL];
@@ -261,9 +261,9 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
         C = Cn;
       }
       const float rg = xh * gx + yh * gy + u * gz;
-      dpos[3 * j] = ys * xh + (gx - xh * rg) * ir;
-      dpos[3 * j + 1] = ys * yh + (gy - yh * rg) * ir;
-      dpos[3 * j + 2] = ys * u + (gz - u * rg) * ir;
+      dpos[3 * j] = alpha * (ys * xh + (gx - xh * rg) * ir);
+      dpos[3 * j + 1] = alpha * (ys * yh + (gy - yh * rg) * ir);
+      dpos[3 * j + 2] = alpha * (ys * u + (gz - u * rg) * ir);
     }
   }
 }
@@ -340,11 +340,11 @@ cudaError_t launch_pool(const float* pos, const int64_t* offsets, int64_t n_env,
 }
 
 cudaError_t launch_pool_grad(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
-                             int lmax, const float* dA, float* dpos, cudaStream_t st) {
+                             int lmax, const float* dA, float alpha, float* dpos, cudaStream_t st) {
   cudaError_t e = ensure_pool_constants();
   if (e != cudaSuccess) return e;
   const int grid = pool_grid(n_env);
-  ACE_POOL_DISPATCH(pool_grad_kernel, pos, offsets, n_env, rc, nmin, nmax, dA, dpos)
+  ACE_POOL_DISPATCH(pool_grad_kernel, pos, offsets, n_env, rc, nmin, nmax, dA, alpha, dpos)
   return cudaGetLastError();
 }
 

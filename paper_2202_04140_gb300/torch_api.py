@@ -81,13 +81,17 @@ class Dag:
     def upload(self):
         L.ace_dag_upload(self.handle, _stream())
 
-    def _c_arg(self, mode: str, c: torch.Tensor, n_out: int) -> int:
-        """Device pointer of c, or 0 when the same, unmodified tensor is already bound for this mode."""
-        key = (c.data_ptr(), c._version, n_out, c.dtype, c.device)
-        if self._bound.get(mode) == key:
+    def _c_arg(self, mode: str, c: torch.Tensor, c2: torch.Tensor, n_out: int) -> int:
+        """Device pointer of c, or 0 when this very tensor, unmodified, is already bound for this mode.
+
+        The bound tensor is kept referenced, so its memory cannot be handed to a
+        different tensor while the library still holds coefficients gathered from it.
+        """
+        prev = self._bound.get(mode)
+        if prev is not None and prev[0] is c and prev[1] == c._version and prev[2] == n_out:
             return 0
-        self._bound[mode] = key
-        return c.data_ptr()
+        self._bound[mode] = (c, c._version, n_out)
+        return c2.data_ptr()
 
     def evaluate(self, A: torch.Tensor, c: torch.Tensor, readout: str = "plain") -> torch.Tensor:
         """phi[e][ch] = sum_k c[k][ch] prod_t A[e][k_t] (Eq. 2) through G (Eq. 4)."""
@@ -97,7 +101,7 @@ class Dag:
         c2 = c.reshape(self.n_basis, -1)
         n_out = c2.shape[1]
         phi = torch.empty((n_env, n_out), dtype=A.dtype, device=A.device)
-        L.ace_eval(self.handle, A.data_ptr(), self._c_arg("one", c2, n_out), n_env, n_out, _DTYPE[A.dtype],
+        L.ace_eval(self.handle, A.data_ptr(), self._c_arg("one", c, c2, n_out), n_env, n_out, _DTYPE[A.dtype],
                    _READOUT[readout], phi.data_ptr(), _stream())
         return phi
 
@@ -115,7 +119,7 @@ class Dag:
             pb = phi_bar.data_ptr()
         phi = torch.empty((n_env, n_out), dtype=A.dtype, device=A.device) if want_phi else None
         dA = torch.empty_like(A)
-        L.ace_eval_grad(self.handle, A.data_ptr(), self._c_arg("sym", c2, n_out), pb, n_env, n_out,
+        L.ace_eval_grad(self.handle, A.data_ptr(), self._c_arg("sym", c, c2, n_out), pb, n_env, n_out,
                         _DTYPE[A.dtype], _READOUT[readout], phi.data_ptr() if want_phi else 0, dA.data_ptr(),
                         _stream())
         return phi, dA
@@ -182,15 +186,15 @@ def pool_A(pos: torch.Tensor, offsets: torch.Tensor, nmin: int, nmax: int, lmax:
 
 
 def pool_A_grad(pos: torch.Tensor, offsets: torch.Tensor, dA: torch.Tensor, nmin: int, nmax: int, lmax: int,
-                rc: float) -> torch.Tensor:
-    """dpos[j] = sum_k dA[e(j)][k] grad (R_n Y_lm)(r_j); forces are -dpos when dA = dphi/dA."""
+                rc: float, alpha: float = 1.0) -> torch.Tensor:
+    """dpos[j] = alpha sum_k dA[e(j)][k] grad (R_n Y_lm)(r_j); alpha = -1 with dA = dphi/dA gives the forces."""
     pos = _dev(pos, "pos", torch.float32)
     offsets = _dev(offsets, "offsets", torch.int64)
     dA = _dev(dA, "dA", torch.float32)
     n_env = offsets.numel() - 1
     dpos = torch.empty_like(pos)
     L.ace_pool_A_grad(pos.data_ptr(), offsets.data_ptr(), n_env, pos.shape[0], rc, nmin, nmax, lmax,
-                      dA.data_ptr(), dpos.data_ptr(), _stream())
+                      dA.data_ptr(), alpha, dpos.data_ptr(), _stream())
     return dpos
 
 
@@ -199,5 +203,5 @@ def energy_and_forces(dag: Dag, pos: torch.Tensor, offsets: torch.Tensor, c: tor
     """Full pipeline: pooling -> fused forward+adjoint -> pooling adjoint.  Returns (phi, F = -dphi/dr)."""
     A = pool_A(pos, offsets, nmin, nmax, lmax, rc)
     phi, dA = dag.evaluate_grad(A, c, None, readout)
-    dpos = pool_A_grad(pos, offsets, dA, nmin, nmax, lmax, rc)
-    return phi, -dpos
+    F = pool_A_grad(pos, offsets, dA, nmin, nmax, lmax, rc, alpha=-1.0)
+    return phi, F

@@ -134,6 +134,17 @@ def test_coefficient_rebinding_and_edge_sizes(dev, kernel, monkeypatch):
     c2 = to_f32(2.0 * c32)
     phi2 = d.evaluate(At, t(c2, torch.float32, dev)).cpu().numpy()
     assert normalized_error(phi2, phi_naive(A32, o, c2), error_scale(A32, o, c2)) < TOL32
+    # a new coefficient tensor at a recycled address is bound again (no stale coefficients)
+    for scale in (3.0, 5.0):
+        cs = to_f32(scale * c32)
+        phis = d.evaluate(At, t(cs, torch.float32, dev)).cpu().numpy()
+        assert normalized_error(phis, phi_naive(A32, o, cs), error_scale(A32, o, cs)) < TOL32
+    # an in-place update of the bound tensor is seen (its version changes)
+    cin = t(c32, torch.float32, dev)
+    d.evaluate(At, cin)
+    cin.mul_(2.0)
+    phii = d.evaluate(At, cin).cpu().numpy()
+    assert normalized_error(phii, phi_naive(A32, o, c2), error_scale(A32, o, c2)) < TOL32
     empty = torch.empty((0, d.K), dtype=torch.float32, device=dev)
     assert d.evaluate(empty, ct).shape == (0, 1)          # binds c32 again, evaluates nothing
     # c = NULL reuses the coefficients bound by the previous call (c32 here)

@@ -304,3 +304,5 @@ def test_invalid_arguments_fail_cleanly():
         L.ace_eval(d.handle, 8, 0, 1, 1, L.ACE_F32, 0, 16)
     with pytest.raises(L.AceError):
         L.ace_pool_A(0, 0, 1, 0, 5.0, 1, 8, 9, 0)                  # lmax > 8 unsupported
+    with pytest.raises(L.AceError):
+        L.ace_pool_A_grad(0, 0, 1, 0, 5.0, 1, 20, 2, 0, -1.0, 0)   # more than 16 radial functions
