@@ -64,6 +64,28 @@ def algorithmic_ops(w, n_nodes_ge2: int, n_basis: int, mode: str) -> float:
     return float(fwd + (adj if mode != "forward" else 0))
 
 
+# ---- traffic recorded from an ncu capture ---------------------------------------------------
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch of the workload's dominant kernel from profiles/traffic.json, or None
+    when no capture exists or the kernel or plan sources changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[workload]
+    except (OSError, KeyError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        try:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        except OSError:
+            return None
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
 # ---- ranks ----------------------------------------------------------------------------------
 
 def max_over_ranks(x: float, dist=None, device=None) -> float:
@@ -431,7 +453,8 @@ def main():
                        "n_sinks": dag.n_sinks, "mode": mode, "readout": args.readout,
                        "l2": f"inputs larger than L2: {n_sets} rotating buffer sets of {per_set / 1e6:.0f} MB"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved / peak_flops, "traffic": None,
+                         "frac": achieved / peak_flops,
+                         "traffic": recorded_traffic(w.name) if w.n_env == W.WORKLOADS[w.name].n_env else None,
                          "kernel": "fused forward+adjoint (ace_eval_grad)", "kernel_ms": kernel_ms,
                          "ops_per_env": ops_env, "fma_probe_tflops": probe_tflops},
             "clocks": clk.summary(),
