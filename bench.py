@@ -295,6 +295,8 @@ def main():
     w = W.workload(args.workload, **({"n_env": args.n_env} if args.n_env else {}))
     spec = Spec.from_workload(w)
     dag = Dag(spec)
+    # kernel form and environments per CTA chosen by the autotuner for exactly this request
+    tuned = dag.autotune(w.n_env, w.n_out, torch.float32, w.grad, args.readout)
     n_ge2 = dag.n_nodes - dag.K
     mode = "forward" if not w.grad else "forward+adjoint"
     ops_env = algorithmic_ops(w, n_ge2, dag.n_basis, mode)
@@ -451,6 +453,7 @@ def main():
                        "K": dag.K, "nu_max": w.nu_max, "deg_max": w.deg_max, "n_basis": dag.n_basis,
                        "n_nodes": dag.n_nodes, "n_aux": dag.n_aux, "n_operands": dag.n_operands,
                        "n_sinks": dag.n_sinks, "mode": mode, "readout": args.readout,
+                       "kernel_config": {"kernel": tuned["kernel"], "E": tuned["E"], "by": "autotuner"},
                        "l2": f"inputs larger than L2: {n_sets} rotating buffer sets of {per_set / 1e6:.0f} MB"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
                          "frac": achieved / peak_flops,

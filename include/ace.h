@@ -184,6 +184,20 @@ ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void*
                          int64_t n_env, int32_t n_out, int32_t dtype, int32_t readout, void* phi,
                          void* dA, void* stream);
 
+/* Autotuner (not in the paper): time every compiled kernel configuration for
+ * this request — the one-environment-per-lane kernel, and the tile-per-lane
+ * kernel with each tile size E of 1, 2, 4, 8, 16 environments — on n_env
+ * environments of zeros, and keep the fastest in the graph handle; later
+ * ace_eval / ace_eval_grad calls with the same dtype, n_out and mode use it.
+ * Allocates and frees temporary device buffers (inputs, outputs, coefficients)
+ * and leaves no coefficients bound.  best_kind (1 tile per lane, 2 one
+ * environment per lane), best_E and best_ms (mean of 3 launches) may be NULL.
+ * Environment variables ACE_KERNEL=lon|loe and ACE_TILE_E=<E> override both
+ * the tuned and the default choice.  Errors: as ace_eval, UNSUPPORTED when no
+ * configuration runs. */
+ace_status ace_dag_autotune(ace_dag* dag, int64_t n_env, int32_t n_out, int32_t dtype, int32_t grad, int32_t readout,
+                            void* stream, int32_t* best_kind, int32_t* best_E, float* best_ms);
+
 /* The plain FP64 GPU evaluation of G: one thread per environment walks every
  * node in id order (Eq. 4), keeping every node value in global memory, reads
  * out phi and, if dA != NULL, runs the reverse sweep.  It is the baseline the

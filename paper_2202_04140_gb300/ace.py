@@ -31,7 +31,7 @@ ACE_READOUT_PLAIN, ACE_READOUT_COMPENSATED, ACE_READOUT_FP64_FINAL = 0, 1, 2
 EXPORTED = [
     "ace_last_error", "ace_abi_version", "ace_build_spec", "ace_spec_info", "ace_spec_tuples",
     "ace_spec_free", "ace_build_dag", "ace_dag_info", "ace_dag_export", "ace_dag_plan_info",
-    "ace_dag_plan_array", "ace_dag_free", "ace_dag_upload", "ace_eval", "ace_eval_grad", "ace_eval_plain_workspace_bytes",
+    "ace_dag_plan_array", "ace_dag_free", "ace_dag_upload", "ace_dag_autotune", "ace_eval", "ace_eval_grad", "ace_eval_plain_workspace_bytes",
     "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_stream_status", "ace_device_info",
     "ace_fma_peak",
 ]
@@ -69,6 +69,7 @@ _SIG = {
     "ace_dag_plan_array": (C.c_int, [_p, C.c_char_p, _p, _P(_i64)]),
     "ace_dag_free": (None, [_p]),
     "ace_dag_upload": (C.c_int, [_p, _p]),
+    "ace_dag_autotune": (C.c_int, [_p, _i64, _i32, _i32, _i32, _i32, _p, _P(_i32), _P(_i32), _P(C.c_float)]),
     "ace_eval": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, _i32, _p, _p]),
     "ace_eval_grad": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _i32, _i32, _p, _p, _p]),
     "ace_eval_plain_workspace_bytes": (C.c_int, [_p, _i64, _i32, _P(_sz)]),
@@ -179,6 +180,14 @@ def ace_dag_upload(dag: int, stream: int = 0):
 
 
 # ---- evaluation -----------------------------------------------------------------------------
+
+def ace_dag_autotune(dag, n_env, n_out, dtype, grad, readout, stream=0):
+    """Returns (kind, E, ms) of the fastest configuration, now used by later evaluations."""
+    k, E, ms = C.c_int32(), C.c_int32(), C.c_float()
+    _check(_lib.ace_dag_autotune(dag, n_env, n_out, dtype, int(grad), readout, stream, C.byref(k), C.byref(E),
+                                 C.byref(ms)), "ace_dag_autotune")
+    return k.value, E.value, ms.value
+
 
 def ace_eval(dag, A, c, n_env, n_out, dtype, readout, phi, stream=0):
     _check(_lib.ace_eval(dag, A, c, n_env, n_out, dtype, readout, phi, stream), "ace_eval")

@@ -1,6 +1,8 @@
 // extern "C" entry points of libace (include/ace.h).
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -68,6 +70,9 @@ struct DevTaskSet {
 }  // namespace
 
 struct ace_dag {
+  // autotuned kernel choice per (dtype, padded channel count, adjoint): kind 1 = tile per lane
+  // (with tile size E), 2 = one environment per lane
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
   int32_t K = 0;
   int64_t n_basis = 0;
   Graph g;
@@ -274,8 +279,8 @@ bool checked_mode() {
 // Environments per CTA: the largest compiled E whose shared-memory tile fits,
 // with E * NOUT <= 64 accumulators per lane, and not so large that fewer tiles
 // than SMs remain.
-ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t n_env, int* E_out, int* nt_out,
-                       size_t* smem_out, const void** kern_out) {
+ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t n_env, int E_force, int* E_out,
+                       int* nt_out, size_t* smem_out, const void** kern_out) {
   const int cands_f32_1[] = {16, 8, 4, 2, 1};
   const int cands_f32_16[] = {4, 2, 1};
   const int cands_f64_1[] = {8, 4, 2, 1};
@@ -293,7 +298,8 @@ ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t
   const int64_t per_sm = std::max<int64_t>(1, n_env / std::max(1, d->sm_count));
   for (int i = 0; i < nc; ++i) {
     const int E = cands[i];
-    if (E > 1 && E > per_sm) continue;
+    if (E_force > 0 && E != E_force) continue;
+    if (E_force <= 0 && E > 1 && E > per_sm) continue;
     int nt = 0;
     const void* k = fused_kernel_ptr(dtype, E, npad, grad, 0, &nt);
     if (!k) continue;
@@ -372,17 +378,27 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
   DevTaskSet& dt = grad ? d->sym : d->one;
   ace_status s = bind(d, dt, c, n_out, dtype, st);
   if (s != ACE_OK) return s;
-  const int choice = kernel_choice();
+  const int npad = nout_pad_of(n_out);
+  // kernel choice: environment overrides (ACE_KERNEL, ACE_TILE_E), else the autotuned choice for
+  // this (dtype, channels, adjoint), else one environment per lane whenever it fits
+  int choice = kernel_choice(), E_force = 0;
+  if (const char* v = std::getenv("ACE_TILE_E")) E_force = std::atoi(v);
+  if (choice == 0 && E_force == 0) {
+    auto it = d->tuned.find(std::make_tuple(dtype, npad, grad ? 1 : 0));
+    if (it != d->tuned.end()) {
+      choice = it->second.first;
+      E_force = it->second.second;
+    }
+  }
   const bool loe_ok = dtype == ACE_F32 && n_out == 1 && dt.rm_bound &&
                       loe_smem(d->plan.n_slots, d->plan.n_g, grad, 1024) <= (size_t)d->smem_optin;
   if (choice == 2 && !loe_ok) return fail(ACE_ERR_UNSUPPORTED, "ACE_KERNEL=loe: graph or request does not fit");
   if (loe_ok && choice != 1) return run_loe(d, dt, A, phibar, n_env, readout, phi, dA, grad, st);
   if (!dt.col16) return fail(ACE_ERR_UNSUPPORTED, "more than 65535 stored values per environment");
-  const int npad = nout_pad_of(n_out);
   int E = 0, nt = 0;
   size_t smem = 0;
   const void* k = nullptr;
-  if ((s = choose_tile(d, dtype, npad, grad, n_env, &E, &nt, &smem, &k)) != ACE_OK) return s;
+  if ((s = choose_tile(d, dtype, npad, grad, n_env, E_force, &E, &nt, &smem, &k)) != ACE_OK) return s;
   const int ro = dtype == ACE_F32 ? readout : 0;
   k = fused_kernel_ptr(dtype, E, npad, grad, ro, &nt);
   if (!k) return fail(ACE_ERR_UNSUPPORTED, "no kernel for this readout mode");
@@ -665,6 +681,83 @@ ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void*
   if ((s = ensure_uploaded(dag, st)) != ACE_OK) return s;
   if (n_env == 0) return bind(dag, dag->sym, c, n_out, dtype, st);
   return run_fused(dag, A, c, phi_bar, n_env, n_out, dtype, readout, phi, dA, true, st);
+}
+
+ace_status ace_dag_autotune(ace_dag* dag, int64_t n_env, int32_t n_out, int32_t dtype, int32_t grad, int32_t readout,
+                            void* stream, int32_t* best_kind, int32_t* best_E, float* best_ms) {
+  ace_status s = check_eval_args(dag, nullptr, 0, n_out, dtype, readout);
+  if (s != ACE_OK) return s;
+  if (n_env < 1) return fail(ACE_ERR_INVALID_ARG, "n_env must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = ensure_uploaded(dag, st)) != ACE_OK) return s;
+  const size_t tsz = dtype == ACE_F32 ? 4 : 8;
+  void *A = nullptr, *c = nullptr, *phi = nullptr, *dA = nullptr;
+  cudaError_t e;
+  auto cleanup = [&]() {
+    for (void* p : {A, c, phi, dA})
+      if (p) cudaFree(p);
+  };
+  if ((e = cudaMalloc(&A, (size_t)n_env * dag->K * tsz)) != cudaSuccess ||
+      (e = cudaMalloc(&c, (size_t)dag->n_basis * n_out * tsz)) != cudaSuccess ||
+      (e = cudaMalloc(&phi, (size_t)n_env * n_out * tsz)) != cudaSuccess ||
+      (e = cudaMalloc(&dA, (size_t)n_env * dag->K * tsz)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cudaMalloc (autotune buffers)");
+  }
+  cudaMemsetAsync(A, 0, (size_t)n_env * dag->K * tsz, st);
+  cudaMemsetAsync(c, 0, (size_t)dag->n_basis * n_out * tsz, st);
+  const int npad = nout_pad_of(n_out);
+  const auto key = std::make_tuple((int)dtype, npad, grad ? 1 : 0);
+  dag->tuned.erase(key);
+  std::vector<std::pair<int, int>> cands = {{2, 0}};
+  for (int E : {1, 2, 4, 8, 16}) cands.push_back({1, E});
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = -1.f;
+  std::pair<int, int> pick{0, 0};
+  bool first = true;
+  for (auto cand : cands) {
+    dag->tuned[key] = cand;
+    auto run = [&]() {
+      const void* cc = first ? c : nullptr;
+      const ace_status r = grad ? ace_eval_grad(dag, A, cc, nullptr, n_env, n_out, dtype, readout, phi, dA, stream)
+                                : ace_eval(dag, A, cc, n_env, n_out, dtype, readout, phi, stream);
+      if (r == ACE_OK) first = false;
+      return r;
+    };
+    if (run() != ACE_OK) continue;  // configuration not compiled or does not fit
+    cudaEventRecord(a, st);
+    bool ok = true;
+    for (int r = 0; r < 3 && ok; ++r) ok = run() == ACE_OK;
+    cudaEventRecord(b, st);
+    if (!ok || cudaEventSynchronize(b) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    ms /= 3.f;
+    if (best < 0.f || ms < best) {
+      best = ms;
+      pick = cand;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  dag->tuned.erase(key);
+  DevTaskSet& used = grad ? dag->sym : dag->one;  // the zero coefficients must not serve a later NULL c
+  used.bound = false;
+  used.rm_bound = false;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "autotune");
+  }
+  cleanup();
+  clear_error();
+  if (best < 0.f) return fail(ACE_ERR_UNSUPPORTED, "no kernel configuration runs this request");
+  dag->tuned[key] = pick;
+  if (best_kind) *best_kind = pick.first;
+  if (best_E) *best_E = pick.second;
+  if (best_ms) *best_ms = best;
+  return ACE_OK;
 }
 
 ace_status ace_eval_plain_workspace_bytes(const ace_dag* dag, int64_t n_env, int32_t with_grad, size_t* bytes) {

@@ -81,6 +81,14 @@ class Dag:
     def upload(self):
         L.ace_dag_upload(self.handle, _stream())
 
+    def autotune(self, n_env: int, n_out: int = 1, dtype=torch.float32, grad: bool = True,
+                 readout: str = "plain") -> dict:
+        """Time every kernel configuration for this request and keep the fastest (see ace_dag_autotune)."""
+        kind, E, ms = L.ace_dag_autotune(self.handle, n_env, n_out, _DTYPE[dtype], grad, _READOUT[readout],
+                                         _stream())
+        self._bound.clear()          # the tuner leaves no coefficients bound
+        return {"kernel": {1: "tile_per_lane", 2: "env_per_lane"}[kind], "E": E, "ms": ms}
+
     def _c_arg(self, mode: str, c: torch.Tensor, c2: torch.Tensor, n_out: int) -> int:
         """Device pointer of c, or 0 when this very tensor, unmodified, is already bound for this mode.
 

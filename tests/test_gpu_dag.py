@@ -222,3 +222,48 @@ def test_stress_k810_fp64_sampled(dev):
     assert normalized_error(phi.cpu().numpy()[sub], phi_naive(A[sub], o, c), error_scale(A[sub], o, c)) < TOL64
     assert normalized_error(dA.cpu().numpy()[sub], grad_naive(A[sub], o, c),
                             grad_error_scale(A[sub], o, c)) < TOL64
+
+
+# ---- kernel configurations: every tile size, and the autotuner ---------------------------------
+
+@pytest.mark.parametrize("dtype,E", [("f32", 1), ("f32", 2), ("f32", 4), ("f32", 8), ("f32", 16),
+                                     ("f64", 1), ("f64", 2), ("f64", 4), ("f64", 8)])
+def test_every_tile_size(dev, dtype, E, monkeypatch):
+    """The tile-per-lane kernel with each compiled environments-per-CTA E (ragged last tile)."""
+    from paper_2202_04140_gb300.ace import AceError
+    monkeypatch.setenv("ACE_KERNEL", "lon")
+    monkeypatch.setenv("ACE_TILE_E", str(E))
+    w, o, d, A, c = setup("fwd_grad_k392", n_env=8 * E + 3)
+    tol = TOL32 if dtype == "f32" else TOL64
+    if dtype == "f32":
+        A, c = to_f32(A), to_f32(c)
+    td = torch.float32 if dtype == "f32" else torch.float64
+    try:
+        phi, dA = d.evaluate_grad(t(A, td, dev), t(c, td, dev))
+    except AceError as e:
+        assert "shared memory" in str(e)
+        pytest.skip(f"E={E} does not fit in shared memory for this graph")
+    assert normalized_error(phi.cpu().numpy(), phi_naive(A, o, c), error_scale(A, o, c)) < tol
+    assert normalized_error(dA.cpu().numpy(), grad_naive(A, o, c), grad_error_scale(A, o, c)) < tol
+
+
+@pytest.mark.parametrize("name,n_out,grad", [("fwd_grad_k392", 1, True), ("uneven_16ch_k392", 16, False)])
+def test_autotune_then_evaluate(dev, name, n_out, grad):
+    from paper_2202_04140_gb300.torch_api import Dag
+    w, o, _, A, c = setup(name, n_env=301)
+    d = Dag(_CACHE[(name, "balanced")][2])          # own graph handle: the tuned choice stays local
+    res = d.autotune(n_env=4096, n_out=n_out, dtype=torch.float32, grad=grad)
+    assert res["kernel"] in ("tile_per_lane", "env_per_lane") and res["ms"] > 0
+    if res["kernel"] == "tile_per_lane":
+        assert res["E"] in (1, 2, 4, 8, 16)
+    if n_out > 1:
+        assert res["kernel"] == "tile_per_lane"
+    A32, c32 = to_f32(A), to_f32(c)
+    At, ct = t(A32, torch.float32, dev), t(c32, torch.float32, dev)
+    ref, scale = phi_naive(A32, o, c32), error_scale(A32, o, c32)
+    if grad:
+        phi, dA = d.evaluate_grad(At, ct)
+        assert normalized_error(dA.cpu().numpy(), grad_naive(A32, o, c32), grad_error_scale(A32, o, c32)) < TOL32
+    else:
+        phi = d.evaluate(At, ct)
+    assert normalized_error(phi.cpu().numpy(), ref, scale) < TOL32
