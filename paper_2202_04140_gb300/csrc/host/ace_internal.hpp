@@ -91,6 +91,18 @@ struct LevelList {
   std::vector<int32_t> off;           // level offsets (size n_levels + 1)
 };
 
+// The adjoint sweep through the inner operand nodes as one flat list of
+// (consumer, partner, target) triples: every inner operand i = [x, p]
+// contributes G_i AA_p to G_x (and G_i AA_x to G_p).  Triples are grouped by the
+// correlation order of their target, descending (every consumer of a target has
+// a higher order, so its G is final when the target's level runs), and sorted
+// by target within a level, so that equal targets are contiguous and can be
+// summed before one update.
+struct PullList {
+  std::vector<int32_t> src, par, tgt; // consumer slot i, partner factor slot p, target slot x
+  std::vector<int32_t> lvl;           // level offsets into the triples (size n_levels + 1)
+};
+
 struct Plan {
   int32_t K = 0, n_slots = 0, n_g = 0;
   int64_t n_sinks = 0;
@@ -99,6 +111,7 @@ struct Plan {
   std::vector<int32_t> slot_basis;    // slot -> basis index or -1 (linear coefficient)
   LevelList fwd;                      // operand nodes by increasing order
   LevelList rev;                      // inner operand nodes by decreasing order
+  PullList pull;                      // the same sweep, gathered per target
   TaskSet sym;                        // symmetric sink form (forward + adjoint)
   TaskSet one;                        // one-sided sink form (forward only)
 };

@@ -81,6 +81,8 @@ struct ace_dag {
   int sm_count = 0, smem_optin = 0;
   int32_t *fwd_slot = nullptr, *fwd_l = nullptr, *fwd_r = nullptr;
   int32_t *rev_slot = nullptr, *rev_l = nullptr, *rev_r = nullptr;
+  int4* pull = nullptr;  // {consumer slot, partner slot, target slot, 0}
+  std::vector<int4> pull_host;
   int32_t *node_left = nullptr, *node_right = nullptr, *node_basis = nullptr, *slot_basis = nullptr;
   DevTaskSet sym, one;
   uint32_t* status = nullptr;
@@ -153,6 +155,13 @@ ace_status validate_plan(const Plan& p) {
   for (size_t i = 0; i < p.rev.slot.size(); ++i)
     if (!in(p.rev.slot[i], p.n_g) || !in(p.rev.l[i], p.n_g) || !in(p.rev.r[i], p.n_g))
       return fail(ACE_ERR_BOUNDS, "plan: adjoint index out of range");
+  const PullList& q = p.pull;
+  if (q.src.size() != q.par.size() || q.src.size() != q.tgt.size() || q.lvl.empty() ||
+      q.lvl.back() != (int32_t)q.src.size())
+    return fail(ACE_ERR_BOUNDS, "plan: adjoint gather list inconsistent");
+  for (size_t j = 0; j < q.src.size(); ++j)
+    if (!in(q.src[j], p.n_g) || !in(q.par[j], p.n_g) || !in(q.tgt[j], p.n_g))
+      return fail(ACE_ERR_BOUNDS, "plan: adjoint triple out of range");
   for (const TaskSet* ts : {&p.sym, &p.one}) {
     for (int32_t c : ts->col)
       if (!in(c, p.n_slots)) return fail(ACE_ERR_BOUNDS, "plan: entry column out of range");
@@ -200,6 +209,10 @@ ace_status ensure_uploaded(ace_dag* d, cudaStream_t st) {
   if ((s = upload_vec(d, p.rev.slot, &d->rev_slot, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.rev.l, &d->rev_l, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.rev.r, &d->rev_r, st)) != ACE_OK) return s;
+  d->pull_host.resize(p.pull.src.size());
+  for (size_t j = 0; j < p.pull.src.size(); ++j)
+    d->pull_host[j] = make_int4(p.pull.src[j], p.pull.par[j], p.pull.tgt[j], 0);
+  if ((s = upload_vec(d, d->pull_host, &d->pull, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, d->g.left, &d->node_left, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, d->g.right, &d->node_right, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, d->g.node_basis, &d->node_basis, st)) != ACE_OK) return s;
@@ -426,14 +439,12 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     a.fwd_slot = d->fwd_slot;
     a.fwd_l = d->fwd_l;
     a.fwd_r = d->fwd_r;
-    a.rev_slot = d->rev_slot;
-    a.rev_l = d->rev_l;
-    a.rev_r = d->rev_r;
+    a.pull = d->pull;
     a.n_fwd_levels = (int32_t)p.fwd.off.size() - 1;
-    a.n_rev_levels = (int32_t)p.rev.off.size() - 1;
+    a.n_pull_levels = (int32_t)p.pull.lvl.size() - 1;
     for (int i = 0; i <= dev::kMaxLevels; ++i) {
       a.fwd_off[i] = i < (int)p.fwd.off.size() ? p.fwd.off[i] : 0;
-      a.rev_off[i] = i < (int)p.rev.off.size() ? p.rev.off[i] : 0;
+      a.pull_lvl[i] = i < (int)p.pull.lvl.size() ? p.pull.lvl[i] : 0;
     }
     a.tasks = dt.tasks;
     a.slice_off = dt.slice_off;
@@ -623,6 +634,10 @@ ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out
   else if (n == "rev_l") v = &p.rev.l;
   else if (n == "rev_r") v = &p.rev.r;
   else if (n == "rev_off") v = &p.rev.off;
+  else if (n == "pull_tgt") v = &p.pull.tgt;
+  else if (n == "pull_src") v = &p.pull.src;
+  else if (n == "pull_par") v = &p.pull.par;
+  else if (n == "pull_lvl") v = &p.pull.lvl;
   else if (n.rfind("sym_", 0) == 0) {
     if (!from_ts(p.sym, n.substr(4))) v = nullptr;
   } else if (n.rfind("one_", 0) == 0) {

@@ -357,6 +357,40 @@ ace_status build_plan(const Spec& spec, const Graph& g, int task_len, Plan& plan
   if ((int)plan.fwd.off.size() - 1 > nu_max || (int)plan.rev.off.size() - 1 > nu_max)
     return fail(ACE_ERR_INVALID_ARG, "internal: too many levels");
 
+  // gather form of the reverse sweep: consumers of each factor among the inner operands
+  {
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> cons(plan.n_g);
+    for (int32_t i = K; i < plan.n_g; ++i) {
+      cons[slot_l[i]].push_back({i, slot_r[i]});
+      cons[slot_r[i]].push_back({i, slot_l[i]});
+    }
+    std::vector<int32_t> tg;
+    for (int32_t x = 0; x < plan.n_g; ++x)
+      if (!cons[x].empty()) tg.push_back(x);
+    auto order_of = [&](int32_t x) { return g.order[plan.slot_node[x]]; };
+    // order descending, then by slot
+    std::stable_sort(tg.begin(), tg.end(), [&](int32_t a, int32_t b) {
+      if (order_of(a) != order_of(b)) return order_of(a) > order_of(b);
+      return a < b;
+    });
+    PullList& P = plan.pull;
+    P = PullList();
+    int32_t cur = -1;
+    for (int32_t x : tg) {
+      if (order_of(x) != cur) {
+        P.lvl.push_back((int32_t)P.src.size());
+        cur = order_of(x);
+      }
+      for (auto& pr : cons[x]) {
+        P.src.push_back(pr.first);
+        P.par.push_back(pr.second);
+        P.tgt.push_back(x);
+      }
+    }
+    P.lvl.push_back((int32_t)P.src.size());
+    if ((int)P.lvl.size() - 1 > nu_max) return fail(ACE_ERR_INVALID_ARG, "internal: too many levels");
+  }
+
   // sinks -> sparse rows
   std::vector<std::vector<Entry>> sym_rows(n_slots), one_rows(n_slots);
   std::vector<int32_t> sink_deg(n_slots, 0);

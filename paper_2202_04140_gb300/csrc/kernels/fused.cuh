@@ -14,7 +14,8 @@
 //     the adjoint pass adds g = phibar . (c_s + u) to G_s, or pushes it to the
 //     factors of s (G_l += g AA_r, G_r += g AA_l) when s is a top operand.
 //  4. Adjoint through the inner operand nodes, order descending:
-//     G_l += G_i AA_r, G_r += G_i AA_l.
+//     G_x += G_i AA_p for every inner operand i = [x, p], summed per target x
+//     across the warp before one shared-memory update.
 //  5. dA[e][k] = G[k][e]; phi[e] = block sum of the lane accumulators.
 // No global scratch memory, no inter-CTA communication: tiles are assigned
 // statically (tile = blockIdx.x + i * gridDim.x).
@@ -44,12 +45,10 @@ struct FusedArgs {
   const int32_t* fwd_slot;
   const int32_t* fwd_l;
   const int32_t* fwd_r;
-  const int32_t* rev_slot;
-  const int32_t* rev_l;
-  const int32_t* rev_r;
+  const int4* pull;  // adjoint sweep: {inner consumer, partner factor, target, 0} by target level
   int32_t fwd_off[kMaxLevels + 1];
-  int32_t rev_off[kMaxLevels + 1];
-  int32_t n_fwd_levels, n_rev_levels;
+  int32_t pull_lvl[kMaxLevels + 1];
+  int32_t n_fwd_levels, n_pull_levels;
   const int4* tasks;
   const int32_t* slice_off;
   const int32_t* slice_steps;
@@ -246,6 +245,8 @@ struct Acc<double, kReadPlain> : AccD<double> {};
 // Entries of one lane's task, software-pipelined: the (column, coefficient)
 // pairs of the next kBatch steps are loaded while the current kBatch are used.
 constexpr int kBatch = 4;
+// Operand nodes per thread whose indices are loaded together in the level loops.
+constexpr int kNodeBatch = 4;
 
 template <typename T, int E, int NOUT, bool CHECK>
 __device__ __forceinline__ void use_entry(const FusedArgs<T>& a, const T* __restrict__ AA, int j, const T (&v)[NOUT],
@@ -333,10 +334,25 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
   const int warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
   const int gs = a.gs;
+  // The header of the warp's next slice (its tasks, length and entry offset) is
+  // loaded while the current slice runs.
+  int4 task_n = make_int4(-1, 0, -1, -1);
+  int steps_n = 0;
+  int32_t off_n = 0;
+  if (warp < a.n_slices) {
+    task_n = __ldg(a.tasks + (size_t)warp * 32 + lane);
+    steps_n = __ldg(a.slice_steps + warp);
+    off_n = __ldg(a.slice_off + warp);
+  }
   for (int sl = warp; sl < a.n_slices; sl += NW) {
-    const int4 task = __ldg(a.tasks + (size_t)sl * 32 + lane);
-    const int steps = __ldg(a.slice_steps + sl);
-    const int32_t off = __ldg(a.slice_off + sl);
+    const int4 task = task_n;
+    const int steps = steps_n;
+    const int32_t off = off_n;
+    if (sl + NW < a.n_slices) {
+      task_n = __ldg(a.tasks + (size_t)(sl + NW) * 32 + lane);
+      steps_n = __ldg(a.slice_steps + sl + NW);
+      off_n = __ldg(a.slice_off + sl + NW);
+    }
     T acc[E][NOUT];
 #pragma unroll
     for (int e = 0; e < E; ++e)
@@ -456,19 +472,32 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
     // 2. operand nodes, order ascending (Eq. 4)
     for (int lv = 0; lv < a.n_fwd_levels; ++lv) {
       const int b = a.fwd_off[lv], eidx = a.fwd_off[lv + 1];
-      for (int i = b + tid; i < eidx; i += NT) {
-        const int s = __ldg(a.fwd_slot + i), l = __ldg(a.fwd_l + i), r = __ldg(a.fwd_r + i);
-        if (a.check && ((unsigned)s >= (unsigned)a.n_slots || (unsigned)l >= (unsigned)a.n_slots ||
-                        (unsigned)r >= (unsigned)a.n_slots)) {
-          atomicOr(a.status, kStatusBounds);
-          continue;
-        }
-        T xl[E], xr[E], y[E];
-        load_slot<T, E>(AA + (size_t)l * E, xl);
-        load_slot<T, E>(AA + (size_t)r * E, xr);
+      // kNodeBatch nodes per thread at a time, their indices loaded together
+      for (int i0 = b + tid; i0 < eidx; i0 += NT * kNodeBatch) {
+        int s[kNodeBatch], l[kNodeBatch], r[kNodeBatch];
 #pragma unroll
-        for (int e = 0; e < E; ++e) y[e] = xl[e] * xr[e];
-        store_slot<T, E>(AA + (size_t)s * E, y);
+        for (int u = 0; u < kNodeBatch; ++u) {
+          const int i = i0 + u * NT;
+          const bool in = i < eidx;
+          s[u] = in ? __ldg(a.fwd_slot + i) : -1;
+          l[u] = in ? __ldg(a.fwd_l + i) : 0;
+          r[u] = in ? __ldg(a.fwd_r + i) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kNodeBatch; ++u) {
+          if (s[u] < 0) continue;
+          if (a.check && ((unsigned)s[u] >= (unsigned)a.n_slots || (unsigned)l[u] >= (unsigned)a.n_slots ||
+                          (unsigned)r[u] >= (unsigned)a.n_slots)) {
+            atomicOr(a.status, kStatusBounds);
+            continue;
+          }
+          T xl[E], xr[E], y[E];
+          load_slot<T, E>(AA + (size_t)l[u] * E, xl);
+          load_slot<T, E>(AA + (size_t)r[u] * E, xr);
+#pragma unroll
+          for (int e = 0; e < E; ++e) y[e] = xl[e] * xr[e];
+          store_slot<T, E>(AA + (size_t)s[u] * E, y);
+        }
       }
       __syncthreads();
     }
@@ -477,25 +506,41 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
     if (a.check) run_tasks<T, E, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc);
     else run_tasks<T, E, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc);
     __syncthreads();
-    // 4. adjoint through the inner operand nodes, order descending
+    // 4. adjoint through the inner operand nodes, order descending: one lane per
+    //    (consumer i, partner p, target x) triple forms G_i AA_p; triples of equal
+    //    target are contiguous, so a segmented warp sum leaves one update per run
     if constexpr (GRAD) {
-      for (int lv = 0; lv < a.n_rev_levels; ++lv) {
-        const int b = a.rev_off[lv], eidx = a.rev_off[lv + 1];
-        for (int i = b + tid; i < eidx; i += NT) {
-          const int s = __ldg(a.rev_slot + i), l = __ldg(a.rev_l + i), r = __ldg(a.rev_r + i);
-          if (a.check && ((unsigned)s >= (unsigned)a.n_g || (unsigned)l >= (unsigned)a.n_g ||
-                          (unsigned)r >= (unsigned)a.n_g)) {
+      for (int lv = 0; lv < a.n_pull_levels; ++lv) {
+        const int end = a.pull_lvl[lv + 1];
+        for (int j0 = a.pull_lvl[lv] + warp * 32; j0 < end; j0 += NT) {
+          const int j = j0 + lane;
+          int4 q = j < end ? __ldg(a.pull + j) : make_int4(0, 0, -1, 0);
+          bool valid = q.z >= 0;
+          if (a.check && valid &&
+              ((unsigned)q.x >= (unsigned)a.n_g || (unsigned)q.y >= (unsigned)a.n_g || (unsigned)q.z >= (unsigned)a.n_g)) {
             atomicOr(a.status, kStatusBounds);
-            continue;
+            valid = false;
           }
-          T xl[E], xr[E];
-          load_slot<T, E>(AA + (size_t)l * E, xl);
-          load_slot<T, E>(AA + (size_t)r * E, xr);
+          if (!valid) q = make_int4(0, 0, -1 - lane, 0);
+          T xp[E], v[E];
+          load_slot<T, E>(AA + (size_t)q.y * E, xp);
 #pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const T g = G[(size_t)e * a.gs + s];
-            atomicAdd(G + (size_t)e * a.gs + l, g * xr[e]);
-            atomicAdd(G + (size_t)e * a.gs + r, g * xl[e]);
+          for (int e = 0; e < E; ++e) v[e] = valid ? G[(size_t)e * a.gs + q.x] * xp[e] : T(0);
+          const int key = q.z;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const int k2 = __shfl_down_sync(0xffffffffu, key, d);
+            const bool same = (lane + d < 32) && (k2 == key);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const T y = __shfl_down_sync(0xffffffffu, v[e], d);
+              if (same) v[e] += y;
+            }
+          }
+          const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+          if (valid && (lane == 0 || kprev != key)) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * a.gs + key, v[e]);
           }
         }
         __syncthreads();

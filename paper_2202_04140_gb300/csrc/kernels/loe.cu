@@ -22,7 +22,6 @@ namespace dev {
 
 constexpr int kLoeStride = 33;
 constexpr int kPairBatch = 4;  // entry pairs loaded together per warp
-constexpr int kNodeBatch = 4;  // operand nodes whose indices are loaded together per warp
 
 
 __host__ __device__ inline size_t loe_smem_bytes(int n_slots, int n_g, bool grad, int nt) {

@@ -111,14 +111,14 @@ def test_workload_digests(name):
 def plan_arrays(dag, mode):
     P = {k: L.ace_dag_plan_array(dag.handle, k) for k in
          ["slot_node", "slot_basis", "n_g", "fwd_slot", "fwd_l", "fwd_r", "fwd_off", "rev_slot", "rev_l", "rev_r",
-          "rev_off"]}
+          "rev_off", "pull_tgt", "pull_src", "pull_par", "pull_lvl"]}
     for k in ["tasks", "slice_off", "slice_steps", "col", "ebasis", "ew2"]:
         P[k] = L.ace_dag_plan_array(dag.handle, f"{mode}_{k}")
     P["tasks"] = P["tasks"].reshape(-1, 4)
     return P
 
 
-def emulate(dag, mode, A, c, phibar=None):
+def emulate(dag, mode, A, c, phibar=None, sweep="push"):
     P = plan_arrays(dag, mode)
     n_env, K = A.shape
     n_slots = len(P["slot_node"])
@@ -160,12 +160,22 @@ def emulate(dag, mode, A, c, phibar=None):
     np.add.at(G.T, pl, (gt * AA[:, pr]).T)
     np.add.at(G.T, pr, (gt * AA[:, pl]).T)
     np.add.at(G.T, row[valid & ~top], g[:, valid & ~top].T)
-    off = P["rev_off"]
-    for lv in range(len(off) - 1):
-        s = slice(off[lv], off[lv + 1])
-        gs = G[:, P["rev_slot"][s]]
-        np.add.at(G.T, P["rev_l"][s], (gs * AA[:, P["rev_r"][s]]).T)
-        np.add.at(G.T, P["rev_r"][s], (gs * AA[:, P["rev_l"][s]]).T)
+    if sweep == "push":
+        off = P["rev_off"]
+        for lv in range(len(off) - 1):
+            s = slice(off[lv], off[lv + 1])
+            gs = G[:, P["rev_slot"][s]]
+            np.add.at(G.T, P["rev_l"][s], (gs * AA[:, P["rev_r"][s]]).T)
+            np.add.at(G.T, P["rev_r"][s], (gs * AA[:, P["rev_l"][s]]).T)
+    else:
+        # gather form: per level, every triple reads a consumer whose value is final
+        lvl, tgt, src = P["pull_lvl"], P["pull_tgt"], P["pull_src"]
+        for lv in range(len(lvl) - 1):
+            j = slice(lvl[lv], lvl[lv + 1])
+            assert not set(src[j].tolist()) & set(tgt[j].tolist())
+            assert np.all(np.diff(tgt[j]) >= 0)
+            upd = G[:, src[j]] * AA[:, P["pull_par"][j]]
+            np.add.at(G.T, tgt[j], upd.T)
     return phi, G[:, :K]
 
 
@@ -184,10 +194,11 @@ def test_plan_emulation_matches_oracle(name, n_out, rule):
     for mode in ["one", "sym"]:
         phi, _ = emulate(dag, mode, A, c, pb)
         assert normalized_error(phi, ref, scale) < 1e-12
-    _, dA = emulate(dag, "sym", A, c, pb)
     gref = grad_naive(A, o, c, pb)
     gscale = grad_error_scale(A, o, c, pb)
-    assert normalized_error(dA, gref, gscale) < 1e-12
+    for sweep in ["push", "pull"]:
+        _, dA = emulate(dag, "sym", A, c, pb, sweep=sweep)
+        assert normalized_error(dA, gref, gscale) < 1e-12
 
 
 def emulate_row_major(dag, mode, A, c, phibar=None):
