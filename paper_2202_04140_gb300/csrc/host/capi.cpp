@@ -40,7 +40,8 @@ namespace {
 struct DevTaskSet {
   int4* tasks = nullptr;
   int32_t* slice_off = nullptr;
-  int32_t* slice_steps = nullptr;
+  int32_t* slice_steps = nullptr;  // device copy: steps | (adjoint reduction rounds << 16)
+  int32_t* tbasis = nullptr;       // per task: basis index of its row's own coefficient, or -1
   int32_t* col = nullptr;
   uint16_t* col16 = nullptr;  // columns as uint16 when every slot index fits
   int32_t* ebasis = nullptr;
@@ -89,6 +90,7 @@ struct ace_dag {
   std::vector<void*> allocations;
   std::vector<std::vector<uint16_t>> staging16;  // host copies kept alive until the upload completes
   std::vector<std::vector<int4>> staging_int4;
+  std::vector<std::vector<int32_t>> staging32;
 };
 
 namespace {
@@ -122,7 +124,32 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   ace_status s;
   if ((s = upload_vec(d, d->staging_int4.back(), &dt.tasks, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.slice_off, &dt.slice_off, st)) != ACE_OK) return s;
-  if ((s = upload_vec(d, ts.slice_steps, &dt.slice_steps, st)) != ACE_OK) return s;
+  // Per slice, the rounds of the segmented warp sum over equal adjoint targets
+  // (ceil(log2) of the longest run of equal targets among its 32 tasks), and per
+  // task the basis index of its row's own coefficient (first task of a row only).
+  std::vector<int32_t> steps_dev(ts.slice_steps.size()), tb(ts.tasks.size(), -1);
+  for (size_t sl = 0; sl < ts.slice_steps.size(); ++sl) {
+    int run = 1, longest = 1;
+    int prev_key = 0;
+    for (int j = 0; j < 32; ++j) {
+      const Task& t = ts.tasks[sl * 32 + j];
+      const int key = t.row < 0 ? -1 - j : ((t.flags & 2) ? t.pl : t.row);
+      run = (j > 0 && key == prev_key) ? run + 1 : 1;
+      longest = std::max(longest, run);
+      prev_key = key;
+    }
+    int rounds = 0;
+    while ((1 << rounds) < longest) ++rounds;
+    steps_dev[sl] = ts.slice_steps[sl] | (rounds << 16);
+  }
+  for (size_t i = 0; i < ts.tasks.size(); ++i) {
+    const Task& t = ts.tasks[i];
+    if (t.row >= 0 && (t.flags & 5) == 5) tb[i] = d->plan.slot_basis[t.row];
+  }
+  d->staging32.push_back(std::move(steps_dev));
+  if ((s = upload_vec(d, d->staging32.back(), &dt.slice_steps, st)) != ACE_OK) return s;
+  d->staging32.push_back(std::move(tb));
+  if ((s = upload_vec(d, d->staging32.back(), &dt.tbasis, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.col, &dt.col, st)) != ACE_OK) return s;
   if (d->plan.n_slots <= 65535) {
     d->staging16.emplace_back(ts.col.begin(), ts.col.end());
@@ -243,7 +270,7 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
     return ACE_OK;
   }
   const size_t vb = std::max<size_t>((size_t)dt.n_pad * npad * tsz, 16);
-  const size_t lb = std::max<size_t>((size_t)d->plan.n_slots * npad * tsz, 16);
+  const size_t lb = std::max<size_t>((size_t)dt.n_slices * 32 * npad * tsz, 16);
   cudaError_t e;
   if (vb > dt.vals_bytes) {
     if (dt.vals) cudaFree(dt.vals);
@@ -259,7 +286,7 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
     if ((e = cudaMalloc(&dt.lin, lb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     dt.lin_bytes = lb;
   }
-  e = launch_bind(dtype, c, n_out, npad, dt.ebasis, dt.ew2, dt.n_pad, dt.vals, d->slot_basis, d->plan.n_slots,
+  e = launch_bind(dtype, c, n_out, npad, dt.ebasis, dt.ew2, dt.n_pad, dt.vals, dt.tbasis, (int64_t)dt.n_slices * 32,
                   dt.lin, st);
   if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
   dt.rm_bound = false;

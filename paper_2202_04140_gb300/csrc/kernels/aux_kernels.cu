@@ -9,14 +9,14 @@ namespace ace {
 namespace dev {
 
 // vals[e][ch] = w(e) * c[basis(e)][ch] (w = 2 on the diagonal of the symmetric
-// sink form), 0 for padding entries and for ch >= n_out; lin[s][ch] likewise for
-// the stored value of slot s.
+// sink form), 0 for padding entries and for ch >= n_out; lin[t][ch] likewise for
+// the row coefficient of task t (lin_basis[t] = its basis index, or -1).
 template <typename T>
 __global__ void bind_kernel(const T* __restrict__ c, int n_out, int nout_pad, const int32_t* __restrict__ ebasis,
                             const uint8_t* __restrict__ ew2, int64_t n_entries, T* __restrict__ vals,
-                            const int32_t* __restrict__ slot_basis, int64_t n_slots, T* __restrict__ lin) {
+                            const int32_t* __restrict__ lin_basis, int64_t n_lin, T* __restrict__ lin) {
   const int64_t total_e = n_entries * nout_pad;
-  const int64_t total = total_e + n_slots * nout_pad;
+  const int64_t total = total_e + n_lin * nout_pad;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     if (i < total_e) {
       const int64_t e = i / nout_pad;
@@ -29,7 +29,7 @@ __global__ void bind_kernel(const T* __restrict__ c, int n_out, int nout_pad, co
       const int64_t j = i - total_e;
       const int64_t s = j / nout_pad;
       const int ch = (int)(j - s * nout_pad);
-      const int32_t b = slot_basis[s];
+      const int32_t b = lin_basis[s];
       lin[j] = (b >= 0 && ch < n_out) ? c[(int64_t)b * n_out + ch] : T(0);
     }
   }
@@ -106,17 +106,17 @@ __global__ void fma_probe_kernel(int64_t iters, float* out) {
 }  // namespace dev
 
 cudaError_t launch_bind(int dtype, const void* c, int n_out, int nout_pad, const int32_t* ebasis, const uint8_t* ew2,
-                        int64_t n_entries, void* vals, const int32_t* slot_basis, int64_t n_slots, void* lin,
+                        int64_t n_entries, void* vals, const int32_t* lin_basis, int64_t n_lin, void* lin,
                         cudaStream_t st) {
-  const int64_t total = (n_entries + n_slots) * nout_pad;
+  const int64_t total = (n_entries + n_lin) * nout_pad;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
   if (blocks < 1) blocks = 1;
   if (dtype == ACE_F32)
     dev::bind_kernel<float><<<blocks, 256, 0, st>>>((const float*)c, n_out, nout_pad, ebasis, ew2, n_entries,
-                                                    (float*)vals, slot_basis, n_slots, (float*)lin);
+                                                    (float*)vals, lin_basis, n_lin, (float*)lin);
   else
     dev::bind_kernel<double><<<blocks, 256, 0, st>>>((const double*)c, n_out, nout_pad, ebasis, ew2, n_entries,
-                                                     (double*)vals, slot_basis, n_slots, (double*)lin);
+                                                     (double*)vals, lin_basis, n_lin, (double*)lin);
   return cudaGetLastError();
 }
 

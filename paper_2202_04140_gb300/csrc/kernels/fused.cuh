@@ -55,7 +55,7 @@ struct FusedArgs {
   int32_t n_slices;
   const uint16_t* col16;    // entry columns (slot indices)
   const T* vals;  // [entries][NOUT]
-  const T* lin;   // [n_slots][NOUT]
+  const T* lin;   // [tasks][NOUT] row coefficient of each task (first task of a basis row), else 0
   int32_t check;
   uint32_t* status;
 };
@@ -336,22 +336,29 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
   const int gs = a.gs;
   // The header of the warp's next slice (its tasks, length and entry offset) is
   // loaded while the current slice runs.
+  // slice_steps holds the entry steps in its low 16 bits and the number of
+  // rounds of the segmented adjoint sum in the high bits.
   int4 task_n = make_int4(-1, 0, -1, -1);
-  int steps_n = 0;
+  int hdr_n = 0;
   int32_t off_n = 0;
+  T lin_n = T(0);  // one channel: the row coefficient is prefetched too
   if (warp < a.n_slices) {
     task_n = __ldg(a.tasks + (size_t)warp * 32 + lane);
-    steps_n = __ldg(a.slice_steps + warp);
+    hdr_n = __ldg(a.slice_steps + warp);
     off_n = __ldg(a.slice_off + warp);
+    if constexpr (NOUT == 1) lin_n = __ldg(a.lin + (size_t)warp * 32 + lane);
   }
   for (int sl = warp; sl < a.n_slices; sl += NW) {
     const int4 task = task_n;
-    const int steps = steps_n;
+    const int steps = hdr_n & 0xffff, rounds = hdr_n >> 16;
     const int32_t off = off_n;
+    T lin[NOUT];
+    if constexpr (NOUT == 1) lin[0] = lin_n;
     if (sl + NW < a.n_slices) {
       task_n = __ldg(a.tasks + (size_t)(sl + NW) * 32 + lane);
-      steps_n = __ldg(a.slice_steps + sl + NW);
+      hdr_n = __ldg(a.slice_steps + sl + NW);
       off_n = __ldg(a.slice_off + sl + NW);
+      if constexpr (NOUT == 1) lin_n = __ldg(a.lin + (size_t)(sl + NW) * 32 + lane);
     }
     T acc[E][NOUT];
 #pragma unroll
@@ -371,10 +378,7 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
       }
     }
     const int row = valid ? task.x : 0;
-    T lin[NOUT];
-#pragma unroll
-    for (int c = 0; c < NOUT; ++c) lin[c] = T(0);
-    if (valid && (task.y & 5) == 5) load_vals<T, NOUT>(a.lin + (size_t)row * NOUT, lin);
+    if constexpr (NOUT > 1) load_vals<T, NOUT>(a.lin + ((size_t)sl * 32 + lane) * NOUT, lin);
     // factors of a top operand (adjoint form); AA of the row is their product
     const int pl = (GRAD && valid && top) ? task.z : 0, pr = (GRAD && valid && top) ? task.w : 0;
     T xl[E], xr[E], ap[E];
@@ -412,8 +416,7 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
       T va[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) va[e] = top ? g[e] * xr[e] : g[e];
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
+      for (int r = 0, d = 1; r < rounds; ++r, d <<= 1) {  // rounds: warp-uniform, from the plan
         const int k2 = __shfl_down_sync(0xffffffffu, key, d);
         const bool same = (lane + d < 32) && (k2 == key);
 #pragma unroll

@@ -21,7 +21,7 @@ cudaError_t launch_bind_rm(const float* c, const int32_t* col, const int32_t* eb
                            int32_t n_tasks, int4* thdr, cudaStream_t st);
 
 cudaError_t launch_bind(int dtype, const void* c, int n_out, int nout_pad, const int32_t* ebasis, const uint8_t* ew2,
-                        int64_t n_entries, void* vals, const int32_t* slot_basis, int64_t n_slots, void* lin,
+                        int64_t n_entries, void* vals, const int32_t* lin_basis, int64_t n_lin, void* lin,
                         cudaStream_t st);
 
 cudaError_t launch_plain_f64(const double* A, const double* c, const double* phibar, int64_t n_env, int n_out, int K,
