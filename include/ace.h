@@ -187,7 +187,7 @@ ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void*
 /* Autotuner (not in the paper): time every compiled kernel configuration for
  * this request — the one-environment-per-lane kernel, and the tile-per-lane
  * kernel with each tile size E of 1, 2, 4, 8, 16 environments — on n_env
- * environments of zeros, and keep the fastest in the graph handle; later
+ * environments of small constant inputs, and keep the fastest in the graph handle; later
  * ace_eval / ace_eval_grad calls with the same dtype, n_out and mode use it.
  * Allocates and frees temporary device buffers (inputs, outputs, coefficients)
  * and leaves no coefficients bound.  best_kind (1 tile per lane, 2 one

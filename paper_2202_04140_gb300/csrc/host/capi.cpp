@@ -44,6 +44,16 @@ struct DevTaskSet {
   int32_t* tbasis = nullptr;       // per task: basis index of its row's own coefficient, or -1
   int32_t* col = nullptr;
   uint16_t* col16 = nullptr;  // columns as uint16 when every slot index fits
+  // The same entries packed four steps at a time for the FP32 one-channel kernels:
+  // group g of a slice holds steps 4g..4g+3 of each lane, columns as 4 x uint16 in
+  // a uint2 and coefficients as a float4, at off4[slice] + 32 g + lane.
+  uint2* col4 = nullptr;
+  int32_t* off4 = nullptr;
+  int32_t* ebasis4 = nullptr;
+  uint8_t* ew2_4 = nullptr;
+  int64_t n_pack = 0;  // packed entries (groups x 32 lanes x 4)
+  void* vals4 = nullptr;
+  size_t vals4_bytes = 0;
   int32_t* ebasis = nullptr;
   uint8_t* ew2 = nullptr;
   int32_t n_slices = 0;
@@ -91,6 +101,8 @@ struct ace_dag {
   std::vector<std::vector<uint16_t>> staging16;  // host copies kept alive until the upload completes
   std::vector<std::vector<int4>> staging_int4;
   std::vector<std::vector<int32_t>> staging32;
+  std::vector<std::vector<uint2>> staging_u2;
+  std::vector<std::vector<uint8_t>> staging8;
 };
 
 namespace {
@@ -154,6 +166,36 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   if (d->plan.n_slots <= 65535) {
     d->staging16.emplace_back(ts.col.begin(), ts.col.end());
     if ((s = upload_vec(d, d->staging16.back(), &dt.col16, st)) != ACE_OK) return s;
+    // packed copy: padding steps of a slice's last group get column 0 and no coefficient
+    std::vector<int32_t> off4(ts.slice_steps.size() + 1, 0);
+    for (size_t sl = 0; sl < ts.slice_steps.size(); ++sl)
+      off4[sl + 1] = off4[sl] + 32 * ((ts.slice_steps[sl] + 3) / 4);
+    const size_t n_groups = (size_t)off4.back();
+    std::vector<uint2> c4(n_groups, make_uint2(0u, 0u));
+    std::vector<int32_t> eb4(n_groups * 4, -1);
+    std::vector<uint8_t> w4(n_groups * 4, 0);
+    for (size_t sl = 0; sl < ts.slice_steps.size(); ++sl) {
+      const int steps = ts.slice_steps[sl];
+      for (int st4 = 0; st4 < steps; ++st4)
+        for (int j = 0; j < 32; ++j) {
+          const size_t src = (size_t)ts.slice_off[sl] + (size_t)st4 * 32 + j;
+          const size_t gi = (size_t)off4[sl] + (size_t)(st4 / 4) * 32 + j;
+          const uint32_t cv = (uint32_t)ts.col[src] << (16 * (st4 & 1));
+          if ((st4 & 2) == 0) c4[gi].x |= cv;
+          else c4[gi].y |= cv;
+          eb4[gi * 4 + (st4 & 3)] = ts.ebasis[src];
+          w4[gi * 4 + (st4 & 3)] = ts.ew2[src];
+        }
+    }
+    d->staging32.push_back(std::move(off4));
+    if ((s = upload_vec(d, d->staging32.back(), &dt.off4, st)) != ACE_OK) return s;
+    d->staging_u2.push_back(std::move(c4));
+    if ((s = upload_vec(d, d->staging_u2.back(), &dt.col4, st)) != ACE_OK) return s;
+    d->staging32.push_back(std::move(eb4));
+    if ((s = upload_vec(d, d->staging32.back(), &dt.ebasis4, st)) != ACE_OK) return s;
+    d->staging8.push_back(std::move(w4));
+    if ((s = upload_vec(d, d->staging8.back(), &dt.ew2_4, st)) != ACE_OK) return s;
+    dt.n_pack = (int64_t)n_groups * 4;
   }
   if ((s = upload_vec(d, ts.ebasis, &dt.ebasis, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.ew2, &dt.ew2, st)) != ACE_OK) return s;
@@ -289,6 +331,18 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
   e = launch_bind(dtype, c, n_out, npad, dt.ebasis, dt.ew2, dt.n_pad, dt.vals, dt.tbasis, (int64_t)dt.n_slices * 32,
                   dt.lin, st);
   if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
+  if (dtype == ACE_F32 && n_out == 1 && dt.col4) {
+    const size_t b4 = std::max<size_t>((size_t)dt.n_pack * 4, 16);
+    if (b4 > dt.vals4_bytes) {
+      if (dt.vals4) cudaFree(dt.vals4);
+      dt.vals4 = nullptr;
+      dt.vals4_bytes = 0;
+      if ((e = cudaMalloc(&dt.vals4, b4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      dt.vals4_bytes = b4;
+    }
+    e = launch_bind(dtype, c, n_out, 1, dt.ebasis4, dt.ew2_4, dt.n_pack, dt.vals4, nullptr, 0, nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
+  }
   dt.rm_bound = false;
   if (dtype == ACE_F32 && n_out == 1) {
     if (!dt.rm_ent) {
@@ -478,6 +532,9 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     a.slice_steps = dt.slice_steps;
     a.n_slices = dt.n_slices;
     a.col16 = dt.col16;
+    a.col4 = dt.col4;
+    a.off4 = dt.off4;
+    a.vals4 = dt.vals4;
     a.gs = dev::g_stride(p.n_g);
     a.vals = static_cast<const TT*>(dt.vals);
     a.lin = static_cast<const TT*>(dt.lin);
@@ -686,6 +743,7 @@ void ace_dag_free(ace_dag* dag) {
     for (DevTaskSet* t : {&dag->sym, &dag->one}) {
       if (t->vals) cudaFree(t->vals);
       if (t->lin) cudaFree(t->lin);
+      if (t->vals4) cudaFree(t->vals4);
       if (t->rm_ent) cudaFree(t->rm_ent);
       if (t->rm_thdr) cudaFree(t->rm_thdr);
     }
@@ -746,8 +804,10 @@ ace_status ace_dag_autotune(ace_dag* dag, int64_t n_env, int32_t n_out, int32_t 
     cleanup();
     return cuda_fail(e, "cudaMalloc (autotune buffers)");
   }
-  cudaMemsetAsync(A, 0, (size_t)n_env * dag->K * tsz, st);
-  cudaMemsetAsync(c, 0, (size_t)dag->n_basis * n_out * tsz, st);
+  // small non-zero inputs (every byte 0x3c: 0.0115 in FP32, 1.6e-18 in FP64), so that the
+  // timed arithmetic and shared-memory updates are those of real data
+  cudaMemsetAsync(A, 0x3c, (size_t)n_env * dag->K * tsz, st);
+  cudaMemsetAsync(c, 0x3c, (size_t)dag->n_basis * n_out * tsz, st);
   const int npad = nout_pad_of(n_out);
   const auto key = std::make_tuple((int)dtype, npad, grad ? 1 : 0);
   dag->tuned.erase(key);

@@ -54,6 +54,11 @@ struct FusedArgs {
   const int32_t* slice_steps;
   int32_t n_slices;
   const uint16_t* col16;    // entry columns (slot indices)
+  // FP32 one-channel kernels: the entries packed four steps per lane at a time
+  // (group g of a slice at off4[slice] + 32 g + lane: 4 x uint16 columns, float4 coefficients)
+  const uint2* col4;
+  const int32_t* off4;
+  const void* vals4;
   const T* vals;  // [entries][NOUT]
   const T* lin;   // [tasks][NOUT] row coefficient of each task (first task of a basis row), else 0
   int32_t check;
@@ -327,6 +332,53 @@ __device__ __forceinline__ void task_entries(const FusedArgs<T>& a, const T* __r
   task_entries_impl<T, E, NOUT, CHECK>(a, AA, a.col16 + off + lane, valp, steps, acc);
 }
 
+// Four packed entries of one lane: the first n (warp-uniform) are used.
+template <int E, bool CHECK, bool FULL>
+__device__ __forceinline__ void use_group(const FusedArgs<float>& a, const float* __restrict__ AA, uint2 c, float4 v,
+                                          int n, float (&acc)[E][1]) {
+  const int j[4] = {(int)(c.x & 0xffffu), (int)(c.x >> 16), (int)(c.y & 0xffffu), (int)(c.y >> 16)};
+  const float w[4][1] = {{v.x}, {v.y}, {v.z}, {v.w}};
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (FULL || k < n) use_entry<float, E, 1, CHECK>(a, AA, j[k], w[k], acc);
+}
+
+// The entries of one lane's task in packed groups; (c0, v0) is the slice's first
+// group, already loaded.  Groups alternate between two register sets, the next
+// one loading while the current one is used.
+template <int E, bool CHECK>
+__device__ __forceinline__ void task_entries_packed(const FusedArgs<float>& a, const float* __restrict__ AA,
+                                                    int32_t off4, int steps, int lane, uint2 c0, float4 v0,
+                                                    float (&acc)[E][1]) {
+  const int ng = (steps + 3) >> 2;
+  if (ng == 0) return;
+  const uint2* cp = a.col4 + off4 + lane;
+  const float4* vp = static_cast<const float4*>(a.vals4) + off4 + lane;
+  uint2 ca = c0, cb;
+  float4 va = v0, vb;
+  int g = 0;
+  while (true) {
+    if (g + 1 < ng) {
+      cb = __ldg(cp + (size_t)(g + 1) * 32);
+      vb = __ldg(vp + (size_t)(g + 1) * 32);
+      use_group<E, CHECK, true>(a, AA, ca, va, 4, acc);
+    } else {
+      use_group<E, CHECK, false>(a, AA, ca, va, steps - 4 * g, acc);
+      break;
+    }
+    ++g;
+    if (g + 1 < ng) {
+      ca = __ldg(cp + (size_t)(g + 1) * 32);
+      va = __ldg(vp + (size_t)(g + 1) * 32);
+      use_group<E, CHECK, true>(a, AA, cb, vb, 4, acc);
+    } else {
+      use_group<E, CHECK, false>(a, AA, cb, vb, steps - 4 * g, acc);
+      break;
+    }
+    ++g;
+  }
+}
+
 template <typename T, int E, int NOUT, bool GRAD, int RO, int NT, bool CHECK>
 __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
                                           const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT]) {
@@ -338,15 +390,28 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
   // loaded while the current slice runs.
   // slice_steps holds the entry steps in its low 16 bits and the number of
   // rounds of the segmented adjoint sum in the high bits.
+  // FP32 with one channel reads the packed entry groups, whose offsets replace
+  // the entry offsets; the first group of the next slice is loaded before the
+  // current slice's epilogue.
+  constexpr bool PACK = sizeof(T) == 4 && NOUT == 1;
+  const int32_t* offs = PACK ? a.off4 : a.slice_off;
   int4 task_n = make_int4(-1, 0, -1, -1);
   int hdr_n = 0;
   int32_t off_n = 0;
   T lin_n = T(0);  // one channel: the row coefficient is prefetched too
+  uint2 c_n = make_uint2(0u, 0u);
+  float4 v_n = make_float4(0.f, 0.f, 0.f, 0.f);
   if (warp < a.n_slices) {
     task_n = __ldg(a.tasks + (size_t)warp * 32 + lane);
     hdr_n = __ldg(a.slice_steps + warp);
-    off_n = __ldg(a.slice_off + warp);
+    off_n = __ldg(offs + warp);
     if constexpr (NOUT == 1) lin_n = __ldg(a.lin + (size_t)warp * 32 + lane);
+    if constexpr (PACK) {
+      if ((hdr_n & 0xffff) > 0) {
+        c_n = __ldg(a.col4 + off_n + lane);
+        v_n = __ldg(static_cast<const float4*>(a.vals4) + off_n + lane);
+      }
+    }
   }
   for (int sl = warp; sl < a.n_slices; sl += NW) {
     const int4 task = task_n;
@@ -354,10 +419,13 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
     const int32_t off = off_n;
     T lin[NOUT];
     if constexpr (NOUT == 1) lin[0] = lin_n;
-    if (sl + NW < a.n_slices) {
+    const uint2 c0 = c_n;
+    const float4 v0 = v_n;
+    const bool has_next = sl + NW < a.n_slices;
+    if (has_next) {
       task_n = __ldg(a.tasks + (size_t)(sl + NW) * 32 + lane);
       hdr_n = __ldg(a.slice_steps + sl + NW);
-      off_n = __ldg(a.slice_off + sl + NW);
+      off_n = __ldg(offs + sl + NW);
       if constexpr (NOUT == 1) lin_n = __ldg(a.lin + (size_t)(sl + NW) * 32 + lane);
     }
     T acc[E][NOUT];
@@ -365,7 +433,15 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
     for (int e = 0; e < E; ++e)
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) acc[e][c] = T(0);
-    task_entries<T, E, NOUT, CHECK>(a, AA, off, steps, lane, acc);
+    if constexpr (PACK) {
+      task_entries_packed<E, CHECK>(a, AA, off, steps, lane, c0, v0, acc);
+      if (has_next && (hdr_n & 0xffff) > 0) {
+        c_n = __ldg(a.col4 + off_n + lane);
+        v_n = __ldg(static_cast<const float4*>(a.vals4) + off_n + lane);
+      }
+    } else {
+      task_entries<T, E, NOUT, CHECK>(a, AA, off, steps, lane, acc);
+    }
     const bool top = (task.y & 2) != 0;
     bool valid = task.x >= 0;
     if constexpr (CHECK) {
