@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--readout", default="compensated", choices=["plain", "compensated", "fp64"])
     ap.add_argument("--no-baselines", action="store_true", help="skip the plain-FP64 GPU and CPU oracle legs")
     ap.add_argument("--n-env", type=int, default=None, help="override the environment count (small profiling cases)")
+    ap.add_argument("--no-graph", action="store_true", help="launch every step directly instead of replaying "
+                    "a captured CUDA graph")
     return ap.parse_args()
 
 
@@ -272,6 +274,46 @@ class Step:
     def launches_per_step(self):
         return 3 if self.w.pooling else 1
 
+    def capture(self):
+        """One CUDA graph per buffer set (the step's launches, outputs in the graph's pool)."""
+        t = self.torch
+        side = t.cuda.Stream()
+        side.wait_stream(t.cuda.current_stream())
+        with t.cuda.stream(side):
+            for i in range(len(self.sets)):
+                self(i)
+        t.cuda.current_stream().wait_stream(side)
+        self.graphs, self.outs = [], []
+        for i in range(len(self.sets)):
+            g = t.cuda.CUDAGraph()
+            with t.cuda.graph(g):
+                out = self(i)
+            self.graphs.append(g)
+            self.outs.append(out)
+
+    def run(self, i):
+        graphs = getattr(self, "graphs", None)
+        if graphs:
+            graphs[i % len(graphs)].replay()
+            return self.outs[i % len(graphs)]
+        return self(i)
+
+
+def capture_or_direct(torch, fn, graph: bool):
+    """fn itself, or the replay of a CUDA graph captured from it (after two warm-up calls)."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    if not graph:
+        return fn
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g.replay
+
 
 def main():
     args = parse()
@@ -311,9 +353,11 @@ def main():
     per_set = step.in_bytes + step.out_bytes
     n_sets = max(1, int(np.ceil(2.5 * l2 / per_set)))
     step = Step(w, dag, torch, dev, n_sets, args.readout)
+    if not args.no_graph:
+        step.capture()
 
     for i in range(args.warmup):
-        step(i)
+        step.run(i)
     barrier()
     st = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -322,7 +366,7 @@ def main():
         barrier()
         ev0.record(st)
         for i in range(args.steps):
-            step(i)
+            step.run(i)
         ev1.record(st)
         barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
@@ -337,7 +381,7 @@ def main():
         barrier()
         ev0.record(st)
         for i in range(args.steps):
-            step(i)
+            step.run(i)
         ev1.record(st)
         barrier()
         kernel_ms = ev0.elapsed_time(ev1) / args.steps
@@ -365,12 +409,8 @@ def main():
         dA_host = torch.empty_like(A_host).pin_memory() if w.grad else None
         phi_host = torch.empty((w.n_env, w.n_out), dtype=torch.float32).pin_memory()
         n_e2e = max(3, min(args.steps, 50))
-        for _ in range(2):
-            x = A_host.to(dev, non_blocking=True)
-            phi, dA = dag.evaluate_grad(x, step.c, None, args.readout) if w.grad else (dag.evaluate(x, step.c), None)
-        barrier()
-        ev0.record(st)
-        for _ in range(n_e2e):
+
+        def e2e_step():
             x = A_host.to(dev, non_blocking=True)
             if w.grad:
                 phi, dA = dag.evaluate_grad(x, step.c, None, args.readout)
@@ -378,6 +418,12 @@ def main():
             else:
                 phi = dag.evaluate(x, step.c, args.readout)
             phi_host.copy_(phi, non_blocking=True)
+
+        run_e2e = capture_or_direct(torch, e2e_step, not args.no_graph)
+        barrier()
+        ev0.record(st)
+        for _ in range(n_e2e):
+            run_e2e()
         ev1.record(st)
         barrier()
         e_ms = ev0.elapsed_time(ev1)
@@ -390,14 +436,19 @@ def main():
         F_host = torch.empty_like(P_host).pin_memory()
         phi_host = torch.empty((w.n_env, 1), dtype=torch.float32).pin_memory()
         n_e2e = max(3, min(args.steps, 50))
-        barrier()
-        ev0.record(st)
-        for _ in range(n_e2e):
+
+        def e2e_step():
             P = P_host.to(dev, non_blocking=True)
             off = off_host.to(dev, non_blocking=True)
             phi, F = energy_and_forces(dag, P, off, step.c, w.nmin, w.nmax, w.lmax, w.rc, args.readout)
             F_host.copy_(F, non_blocking=True)
             phi_host.copy_(phi, non_blocking=True)
+
+        run_e2e = capture_or_direct(torch, e2e_step, not args.no_graph)
+        barrier()
+        ev0.record(st)
+        for _ in range(n_e2e):
+            run_e2e()
         ev1.record(st)
         barrier()
         e_ms = ev0.elapsed_time(ev1)
@@ -432,7 +483,8 @@ def main():
         idx = np.array([0, 1, w.n_env // 2, w.n_env - 1])
         A_s = step.A0[idx].double().cpu().numpy()
         c_s = step.c.double().cpu().numpy()
-        phi, dA = step(0)
+        phi, dA = step.run(0)          # the launch path that was timed (graph replay by default)
+        torch.cuda.synchronize()
         from oracle.evaluate import error_scale, grad_error_scale
         ref_phi, ref_dA = oracle_step(o, A_s, c_s)
         def nerr(x, r, s):
@@ -454,6 +506,7 @@ def main():
                        "n_nodes": dag.n_nodes, "n_aux": dag.n_aux, "n_operands": dag.n_operands,
                        "n_sinks": dag.n_sinks, "mode": mode, "readout": args.readout,
                        "kernel_config": {"kernel": tuned["kernel"], "E": tuned["E"], "by": "autotuner"},
+                       "launch": "direct" if args.no_graph else "CUDA graph replay (one graph per buffer set)",
                        "l2": f"inputs larger than L2: {n_sets} rotating buffer sets of {per_set / 1e6:.0f} MB"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
                          "frac": achieved / peak_flops,
