@@ -374,7 +374,7 @@ bool checked_mode() {
 // with E * NOUT <= 64 accumulators per lane, and not so large that fewer tiles
 // than SMs remain.
 ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t n_env, int E_force, int* E_out,
-                       int* nt_out, size_t* smem_out, const void** kern_out) {
+                       int* nt_out, size_t* smem_out, const void** kern_out, bool* stage_out) {
   const int cands_f32_1[] = {16, 8, 4, 2, 1};
   const int cands_f32_16[] = {4, 2, 1};
   const int cands_f64_1[] = {8, 4, 2, 1};
@@ -397,8 +397,15 @@ ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t
     int nt = 0;
     const void* k = fused_kernel_ptr(dtype, E, npad, grad, 0, &nt);
     if (!k) continue;
-    dev::SmemLayout L = dev::smem_layout(E, npad, grad, d->plan.n_slots, d->plan.n_g, nt, (int)tsz);
+    // with the bulk-copy staging buffer when it fits, else without
+    bool stage = true;
+    dev::SmemLayout L = dev::smem_layout(E, npad, grad, d->plan.n_slots, d->plan.n_g, nt, (int)tsz, d->K, true);
+    if (L.total > (size_t)d->smem_optin) {
+      stage = false;
+      L = dev::smem_layout(E, npad, grad, d->plan.n_slots, d->plan.n_g, nt, (int)tsz, d->K, false);
+    }
     if (L.total > (size_t)d->smem_optin) continue;
+    *stage_out = stage;
     *E_out = E;
     *nt_out = nt;
     *smem_out = L.total;
@@ -492,7 +499,9 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
   int E = 0, nt = 0;
   size_t smem = 0;
   const void* k = nullptr;
-  if ((s = choose_tile(d, dtype, npad, grad, n_env, E_force, &E, &nt, &smem, &k)) != ACE_OK) return s;
+  bool stage = false;
+  if ((s = choose_tile(d, dtype, npad, grad, n_env, E_force, &E, &nt, &smem, &k, &stage)) != ACE_OK) return s;
+  if (const char* v = std::getenv("ACE_STAGE")) stage = stage && v[0] != '0';  // ACE_STAGE=0: plain loads of A
   const int ro = dtype == ACE_F32 ? readout : 0;
   k = fused_kernel_ptr(dtype, E, npad, grad, ro, &nt);
   if (!k) return fail(ACE_ERR_UNSUPPORTED, "no kernel for this readout mode");
@@ -539,6 +548,7 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     a.vals = static_cast<const TT*>(dt.vals);
     a.lin = static_cast<const TT*>(dt.lin);
     a.check = checked_mode() ? 1 : 0;
+    a.stage = stage ? 1 : 0;
     a.status = d->status;
   };
   if (dtype == ACE_F32) {

@@ -62,6 +62,7 @@ struct FusedArgs {
   const T* vals;  // [entries][NOUT]
   const T* lin;   // [tasks][NOUT] row coefficient of each task (first task of a basis row), else 0
   int32_t check;
+  int32_t stage;  // 1: bulk-copy staging of the next tile's A (needs 16-byte aligned A)
   uint32_t* status;
 };
 
@@ -94,9 +95,10 @@ struct LoeArgs {
 // AA [n_slots][E] (slot-major: the E values of one slot are one vector load),
 // G [E][gs] (adjoint only, environment-major: the bank of an accumulator is
 // its slot mod 32, gs = n_g rounded up to 32), phibar [E][NOUT], phi partials
-// [warps][E][NOUT] in FP64.
+// [warps][E][NOUT] in FP64, and, when staging is on, the bulk-copy buffer of
+// the next tile's rows of A (E K values + 16 bytes) and its mbarrier.
 struct SmemLayout {
-  size_t g, pb, red, total;
+  size_t g, pb, red, stage, mbar, total;
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -105,13 +107,72 @@ __host__ __device__ inline int g_stride(int n_g) { return (n_g + 31) & ~31; }
 
 
 __host__ __device__ inline SmemLayout smem_layout(int E, int NOUT, bool grad, int n_slots, int n_g, int NT,
-                                                  int tsize) {
+                                                  int tsize, int K, bool stage) {
   SmemLayout L;
   L.g = align16((size_t)n_slots * E * tsize);
   L.pb = L.g + (grad ? align16((size_t)g_stride(n_g) * E * tsize) : 0);
   L.red = L.pb + align16((size_t)E * NOUT * tsize);
-  L.total = L.red + (size_t)(NT / 32) * E * NOUT * sizeof(double);
+  L.stage = align16(L.red + (size_t)(NT / 32) * E * NOUT * sizeof(double));
+  L.mbar = L.stage + (stage ? align16((size_t)E * K * tsize + 16) : 0);
+  L.total = L.mbar + (stage ? 16 : 0);
   return L;
+}
+
+// ---- bulk-copy staging of A (cp.async.bulk, completion on an mbarrier) ---------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mb) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mb)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Copy the 16-byte aligned window [a0, a1) of the tile's bytes of A into the
+// staging buffer (a1 - a0 may be 0: the barrier phase then completes by the
+// arrival alone).  Called by one thread.
+__device__ __forceinline__ void stage_issue(uint64_t* mb, void* buf, const unsigned char* src, uint32_t bytes) {
+  const uint32_t m = smem_u32(mb);
+  if (bytes > 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(buf)), "l"(src), "r"(bytes), "r"(m) : "memory");
+  } else {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(m) : "memory");
+  }
+}
+
+// Wait for the completion of phase `parity`, for at most about a second of
+// SM clocks; returns false on time-out.
+__device__ __forceinline__ bool stage_wait(uint64_t* mb, uint32_t parity) {
+  const uint32_t m = smem_u32(mb);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(m), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 2000000000LL) return false;
+  }
+}
+
+// Byte window of a tile's rows of A: [b0, b1) exactly, of which [b0 & ~15, b1 & ~15) is bulk-copied.
+struct StageWindow {
+  int64_t b0, b1, a0, a1;
+};
+__device__ __forceinline__ StageWindow stage_window(int64_t env0, int64_t n_env, int E, int K, int tsize) {
+  const int64_t n_here = (n_env - env0) < E ? (n_env - env0) : E;
+  StageWindow w;
+  w.b0 = env0 * K * tsize;
+  w.b1 = w.b0 + n_here * K * tsize;
+  w.a0 = w.b0 & ~(int64_t)15;
+  w.a1 = w.b1 & ~(int64_t)15;
+  if (w.a1 < w.a0) w.a1 = w.a0;
+  return w;
 }
 
 // Fused multiply-add in the arithmetic type T (no implicit conversions: a call
@@ -520,22 +581,61 @@ template <typename T, int E, int NOUT, bool GRAD, int RO, int NT>
 __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NW = NT / 32;
-  const SmemLayout L = smem_layout(E, NOUT, GRAD, a.n_slots, a.n_g, NT, (int)sizeof(T));
+  const SmemLayout L = smem_layout(E, NOUT, GRAD, a.n_slots, a.n_g, NT, (int)sizeof(T), a.K, a.stage != 0);
   T* AA = reinterpret_cast<T*>(smem_raw);
   T* G = reinterpret_cast<T*>(smem_raw + L.g);
   T* pb = reinterpret_cast<T*>(smem_raw + L.pb);
   double* red = reinterpret_cast<double*>(smem_raw + L.red);
+  T* sbuf = reinterpret_cast<T*>(smem_raw + L.stage);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int K = a.K;
+  const unsigned char* Abytes = reinterpret_cast<const unsigned char*>(a.A);
+  // The rows of A of a CTA's next tile are bulk-copied into the staging buffer
+  // while the current tile computes.
+  bool stage = a.stage != 0;
+  uint32_t parity = 0, stale = 0xffffffffu;  // stale: parity of a copy that timed out
+  if (stage) {
+    if (tid == 0) {
+      mbar_init(mbar);
+      if (blockIdx.x < a.n_tiles) {
+        const StageWindow w = stage_window((int64_t)blockIdx.x * E, a.n_env, E, K, (int)sizeof(T));
+        stage_issue(mbar, sbuf, Abytes + w.a0, (uint32_t)(w.a1 - w.a0));
+      }
+    }
+    __syncthreads();
+  }
 
   for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
     const int64_t env0 = tile * E;
-    // 1. leaves
-    for (int i = tid; i < E * K; i += NT) {
-      const int e = i / K, k = i - e * K;
-      const int64_t env = env0 + e;
-      AA[(size_t)k * E + e] = env < a.n_env ? a.A[env * K + k] : T(0);
+    // 1. leaves (from the staging buffer, the unaligned last bytes from global memory)
+    if (stage) {
+      const bool late = !stage_wait(mbar, parity);
+      if (__syncthreads_or(late)) {  // block-uniform decision
+        if (tid == 0) atomicOr(a.status, kStatusTimeout);
+        stage = false;  // this and later tiles read A directly; the copy is waited for at exit
+        stale = parity;
+      }
+      parity ^= 1u;
+    }
+    if (stage) {
+      const StageWindow w = stage_window(env0, a.n_env, E, K, (int)sizeof(T));
+      const int shift = (int)((w.b0 - w.a0) / (int64_t)sizeof(T));
+      const int in_buf = (int)((w.a1 - w.b0) / (int64_t)sizeof(T));  // tile elements held by the buffer
+      for (int i = tid; i < E * K; i += NT) {
+        const int e = i / K, k = i - e * K;
+        const int64_t env = env0 + e;
+        T v = T(0);
+        if (env < a.n_env) v = i < in_buf ? sbuf[shift + i] : a.A[env * K + k];
+        AA[(size_t)k * E + e] = v;
+      }
+    } else {
+      for (int i = tid; i < E * K; i += NT) {
+        const int e = i / K, k = i - e * K;
+        const int64_t env = env0 + e;
+        AA[(size_t)k * E + e] = env < a.n_env ? a.A[env * K + k] : T(0);
+      }
     }
     if constexpr (GRAD) {
       for (int i = tid; i < a.gs * E; i += NT) G[i] = T(0);
@@ -548,6 +648,12 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
       }
     }
     __syncthreads();
+    // the staging buffer is free again: start the copy of the next tile's rows
+    if (stage && tid == 0 && tile + gridDim.x < a.n_tiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const StageWindow w = stage_window((tile + gridDim.x) * E, a.n_env, E, K, (int)sizeof(T));
+      stage_issue(mbar, sbuf, Abytes + w.a0, (uint32_t)(w.a1 - w.a0));
+    }
     // 2. operand nodes, order ascending (Eq. 4)
     for (int lv = 0; lv < a.n_fwd_levels; ++lv) {
       const int b = a.fwd_off[lv], eidx = a.fwd_off[lv + 1];
@@ -651,6 +757,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
     }
     __syncthreads();
   }
+  if (stale != 0xffffffffu) stage_wait(mbar, stale);  // a copy that timed out: wait once more (bounded)
 }
 
 
