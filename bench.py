@@ -243,14 +243,18 @@ class Step:
         t = torch
         self.c = t.tensor(W.round_to(W.draw_c(dag.spec.deg, w.n_out), "f32"), dtype=t.float32, device=dev)
         self.sets = []
+        self.mu = None
         if w.pooling:
             offsets, P = W.draw_neighbours(w.n_env, rc=w.rc, j_range=w.j_range)
             self.offsets = t.tensor(offsets, device=dev)
             self.n_pairs = P.shape[0]
+            if w.n_species:
+                self.mu = t.tensor(W.round_to(W.draw_species(P.shape[0], w.n_species), "f32"), dtype=t.float32,
+                                   device=dev)
             for i in range(n_sets):
                 Pi = P if i == 0 else P[np.random.default_rng(100 + i).permutation(P.shape[0])]
                 self.sets.append(t.tensor(W.round_to(Pi, "f32"), dtype=t.float32, device=dev))
-            self.in_bytes = P.shape[0] * 12 + (w.n_env + 1) * 8
+            self.in_bytes = P.shape[0] * (16 if w.n_species else 12) + (w.n_env + 1) * 8
             self.out_bytes = w.n_env * 4 + P.shape[0] * 12
         else:
             A = W.round_to(W.draw_A(w.n_env, dag.K, env_scale=w.env_scale), "f32")
@@ -266,7 +270,8 @@ class Step:
         x = self.sets[i % len(self.sets)]
         w = self.w
         if w.pooling:
-            return energy_and_forces(self.dag, x, self.offsets, self.c, w.nmin, w.nmax, w.lmax, w.rc, self.readout)
+            return energy_and_forces(self.dag, x, self.offsets, self.c, w.nmin, w.nmax, w.lmax, w.rc, self.readout,
+                                     mu=self.mu, kmax=w.kmax)
         if w.grad:
             return self.dag.evaluate_grad(x, self.c, None, self.readout)
         return self.dag.evaluate(x, self.c, self.readout), None
@@ -387,7 +392,7 @@ def main():
         kernel_ms = ev0.elapsed_time(ev1) / args.steps
     else:
         from paper_2202_04140_gb300.torch_api import pool_A
-        A_dev = pool_A(step.A0, step.offsets, w.nmin, w.nmax, w.lmax, w.rc)
+        A_dev = pool_A(step.A0, step.offsets, w.nmin, w.nmax, w.lmax, w.rc, step.mu, w.kmax)
         barrier()
         ev0.record(st)
         for i in range(args.steps):
@@ -433,6 +438,7 @@ def main():
         from paper_2202_04140_gb300.torch_api import energy_and_forces
         P_host = step.A0.cpu().pin_memory()
         off_host = step.offsets.cpu().pin_memory()
+        mu_host = step.mu.cpu().pin_memory() if step.mu is not None else None
         F_host = torch.empty_like(P_host).pin_memory()
         phi_host = torch.empty((w.n_env, 1), dtype=torch.float32).pin_memory()
         n_e2e = max(3, min(args.steps, 50))
@@ -440,7 +446,9 @@ def main():
         def e2e_step():
             P = P_host.to(dev, non_blocking=True)
             off = off_host.to(dev, non_blocking=True)
-            phi, F = energy_and_forces(dag, P, off, step.c, w.nmin, w.nmax, w.lmax, w.rc, args.readout)
+            mu = mu_host.to(dev, non_blocking=True) if mu_host is not None else None
+            phi, F = energy_and_forces(dag, P, off, step.c, w.nmin, w.nmax, w.lmax, w.rc, args.readout, mu=mu,
+                                       kmax=w.kmax)
             F_host.copy_(F, non_blocking=True)
             phi_host.copy_(phi, non_blocking=True)
 

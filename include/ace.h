@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define ACE_ABI_VERSION 1
+#define ACE_ABI_VERSION 2
 
 typedef enum {
   ACE_OK = 0,
@@ -67,6 +67,10 @@ typedef struct ace_dag ace_dag;   /* the graph G and its device plan (library-ow
 /* Index-set parameters (sections 2.2-2.5, Eq. 3, with p = 1 on the evaluated path).
  *  O(3):  k = (n, l, m), nmin <= n <= nmax, 0 <= l <= lmax, |m| <= l,
  *         degree wn*n + wl*l; invariance sum m = 0 and (if require_l_even) sum l even.
+ *         With invariant features (section "Invariant features", phi_nlmk =
+ *         R_n Y_l^m T_k(mu)): 0 <= k <= kmax, degree wn*n + wl*l + wk*k; the
+ *         one-particle id is ((n - nmin)(kmax+1) + k)(lmax+1)^2 + l^2 + l + m
+ *         (kmax = 0: no feature index).  kmax and wk are ignored by SO(2) and torus.
  *  SO(2): k = (n, m), |m| <= lmax, degree wn*n + wl*|m|; invariance sum m = 0.
  *  Torus: k = m, |m| <= lmax, degree |m|; invariance sum m = 0.
  *  p_norm: 1 (sum of one-particle degrees), 2, or 0 for the maximum.
@@ -80,6 +84,7 @@ typedef struct {
   int32_t wn, wl;
   int32_t p_norm;
   int32_t require_l_even;
+  int32_t kmax, wk;  /* invariant-feature degree range and weight (O(3)); ABI 2 */
 } ace_spec_params;
 
 /* ---- library ---------------------------------------------------------------- */
@@ -254,6 +259,28 @@ ace_status ace_pool_A(const float* pos, const int64_t* offsets, int64_t n_env, i
 ace_status ace_pool_A_grad(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs,
                            float rc, int32_t nmin, int32_t nmax, int32_t lmax, const float* dA,
                            float alpha, float* dpos, void* stream);
+
+/* Pooling with one invariant feature per neighbour (section "Invariant
+ * features", phi_nlmk(r, mu) = R_n(r) Y_l^m(r/|r|) T_k(mu), T_k the Chebyshev
+ * polynomial of degree k, 0 <= k <= kmax):
+ *   A[e][id] = sum_{j in env e} R_n(|r_j|) T_k(mu_j) Y_lm(r_j/|r_j|),
+ *   id = ((n - nmin)(kmax+1) + k)(lmax+1)^2 + l^2 + l + m  (the ids of a spec
+ *   built with the same kmax).
+ *  mu : dev float [n_pairs], feature value of each neighbour (in [-1, 1] for a
+ *       well-conditioned T_k); may be NULL when kmax = 0.
+ *  A  : dev float [n_env][K], K = (nmax-nmin+1)(kmax+1)(lmax+1)^2, written.
+ * Limits: kmax <= 3, (nmax-nmin+1)(kmax+1) <= 16, lmax <= 8 (UNSUPPORTED
+ * beyond).  kmax = 0 is ace_pool_A.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+ace_status ace_pool_A_feat(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env,
+                           int64_t n_pairs, float rc, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax,
+                           float* A, void* stream);
+
+/* Adjoint of ace_pool_A_feat with respect to the positions (the feature is a
+ * label, not a coordinate): dpos[j] = alpha sum_id dA[e(j)][id] T_k(mu_j)
+ * grad_{r_j}(R_n Y_lm)(r_j); alpha = -1 with dA = dphi/dA gives the forces. */
+ace_status ace_pool_A_feat_grad(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env,
+                                int64_t n_pairs, float rc, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax,
+                                const float* dA, float alpha, float* dpos, void* stream);
 
 /* ---- status / utilities --------------------------------------------------------- */
 

@@ -10,12 +10,16 @@ Paper passages followed:
     n + |m| for SO(2), |m| for the torus).
   * section 1 / section 2.6: permutation symmetry, so only sorted tuples
     (multisets) are kept.
+  * section "Invariant features": phi_nlmk(r, mu) = R_n Y_l^m T_k(mu) with the
+    degree l + n + k; the feature index k carries no symmetry charge.
 
 Readings of points the paper leaves open:
   * The one-particle degree is wn*n + wl*l (the paper's n + l is wn = wl = 1;
     the workloads use n + 2l).
   * One-particle ids: O(3) id = (n - nmin)(lmax+1)^2 + l^2 + (l + m), i.e. n
-    outer, then l, then m ascending.  Torus id = m + mmax.  SO(2) id =
+    outer, then l, then m ascending; with invariant features of degree
+    0 <= k <= kmax, id = ((n - nmin)(kmax+1) + k)(lmax+1)^2 + l^2 + (l + m)
+    (n, then k, then l, then m), degree wn*n + wl*l + wk*k.  Torus id = m + mmax.  SO(2) id =
     (n - nmin)(2 mmax + 1) + (m + mmax).
   * A tuple is stored non-decreasing in id; the basis order is (nu, then
     lexicographic on ids).  This one order fixes the coefficient draws and the
@@ -37,19 +41,22 @@ class OneParticleBasis:
     deg: np.ndarray       # (K,) int64 one-particle degree
     m: np.ndarray         # (K,) int64
     l: np.ndarray         # (K,) int64 (zeros outside O(3))
+    k: np.ndarray | None = None  # (K,) int64 invariant-feature degree (None: no feature index)
 
     @property
     def K(self) -> int:
         return int(self.deg.shape[0])
 
 
-def o3_basis(nmin: int, nmax: int, lmax: int, wn: int = 1, wl: int = 1) -> OneParticleBasis:
-    """k = (n, l, m), nmin <= n <= nmax, 0 <= l <= lmax, |m| <= l (section 2.4)."""
-    rows = [(n, l, m) for n in range(nmin, nmax + 1)
+def o3_basis(nmin: int, nmax: int, lmax: int, wn: int = 1, wl: int = 1, kmax: int = 0,
+             wk: int = 1) -> OneParticleBasis:
+    """k = (n, l, m), nmin <= n <= nmax, 0 <= l <= lmax, |m| <= l (section 2.4); with kmax > 0
+    also the invariant-feature degree 0 <= k <= kmax (phi_nlmk, degree wn n + wl l + wk k)."""
+    rows = [(n, l, m, k) for n in range(nmin, nmax + 1) for k in range(kmax + 1)
             for l in range(lmax + 1) for m in range(-l, l + 1)]
     lab = np.array(rows, dtype=np.int64)
-    return OneParticleBasis("O3", lab, wn * lab[:, 0] + wl * lab[:, 1],
-                            lab[:, 2].copy(), lab[:, 1].copy())
+    return OneParticleBasis("O3", lab[:, :3].copy(), wn * lab[:, 0] + wl * lab[:, 1] + wk * lab[:, 3],
+                            lab[:, 2].copy(), lab[:, 1].copy(), lab[:, 3].copy() if kmax > 0 else None)
 
 
 def so2_basis(nmin: int, nmax: int, mmax: int, wn: int = 1, wm: int = 1) -> OneParticleBasis:
@@ -166,6 +173,6 @@ def index_set(basis: OneParticleBasis, nu_max: int, deg_max: int, p: float = 1,
 
 
 def workload_index_set(w) -> IndexSet:
-    """Index set of a ``workloads.Workload`` (O(3), p = 1, degree wn*n + wl*l)."""
-    b = o3_basis(w.nmin, w.nmax, w.lmax, w.wn, w.wl)
+    """Index set of a ``workloads.Workload`` (O(3), p = 1, degree wn*n + wl*l [+ wk*k])."""
+    b = o3_basis(w.nmin, w.nmax, w.lmax, w.wn, w.wl, w.kmax, w.wk)
     return index_set(b, w.nu_max, w.deg_max)

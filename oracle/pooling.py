@@ -18,6 +18,12 @@ uses (readings, applied identically in the GPU path):
     Y_lm = sqrt(2) N_lm Q_lm(z/r) Re/Im((x+iy)^m) r^{-m} with Q_lm = d^m P_l/du^m;
     the gradient below differentiates exactly this product.
   * One-particle id = (n - nmin)(lmax+1)^2 + l^2 + (l + m).
+  * Invariant features (section "Invariant features"): phi_nlmk(r, mu) =
+    R_n(r) Y_l^m(r/|r|) T_k(mu), T_k the Chebyshev polynomial of the first kind
+    (the paper only asks for a polynomial basis of degree k) of the neighbour's
+    feature value mu in [-1, 1]; id = ((n - nmin)(kmax+1) + k)(lmax+1)^2 + l^2 + (l + m).
+    The feature is a label of the neighbour, not a coordinate: forces are
+    derivatives with respect to positions only.
 Forces are F_j = -dphi/dr_j = -sum_k G_k grad(R_n Y_lm)(r_j) with G = dphi/dA.
 """
 from __future__ import annotations
@@ -107,12 +113,36 @@ def radial(r: np.ndarray, nmin: int, nmax: int, rc: float, with_grad: bool = Fal
     return R, dR
 
 
-def one_particle(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float, with_grad: bool = False):
-    """phi_k(r_j) for all neighbours j and one-particle ids k, and grad phi_k (n, K, 3)."""
+def feature_poly(mu: np.ndarray, kmax: int) -> np.ndarray:
+    """(n, kmax+1): T_k(mu_j), the Chebyshev polynomials of the first kind."""
+    mu = np.asarray(mu, dtype=np.float64)
+    out = np.zeros((mu.shape[0], kmax + 1))
+    for k in range(kmax + 1):
+        coef = np.zeros(k + 1)
+        coef[k] = 1.0
+        out[:, k] = C.chebval(mu, coef)
+    return out
+
+
+def _with_features(R, dR, mu, kmax):
+    """Radial factors R_n -> R_n T_k(mu_j) in (n, k) order (and their r-derivatives)."""
+    if mu is None:
+        return R, dR
+    T = feature_poly(mu, kmax)
+    RF = (R[:, :, None] * T[:, None, :]).reshape(R.shape[0], -1)
+    dRF = None if dR is None else (dR[:, :, None] * T[:, None, :]).reshape(R.shape[0], -1)
+    return RF, dRF
+
+
+def one_particle(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float, with_grad: bool = False,
+                 mu: np.ndarray | None = None, kmax: int = 0):
+    """phi_k(r_j) for all neighbours j and one-particle ids k, and grad phi_k (n, K, 3).
+    With mu (one feature value per neighbour) the ids include the feature degree k <= kmax."""
     P = np.asarray(P, dtype=np.float64)
     r = np.linalg.norm(P, axis=1)
     Y, dY = real_sph_harm(P, lmax, with_grad)
     R, dR = radial(r, nmin, nmax, rc, with_grad)
+    R, dR = _with_features(R, dR, mu, kmax)
     nR, nL = R.shape[1], Y.shape[1]
     phi = (R[:, :, None] * Y[:, None, :]).reshape(P.shape[0], nR * nL)
     if not with_grad:
@@ -123,7 +153,8 @@ def one_particle(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float, with
     return phi, g.reshape(P.shape[0], nR * nL, 3)
 
 
-def one_particle_grad_bound(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float) -> np.ndarray:
+def one_particle_grad_bound(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float,
+                            mu: np.ndarray | None = None, kmax: int = 0) -> np.ndarray:
     """(n, K, 3): grad phi_k written as in ``one_particle`` with every product term in absolute value.
 
     Used as the scale of the force error: |F_hat - F| / sum_k |G_k| bound_k is the
@@ -133,16 +164,21 @@ def one_particle_grad_bound(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: 
     r = np.linalg.norm(P, axis=1)
     Y, dYb = real_sph_harm(P, lmax, True, bound=True)
     R, dRb = radial(r, nmin, nmax, rc, True, bound=True)
+    if mu is not None:
+        T = np.abs(feature_poly(mu, kmax))
+        R = (R[:, :, None] * T[:, None, :]).reshape(R.shape[0], -1)
+        dRb = (dRb[:, :, None] * T[:, None, :]).reshape(dRb.shape[0], -1)
     rhat = np.abs(P / r[:, None])
     g = (dRb[:, :, None, None] * np.abs(Y)[:, None, :, None] * rhat[:, None, None, :]
          + np.abs(R)[:, :, None, None] * dYb[:, None, :, :])
     return g.reshape(P.shape[0], R.shape[1] * Y.shape[1], 3)
 
 
-def pool_A(P: np.ndarray, offsets: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float) -> np.ndarray:
+def pool_A(P: np.ndarray, offsets: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float,
+           mu: np.ndarray | None = None, kmax: int = 0) -> np.ndarray:
     """A[e, k] = sum over the neighbours j of environment e of phi_k(r_j) (Eq. 2)."""
     offsets = np.asarray(offsets, dtype=np.int64)
-    phi, _ = one_particle(P, nmin, nmax, lmax, rc)
+    phi, _ = one_particle(P, nmin, nmax, lmax, rc, mu=mu, kmax=kmax)
     A = np.zeros((offsets.shape[0] - 1, phi.shape[1]))
     for e in range(A.shape[0]):
         A[e] = phi[offsets[e]:offsets[e + 1]].sum(axis=0)
@@ -150,10 +186,10 @@ def pool_A(P: np.ndarray, offsets: np.ndarray, nmin: int, nmax: int, lmax: int, 
 
 
 def forces(P: np.ndarray, offsets: np.ndarray, G: np.ndarray, nmin: int, nmax: int, lmax: int,
-           rc: float) -> np.ndarray:
+           rc: float, mu: np.ndarray | None = None, kmax: int = 0) -> np.ndarray:
     """F_j = -sum_k G[e(j), k] grad phi_k(r_j), with G = dphi/dA of the environment of j."""
     offsets = np.asarray(offsets, dtype=np.int64)
-    _, g = one_particle(P, nmin, nmax, lmax, rc, with_grad=True)
+    _, g = one_particle(P, nmin, nmax, lmax, rc, with_grad=True, mu=mu, kmax=kmax)
     F = np.zeros((P.shape[0], 3))
     for e in range(offsets.shape[0] - 1):
         a, b = offsets[e], offsets[e + 1]

@@ -32,7 +32,7 @@ EXPORTED = [
     "ace_last_error", "ace_abi_version", "ace_build_spec", "ace_spec_info", "ace_spec_tuples",
     "ace_spec_free", "ace_build_dag", "ace_dag_info", "ace_dag_export", "ace_dag_plan_info",
     "ace_dag_plan_array", "ace_dag_free", "ace_dag_upload", "ace_dag_autotune", "ace_eval", "ace_eval_grad", "ace_eval_plain_workspace_bytes",
-    "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_stream_status", "ace_device_info",
+    "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_pool_A_feat", "ace_pool_A_feat_grad", "ace_stream_status", "ace_device_info",
     "ace_fma_peak",
 ]
 
@@ -46,7 +46,7 @@ class AceError(RuntimeError):
 class ace_spec_params(C.Structure):
     _fields_ = [("group", C.c_int32), ("nmin", C.c_int32), ("nmax", C.c_int32), ("lmax", C.c_int32),
                 ("nu_max", C.c_int32), ("deg_max", C.c_int32), ("wn", C.c_int32), ("wl", C.c_int32),
-                ("p_norm", C.c_int32), ("require_l_even", C.c_int32)]
+                ("p_norm", C.c_int32), ("require_l_even", C.c_int32), ("kmax", C.c_int32), ("wk", C.c_int32)]
 
 
 if not os.path.exists(_LIB_PATH):
@@ -77,6 +77,8 @@ _SIG = {
     "ace_eval_plain_f64_static": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _p, _p, _p]),
     "ace_pool_A": (C.c_int, [_p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _p, _p]),
     "ace_pool_A_grad": (C.c_int, [_p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _p, _f32, _p, _p]),
+    "ace_pool_A_feat": (C.c_int, [_p, _p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _i32, _p, _p]),
+    "ace_pool_A_feat_grad": (C.c_int, [_p, _p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _i32, _p, _f32, _p, _p]),
     "ace_stream_status": (C.c_int, [_p, _p]),
     "ace_device_info": (C.c_int, [_P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
     "ace_fma_peak": (C.c_int, [_i64, _P(C.c_double), _P(C.c_double), _p]),
@@ -107,8 +109,8 @@ def ace_abi_version() -> int:
 # ---- index set ---------------------------------------------------------------------------
 
 def ace_build_spec(group=ACE_GROUP_O3, nmin=1, nmax=1, lmax=0, nu_max=1, deg_max=0, wn=1, wl=1, p_norm=1,
-                   require_l_even=1) -> int:
-    prm = ace_spec_params(group, nmin, nmax, lmax, nu_max, deg_max, wn, wl, p_norm, require_l_even)
+                   require_l_even=1, kmax=0, wk=1) -> int:
+    prm = ace_spec_params(group, nmin, nmax, lmax, nu_max, deg_max, wn, wl, p_norm, require_l_even, kmax, wk)
     h = C.c_void_p()
     _check(_lib.ace_build_spec(C.byref(prm), C.byref(h)), "ace_build_spec")
     return h.value
@@ -223,6 +225,16 @@ def ace_pool_A(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, A, stream=0):
 def ace_pool_A_grad(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, dA, alpha, dpos, stream=0):
     _check(_lib.ace_pool_A_grad(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, dA, alpha, dpos, stream),
            "ace_pool_A_grad")
+
+
+def ace_pool_A_feat(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax, A, stream=0):
+    _check(_lib.ace_pool_A_feat(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax, A, stream),
+           "ace_pool_A_feat")
+
+
+def ace_pool_A_feat_grad(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax, dA, alpha, dpos, stream=0):
+    _check(_lib.ace_pool_A_feat_grad(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax, dA, alpha, dpos,
+                                     stream), "ace_pool_A_feat_grad")
 
 
 def ace_stream_status(dag, stream=0) -> int:

@@ -939,39 +939,57 @@ ace_status ace_eval_plain_f64_static(ace_dag* dag, const double* A, const double
 }
 
 static ace_status check_pool_args(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
-                                  int32_t nmin, int32_t nmax, int32_t lmax) {
+                                  int32_t nmin, int32_t nmax, int32_t lmax, const float* mu, int32_t kmax) {
   if (n_env < 0 || n_pairs < 0) return fail(ACE_ERR_INVALID_ARG, "sizes must be >= 0");
   if (!offsets && n_env > 0) return fail(ACE_ERR_INVALID_ARG, "offsets is NULL");
   if (!pos && n_pairs > 0) return fail(ACE_ERR_INVALID_ARG, "pos is NULL");
   if (!(rc > 0.f)) return fail(ACE_ERR_INVALID_ARG, "rc must be > 0");
   if (nmin < 0 || nmax < nmin) return fail(ACE_ERR_INVALID_ARG, "need 0 <= nmin <= nmax");
-  if (nmax - nmin + 1 > 16) return fail(ACE_ERR_UNSUPPORTED, "at most 16 radial functions");
+  if (kmax < 0) return fail(ACE_ERR_INVALID_ARG, "kmax must be >= 0");
+  if (kmax > 3) return fail(ACE_ERR_UNSUPPORTED, "feature degree kmax > 3 is not compiled");
+  if (kmax > 0 && !mu && n_pairs > 0) return fail(ACE_ERR_INVALID_ARG, "mu is NULL while kmax > 0");
+  if ((nmax - nmin + 1) * (kmax + 1) > 16)
+    return fail(ACE_ERR_UNSUPPORTED, "at most 16 radial x feature functions per neighbour");
   if (lmax < 0) return fail(ACE_ERR_INVALID_ARG, "lmax must be >= 0");
   if (lmax > 8) return fail(ACE_ERR_UNSUPPORTED, "lmax > 8 is not compiled");
   return ACE_OK;
 }
 
-ace_status ace_pool_A(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
-                      int32_t nmin, int32_t nmax, int32_t lmax, float* A, void* stream) {
-  ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax);
+ace_status ace_pool_A_feat(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, int64_t n_pairs,
+                           float rc, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax, float* A, void* stream) {
+  ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, mu, kmax);
   if (s != ACE_OK) return s;
   if (n_env == 0) return ACE_OK;
   if (!A) return fail(ACE_ERR_INVALID_ARG, "A is NULL");
-  cudaError_t e = launch_pool(pos, offsets, n_env, rc, nmin, nmax, lmax, A, (cudaStream_t)stream);
+  cudaError_t e = launch_pool(pos, kmax > 0 ? mu : nullptr, offsets, n_env, rc, nmin, nmax, lmax, kmax, A,
+                              (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "pooling kernel launch");
   return ACE_OK;
+}
+
+ace_status ace_pool_A_feat_grad(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env,
+                                int64_t n_pairs, float rc, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax,
+                                const float* dA, float alpha, float* dpos, void* stream) {
+  ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, mu, kmax);
+  if (s != ACE_OK) return s;
+  if (n_env == 0) return ACE_OK;
+  if (!dA || (!dpos && n_pairs > 0)) return fail(ACE_ERR_INVALID_ARG, "dA or dpos is NULL");
+  cudaError_t e = launch_pool_grad(pos, kmax > 0 ? mu : nullptr, offsets, n_env, rc, nmin, nmax, lmax, kmax, dA,
+                                   alpha, dpos, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pooling adjoint launch");
+  return ACE_OK;
+}
+
+ace_status ace_pool_A(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
+                      int32_t nmin, int32_t nmax, int32_t lmax, float* A, void* stream) {
+  return ace_pool_A_feat(pos, nullptr, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, 0, A, stream);
 }
 
 ace_status ace_pool_A_grad(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
                            int32_t nmin, int32_t nmax, int32_t lmax, const float* dA, float alpha, float* dpos,
                            void* stream) {
-  ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax);
-  if (s != ACE_OK) return s;
-  if (n_env == 0) return ACE_OK;
-  if (!dA || (!dpos && n_pairs > 0)) return fail(ACE_ERR_INVALID_ARG, "dA or dpos is NULL");
-  cudaError_t e = launch_pool_grad(pos, offsets, n_env, rc, nmin, nmax, lmax, dA, alpha, dpos, (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "pooling adjoint launch");
-  return ACE_OK;
+  return ace_pool_A_feat_grad(pos, nullptr, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, 0, dA, alpha, dpos,
+                              stream);
 }
 
 ace_status ace_stream_status(ace_dag* dag, void* stream) {

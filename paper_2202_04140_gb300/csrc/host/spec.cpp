@@ -81,14 +81,17 @@ ace_status build_spec(const ace_spec_params& p, std::unique_ptr<Spec>& out) {
   s->nu_max = p.nu_max;
   if (p.group == ACE_GROUP_O3) {
     if (p.nmin < 0 || p.nmax < p.nmin) return fail(ACE_ERR_INVALID_ARG, "need 0 <= nmin <= nmax");
-    if (p.wn < 0 || p.wl < 0) return fail(ACE_ERR_INVALID_ARG, "degree weights must be >= 0");
+    if (p.wn < 0 || p.wl < 0 || p.wk < 0) return fail(ACE_ERR_INVALID_ARG, "degree weights must be >= 0");
+    if (p.kmax < 0) return fail(ACE_ERR_INVALID_ARG, "kmax must be >= 0");
+    // id order: n, then the feature degree k, then l, then m
     for (int32_t n = p.nmin; n <= p.nmax; ++n)
-      for (int32_t l = 0; l <= p.lmax; ++l)
-        for (int32_t m = -l; m <= l; ++m) {
-          s->one_deg.push_back(p.wn * n + p.wl * l);
-          s->one_m.push_back(m);
-          s->one_l.push_back(l);
-        }
+      for (int32_t k = 0; k <= p.kmax; ++k)
+        for (int32_t l = 0; l <= p.lmax; ++l)
+          for (int32_t m = -l; m <= l; ++m) {
+            s->one_deg.push_back(p.wn * n + p.wl * l + p.wk * k);
+            s->one_m.push_back(m);
+            s->one_l.push_back(l);
+          }
   } else if (p.group == ACE_GROUP_SO2) {
     if (p.nmin < 0 || p.nmax < p.nmin) return fail(ACE_ERR_INVALID_ARG, "need 0 <= nmin <= nmax");
     for (int32_t n = p.nmin; n <= p.nmax; ++n)

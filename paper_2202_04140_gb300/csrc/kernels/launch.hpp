@@ -34,10 +34,11 @@ cudaError_t static_scratch_ptr(void** out);
 
 cudaError_t launch_fma_probe(int64_t iters, int blocks, int threads, float* out, cudaStream_t st);
 
-cudaError_t launch_pool(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
-                        int lmax, float* A, cudaStream_t st);
+cudaError_t launch_pool(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, float rc, int nmin,
+                        int nmax, int lmax, int kmax, float* A, cudaStream_t st);
 
-cudaError_t launch_pool_grad(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
-                             int lmax, const float* dA, float alpha, float* dpos, cudaStream_t st);
+cudaError_t launch_pool_grad(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, float rc,
+                             int nmin, int nmax, int lmax, int kmax, const float* dA, float alpha, float* dpos,
+                             cudaStream_t st);
 
 }  // namespace ace

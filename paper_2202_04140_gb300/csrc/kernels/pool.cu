@@ -10,6 +10,10 @@
 //   (l-m) Q_l^m = (2l-1) u Q_{l-1}^m - (l+m-1) Q_{l-2}^m.  This is the real
 //   orthonormal harmonic without Condon-Shortley phase, evaluated from the
 //   Cartesian direction (no angles).
+// Invariant features (phi_nlmk = R_n Y_l^m T_k(mu), section "Invariant
+// features"): the radial factor becomes R_n(r) T_k(mu_j) with T_k the Chebyshev
+// polynomial of the neighbour's feature value, radial-feature index
+// q = (n - nmin)(kmax+1) + k, one-particle id q (lmax+1)^2 + l^2 + l + m.
 // Gradients treat Y as a polynomial in the unit vector (xh, yh, zh):
 //   dY/dxh = K Q m C_{m-1} (cos) or K Q m S_{m-1} (sin),
 //   dY/dyh = -K Q m S_{m-1} (cos) or K Q m C_{m-1} (sin),
@@ -26,7 +30,8 @@ namespace dev {
 
 constexpr int kPoolLmax = 8;
 constexpr int kPoolNL = (kPoolLmax + 1) * (kPoolLmax + 1);
-constexpr int kPoolMaxR = 16;
+constexpr int kPoolMaxR = 16;  // radial x feature factors per neighbour
+constexpr int kPoolMaxF = 4;   // feature degrees 0..3
 constexpr int kPoolQ = (kPoolLmax + 2) * (kPoolLmax + 3) / 2;  // Q_l^m for 0 <= m <= l+1 <= lmax+1
 constexpr int kPoolWarps = 4;
 constexpr int kPoolChunk = 32;  // neighbours staged per pass
@@ -78,16 +83,27 @@ __device__ __forceinline__ void legendre_q(float u, float (&Q)[kPoolQ]) {
 
 // A: one warp per environment; lanes compute R and Y of one neighbour each into
 // shared memory, then lane owns lm = lane + 32 i for all radial n.
+// T_k(mu) for k < kf (<= kPoolMaxF), T_0 = 1, T_1 = mu, T_{k+1} = 2 mu T_k - T_{k-1}.
+__device__ __forceinline__ void feature_poly(float mu, int kf, float (&Tf)[kPoolMaxF]) {
+  Tf[0] = 1.f;
+#pragma unroll
+  for (int k = 1; k < kPoolMaxF; ++k) Tf[k] = k == 1 ? mu : 2.f * mu * Tf[k - 1] - Tf[k - 2];
+  (void)kf;
+}
+
 template <int LMAX>
 __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __restrict__ pos,
+                                                               const float* __restrict__ mu,
                                                                const int64_t* __restrict__ offsets, int64_t n_env,
-                                                               float rc, int nmin, int nmax, float* __restrict__ A) {
+                                                               float rc, int nmin, int nmax, int kf,
+                                                               float* __restrict__ A) {
   constexpr int NL = (LMAX + 1) * (LMAX + 1);
   constexpr int NI = (NL + 31) / 32;
   __shared__ float sR[kPoolWarps][kPoolChunk][kPoolMaxR];
   __shared__ float sY[kPoolWarps][kPoolChunk][NL];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nR = nmax - nmin + 1;
+  const int nR0 = nmax - nmin + 1;
+  const int nR = nR0 * kf;  // radial x feature factors
   const int K = nR * NL;
   for (int64_t env = blockIdx.x * (int64_t)kPoolWarps + warp; env < n_env; env += (int64_t)gridDim.x * kPoolWarps) {
     float acc[NI][kPoolMaxR];
@@ -114,6 +130,16 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
           T = Tn;
         }
         if (nmin == 0) sR[warp][lane][0] = env2;
+        if (kf > 1) {  // expand R_n into R_n T_k(mu_j), in place from the last factor down
+          float Tf[kPoolMaxF];
+          feature_poly(mu[j], kf, Tf);
+          for (int i = nR0 - 1; i >= 0; --i) {
+            const float rn = sR[warp][lane][i];
+#pragma unroll
+            for (int k = kPoolMaxF - 1; k >= 0; --k)
+              if (k < kf) sR[warp][lane][i * kf + k] = rn * Tf[k];
+          }
+        }
         float Q[kPoolQ];
         legendre_q<LMAX>(u, Q);
         float C = 1.f, S = 0.f;
@@ -166,15 +192,16 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
 // Adjoint: one warp per environment, one lane per neighbour.
 template <int LMAX>
 __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float* __restrict__ pos,
+                                                                    const float* __restrict__ mu,
                                                                     const int64_t* __restrict__ offsets,
                                                                     int64_t n_env, float rc, int nmin, int nmax,
-                                                                    const float* __restrict__ dA, float alpha,
-                                                                    float* __restrict__ dpos) {
+                                                                    int kf, const float* __restrict__ dA,
+                                                                    float alpha, float* __restrict__ dpos) {
   constexpr int NL = (LMAX + 1) * (LMAX + 1);
   __shared__ float sG[kPoolWarps][kPoolMaxR * NL];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nR = nmax - nmin + 1;
-  const int K = nR * NL;
+  const int K = nR * kf * NL;
   for (int64_t env = blockIdx.x * (int64_t)kPoolWarps + warp; env < n_env; env += (int64_t)gridDim.x * kPoolWarps) {
     __syncwarp();
     for (int i = lane; i < K; i += 32) sG[warp][i] = dA[env * K + i];
@@ -215,6 +242,8 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
           dT = dTn;
         }
       }
+      float Tf[kPoolMaxF];
+      feature_poly(kf > 1 ? mu[j] : 0.f, kf, Tf);
       float Q[kPoolQ];
       legendre_q<LMAX>(u, Q);
       float gx = 0.f, gy = 0.f, gz = 0.f, ys = 0.f;
@@ -228,11 +257,20 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
           const int base = l * l + l;
           float h = 0.f, hd = 0.f, h2 = 0.f, hd2 = 0.f;
           for (int n = 0; n < nR; ++n) {
-            const float ga = sG[warp][n * NL + base + m];
+            // dA of (n, l, m) summed over the feature degrees with weights T_k(mu_j)
+            float ga = sG[warp][n * kf * NL + base + m];
+            float gb = m > 0 ? sG[warp][n * kf * NL + base - m] : 0.f;
+            if (kf > 1) {
+#pragma unroll
+              for (int k = 1; k < kPoolMaxF; ++k)
+                if (k < kf) {
+                  ga = __fmaf_rn(sG[warp][(n * kf + k) * NL + base + m], Tf[k], ga);
+                  if (m > 0) gb = __fmaf_rn(sG[warp][(n * kf + k) * NL + base - m], Tf[k], gb);
+                }
+            }
             h = __fmaf_rn(ga, R[n], h);
             hd = __fmaf_rn(ga, dR[n], hd);
             if (m > 0) {
-              const float gb = sG[warp][n * NL + base - m];
               h2 = __fmaf_rn(gb, R[n], h2);
               hd2 = __fmaf_rn(gb, dR[n], hd2);
             }
@@ -330,21 +368,24 @@ int pool_grid(int64_t n_env) {
     default: return cudaErrorInvalidValue;                                                          \
   }
 
-cudaError_t launch_pool(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
-                        int lmax, float* A, cudaStream_t st) {
+cudaError_t launch_pool(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, float rc, int nmin,
+                        int nmax, int lmax, int kmax, float* A, cudaStream_t st) {
   cudaError_t e = ensure_pool_constants();
   if (e != cudaSuccess) return e;
   const int grid = pool_grid(n_env);
-  ACE_POOL_DISPATCH(pool_kernel, pos, offsets, n_env, rc, nmin, nmax, A)
+  const int kf = kmax + 1;
+  ACE_POOL_DISPATCH(pool_kernel, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A)
   return cudaGetLastError();
 }
 
-cudaError_t launch_pool_grad(const float* pos, const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax,
-                             int lmax, const float* dA, float alpha, float* dpos, cudaStream_t st) {
+cudaError_t launch_pool_grad(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, float rc,
+                             int nmin, int nmax, int lmax, int kmax, const float* dA, float alpha, float* dpos,
+                             cudaStream_t st) {
   cudaError_t e = ensure_pool_constants();
   if (e != cudaSuccess) return e;
   const int grid = pool_grid(n_env);
-  ACE_POOL_DISPATCH(pool_grad_kernel, pos, offsets, n_env, rc, nmin, nmax, dA, alpha, dpos)
+  const int kf = kmax + 1;
+  ACE_POOL_DISPATCH(pool_grad_kernel, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos)
   return cudaGetLastError();
 }
 

@@ -34,17 +34,17 @@ class Spec:
     """The index set K (sections 2.2-2.5, Eq. 3), built by libace."""
 
     def __init__(self, group="O3", nmin=1, nmax=1, lmax=0, nu_max=1, deg_max=0, wn=1, wl=1, p_norm=1,
-                 require_l_even=True):
+                 require_l_even=True, kmax=0, wk=1):
         self.group = group
         self.nu_max = nu_max
         self.handle = L.ace_build_spec(_GROUP[group], nmin, nmax, lmax, nu_max, deg_max, wn, wl, p_norm,
-                                       int(require_l_even))
+                                       int(require_l_even), kmax, wk)
         self.n_basis, self.K, self.counts_per_nu = L.ace_spec_info(self.handle, nu_max)
         self._tuples = None
 
     @classmethod
     def from_workload(cls, w) -> "Spec":
-        return cls("O3", w.nmin, w.nmax, w.lmax, w.nu_max, w.deg_max, w.wn, w.wl, 1, True)
+        return cls("O3", w.nmin, w.nmax, w.lmax, w.nu_max, w.deg_max, w.wn, w.wl, 1, True, w.kmax, w.wk)
 
     def tuples(self):
         if self._tuples is None:
@@ -181,35 +181,39 @@ class _AceEnergy(torch.autograd.Function):
         return dA, None, None, None
 
 
-def pool_A(pos: torch.Tensor, offsets: torch.Tensor, nmin: int, nmax: int, lmax: int, rc: float) -> torch.Tensor:
-    """A[e][id(n,l,m)] = sum_{j in e} R_n(|r_j|) Y_lm(r_j/|r_j|) on the GPU."""
+def pool_A(pos: torch.Tensor, offsets: torch.Tensor, nmin: int, nmax: int, lmax: int, rc: float,
+           mu: torch.Tensor | None = None, kmax: int = 0) -> torch.Tensor:
+    """A[e][id(n,[k,]l,m)] = sum_{j in e} R_n(|r_j|) [T_k(mu_j)] Y_lm(r_j/|r_j|) on the GPU."""
     pos = _dev(pos, "pos", torch.float32)
     offsets = _dev(offsets, "offsets", torch.int64)
+    mu_p = _dev(mu, "mu", torch.float32).data_ptr() if mu is not None else 0
     n_env = offsets.numel() - 1
-    K = (nmax - nmin + 1) * (lmax + 1) ** 2
+    K = (nmax - nmin + 1) * (kmax + 1) * (lmax + 1) ** 2
     A = torch.empty((n_env, K), dtype=torch.float32, device=pos.device)
-    L.ace_pool_A(pos.data_ptr(), offsets.data_ptr(), n_env, pos.shape[0], rc, nmin, nmax, lmax, A.data_ptr(),
-                 _stream())
+    L.ace_pool_A_feat(pos.data_ptr(), mu_p, offsets.data_ptr(), n_env, pos.shape[0], rc, nmin, nmax, lmax, kmax,
+                      A.data_ptr(), _stream())
     return A
 
 
 def pool_A_grad(pos: torch.Tensor, offsets: torch.Tensor, dA: torch.Tensor, nmin: int, nmax: int, lmax: int,
-                rc: float, alpha: float = 1.0) -> torch.Tensor:
-    """dpos[j] = alpha sum_k dA[e(j)][k] grad (R_n Y_lm)(r_j); alpha = -1 with dA = dphi/dA gives the forces."""
+                rc: float, alpha: float = 1.0, mu: torch.Tensor | None = None, kmax: int = 0) -> torch.Tensor:
+    """dpos[j] = alpha sum_k dA[e(j)][k] grad phi_k(r_j); alpha = -1 with dA = dphi/dA gives the forces."""
     pos = _dev(pos, "pos", torch.float32)
     offsets = _dev(offsets, "offsets", torch.int64)
     dA = _dev(dA, "dA", torch.float32)
+    mu_p = _dev(mu, "mu", torch.float32).data_ptr() if mu is not None else 0
     n_env = offsets.numel() - 1
     dpos = torch.empty_like(pos)
-    L.ace_pool_A_grad(pos.data_ptr(), offsets.data_ptr(), n_env, pos.shape[0], rc, nmin, nmax, lmax,
-                      dA.data_ptr(), alpha, dpos.data_ptr(), _stream())
+    L.ace_pool_A_feat_grad(pos.data_ptr(), mu_p, offsets.data_ptr(), n_env, pos.shape[0], rc, nmin, nmax, lmax, kmax,
+                           dA.data_ptr(), alpha, dpos.data_ptr(), _stream())
     return dpos
 
 
 def energy_and_forces(dag: Dag, pos: torch.Tensor, offsets: torch.Tensor, c: torch.Tensor, nmin: int, nmax: int,
-                      lmax: int, rc: float, readout: str = "plain"):
-    """Full pipeline: pooling -> fused forward+adjoint -> pooling adjoint.  Returns (phi, F = -dphi/dr)."""
-    A = pool_A(pos, offsets, nmin, nmax, lmax, rc)
+                      lmax: int, rc: float, readout: str = "plain", mu: torch.Tensor | None = None, kmax: int = 0):
+    """Full pipeline: pooling -> fused forward+adjoint -> pooling adjoint.  Returns (phi, F = -dphi/dr).
+    With mu (one invariant feature value per neighbour) the one-particle basis is R_n Y_lm T_k(mu)."""
+    A = pool_A(pos, offsets, nmin, nmax, lmax, rc, mu, kmax)
     phi, dA = dag.evaluate_grad(A, c, None, readout)
-    F = pool_A_grad(pos, offsets, dA, nmin, nmax, lmax, rc, alpha=-1.0)
+    F = pool_A_grad(pos, offsets, dA, nmin, nmax, lmax, rc, alpha=-1.0, mu=mu, kmax=kmax)
     return phi, F

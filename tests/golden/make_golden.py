@@ -43,7 +43,7 @@ def dag_digest(d) -> str:
 
 def main():
     out = {}
-    for name in ["plain_fp64_k64", "fwd_grad_k392", "uneven_16ch_k392", "stress_k810"]:
+    for name in ["plain_fp64_k64", "fwd_grad_k392", "uneven_16ch_k392", "stress_k810", "species_forces_k375"]:
         w = W.WORKLOADS[name]
         t0 = time.time()
         s = workload_index_set(w)

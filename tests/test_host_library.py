@@ -34,13 +34,13 @@ def test_library_exports_every_declared_symbol():
     for n in names:
         assert hasattr(L._lib, n), n
     assert sorted(L.EXPORTED) == names
-    assert L.ace_abi_version() == 1
+    assert L.ace_abi_version() == 2
 
 
 def spec_of(basis_kind, **kw):
     if basis_kind == "O3":
         return Spec("O3", kw["nmin"], kw["nmax"], kw["lmax"], kw["nu"], kw["D"], kw["wn"], kw["wl"],
-                    kw.get("p", 1), True)
+                    kw.get("p", 1), True, kw.get("kmax", 0), kw.get("wk", 1))
     if basis_kind == "SO2":
         return Spec("SO2", kw["nmin"], kw["nmax"], kw["mmax"], kw["nu"], kw["D"], 1, 1, 1, False)
     return Spec("T", 0, 0, kw["mmax"], kw["nu"], kw["D"], 1, 1, 1, False)
@@ -51,6 +51,8 @@ CASES = [
     ("O3", dict(nmin=1, nmax=3, lmax=3, nu=4, D=9, wn=1, wl=1), lambda: o3_basis(1, 3, 3, 1, 1)),
     ("O3", dict(nmin=1, nmax=3, lmax=2, nu=3, D=5, wn=1, wl=1, p=2), lambda: o3_basis(1, 3, 2, 1, 1)),
     ("O3", dict(nmin=1, nmax=3, lmax=2, nu=3, D=3, wn=1, wl=1, p=0), lambda: o3_basis(1, 3, 2, 1, 1)),
+    ("O3", dict(nmin=1, nmax=3, lmax=2, nu=4, D=7, wn=1, wl=1, kmax=2, wk=1),
+     lambda: o3_basis(1, 3, 2, 1, 1, kmax=2, wk=1)),
     ("SO2", dict(nmin=1, nmax=3, mmax=4, nu=4, D=8), lambda: so2_basis(1, 3, 4)),
     ("T", dict(mmax=10, nu=5, D=10), lambda: torus_basis(10)),
 ]

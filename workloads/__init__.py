@@ -17,6 +17,8 @@ Recipe (all draws are numpy PCG64 `default_rng(seed)`):
                 directions (normalised standard normals, 3 per neighbour), then
                 all radii r = rc * U^(1/3) (uniform in the ball), in that order.
                 A radius below 1e-6 is redrawn (probability ~1e-19 per draw).
+  * species   : seed 4.  s_j ~ U{0..S-1} per neighbour; the feature value is
+                mu_j = -1 + 2 s_j / (S - 1) (S species spread over [-1, 1]).
 FP32 workloads round the FP64 draws to FP32 once; the oracle receives the same
 FP32 values promoted to FP64, so input rounding is never counted as error.
 """
@@ -25,7 +27,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field, asdict
 import numpy as np
 
-__all__ = ["Workload", "WORKLOADS", "draw_A", "draw_c", "draw_neighbours",
+__all__ = ["Workload", "WORKLOADS", "draw_A", "draw_c", "draw_neighbours", "draw_species",
            "round_to", "workload"]
 
 
@@ -54,10 +56,13 @@ class Workload:
     pooling: bool = False          # A built from neighbour positions
     rc: float = 5.0
     j_range: tuple = (10, 60)
+    kmax: int = 0                  # invariant-feature degree range (0: no feature index)
+    wk: int = 1                    # weight of the feature degree in the one-particle degree
+    n_species: int = 0             # neighbours carry one of n_species feature values (pooling)
 
     @property
     def K(self) -> int:
-        return (self.nmax - self.nmin + 1) * (self.lmax + 1) ** 2
+        return (self.nmax - self.nmin + 1) * (self.kmax + 1) * (self.lmax + 1) ** 2
 
     def as_dict(self) -> dict:
         return asdict(self)
@@ -83,6 +88,12 @@ WORKLOADS = {
         "50k environments of 10-60 neighbours in a ball of radius 5",
         nmin=1, nmax=8, lmax=6, nu_max=4, deg_max=16, n_env=50_000, grad=True,
         pooling=True),
+    "species_forces_k375": Workload(
+        "species_forces_k375", "pooling + forward + forces FP32 with an invariant feature per neighbour "
+        "(3 species, phi_nlmk = R_n Y_lm T_k(mu), k <= 2, degree n + l + k), K=375, nu<=4, D=12, "
+        "20k environments of 10-60 neighbours in a ball of radius 5",
+        nmin=1, nmax=5, lmax=4, nu_max=4, deg_max=12, n_env=20_000, wl=1, grad=True, pooling=True,
+        kmax=2, wk=1, n_species=3),
 }
 
 
@@ -141,3 +152,9 @@ def draw_neighbours(n_env: int, seed: int = 3, rc: float = 5.0,
         bad = r < 1e-6
         r[bad] = rc * rng.uniform(0.0, 1.0, int(bad.sum())) ** (1.0 / 3.0)
     return offsets, d * r[:, None]
+
+
+def draw_species(n_pairs: int, n_species: int, seed: int = 4) -> np.ndarray:
+    """Feature value per neighbour: mu_j = -1 + 2 s_j / (S - 1), s_j ~ U{0..S-1} (S >= 2)."""
+    s = np.random.default_rng(seed).integers(0, n_species, size=n_pairs)
+    return -1.0 + 2.0 * s / (n_species - 1)
