@@ -174,6 +174,15 @@ ace_status ace_dag_upload(ace_dag* dag, void* stream);
  *  ACE_READOUT_COMPENSATED (per-task partial sums in FP32, combined with
  *  compensated (TwoSum) FP32 accumulation), ACE_READOUT_FP64_FINAL (partials
  *  combined in FP64).  For ACE_F64 all arithmetic is FP64 and readout is ignored.
+ * Kernel forms (chosen by the autotuner's result, else automatically): one
+ * environment per lane with the stored values of 32 environments in shared
+ * memory (FP32, one channel, graph small enough); a tile of E environments per
+ * CTA with the stored values in shared memory (any dtype and n_out, up to
+ * 65535 stored values per environment); and, for graphs whose stored values do
+ * not fit on chip (e.g. millions of basis functions), one environment per lane
+ * with the stored values in a global-memory workspace of
+ * grid x (n_slots + n_g) x 32 floats, allocated by the first such call and kept
+ * in the graph handle (FP32, one channel).  ACE_KERNEL=lon|loe|loeg forces one.
  * Errors: INVALID_ARG (null/misaligned pointer, n_env < 0, n_out), UNSUPPORTED,
  * NO_DEVICE, CUDA, OOM.  n_env = 0 is a no-op. */
 ace_status ace_eval(ace_dag* dag, const void* A, const void* c, int64_t n_env, int32_t n_out,
@@ -190,14 +199,16 @@ ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void*
                          void* dA, void* stream);
 
 /* Autotuner (not in the paper): time every compiled kernel configuration for
- * this request — the one-environment-per-lane kernel, and the tile-per-lane
- * kernel with each tile size E of 1, 2, 4, 8, 16 environments — on n_env
+ * this request — the one-environment-per-lane kernel with its stored values in
+ * shared memory and in a global workspace, and the tile-per-lane kernel with
+ * each tile size E of 1, 2, 4, 8, 16 environments — on n_env
  * environments of small constant inputs, and keep the fastest in the graph handle; later
  * ace_eval / ace_eval_grad calls with the same dtype, n_out and mode use it.
  * Allocates and frees temporary device buffers (inputs, outputs, coefficients)
  * and leaves no coefficients bound.  best_kind (1 tile per lane, 2 one
- * environment per lane), best_E and best_ms (mean of 3 launches) may be NULL.
- * Environment variables ACE_KERNEL=lon|loe and ACE_TILE_E=<E> override both
+ * environment per lane, 3 one environment per lane with the global workspace),
+ * best_E and best_ms (mean of 3 launches) may be NULL.
+ * Environment variables ACE_KERNEL=lon|loe|loeg and ACE_TILE_E=<E> override both
  * the tuned and the default choice.  Errors: as ace_eval, UNSUPPORTED when no
  * configuration runs. */
 ace_status ace_dag_autotune(ace_dag* dag, int64_t n_env, int32_t n_out, int32_t dtype, int32_t grad, int32_t readout,

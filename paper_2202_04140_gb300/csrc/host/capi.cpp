@@ -96,6 +96,8 @@ struct ace_dag {
   std::vector<int4> pull_host;
   int32_t *node_left = nullptr, *node_right = nullptr, *node_basis = nullptr, *slot_basis = nullptr;
   DevTaskSet sym, one;
+  void* loe_ws = nullptr;  // global workspace of the one-environment-per-lane kernel for large graphs
+  size_t loe_ws_bytes = 0;
   uint32_t* status = nullptr;
   std::vector<void*> allocations;
   std::vector<std::vector<uint16_t>> staging16;  // host copies kept alive until the upload completes
@@ -423,23 +425,38 @@ int kernel_choice() {
   const char* v = std::getenv("ACE_KERNEL");
   if (v && std::strcmp(v, "lon") == 0) return 1;
   if (v && std::strcmp(v, "loe") == 0) return 2;
+  if (v && std::strcmp(v, "loeg") == 0) return 3;
   return 0;
 }
 
 ace_status run_loe(ace_dag* d, DevTaskSet& dt, const void* A, const void* phibar, int64_t n_env, int readout,
-                   void* phi, void* dA, bool grad, cudaStream_t st) {
+                   void* phi, void* dA, bool grad, bool global, cudaStream_t st) {
   int nt = 0;
-  const void* k = loe_kernel_ptr(grad, readout, &nt);
+  const void* k = loe_kernel_ptr(grad, readout, global, &nt);
   if (!k) return fail(ACE_ERR_UNSUPPORTED, "no kernel for this readout mode");
-  const size_t smem = loe_smem(d->plan.n_slots, d->plan.n_g, grad, nt);
+  const size_t smem = global ? loe_global_smem(nt) : loe_smem(d->plan.n_slots, d->plan.n_g, grad, nt);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   int bps = 0;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, nt, smem)) != cudaSuccess)
     return cuda_fail(e, "occupancy query");
   if (bps < 1) return fail(ACE_ERR_UNSUPPORTED, "one-environment-per-lane kernel cannot be resident");
+  const int64_t n_tiles = (n_env + 31) / 32;
+  const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)d->sm_count * bps);
+  if (global) {
+    // one slice of stored values (and adjoints) per CTA, grown on demand and kept in the graph handle
+    const size_t need = (size_t)grid * loe_global_bytes_per_cta(d->plan.n_slots, d->plan.n_g, grad);
+    if (need > d->loe_ws_bytes) {
+      if (d->loe_ws) cudaFree(d->loe_ws);
+      d->loe_ws = nullptr;
+      d->loe_ws_bytes = 0;
+      if ((e = cudaMalloc(&d->loe_ws, need)) != cudaSuccess) return cuda_fail(e, "cudaMalloc (stored-value workspace)");
+      d->loe_ws_bytes = need;
+    }
+  }
   const Plan& p = d->plan;
   dev::LoeArgs a{};
+  a.ws = static_cast<float*>(d->loe_ws);
   a.A = static_cast<const float*>(A);
   a.phibar = static_cast<const float*>(phibar);
   a.phi = static_cast<float*>(phi);
@@ -467,7 +484,6 @@ ace_status run_loe(ace_dag* d, DevTaskSet& dt, const void* A, const void* phibar
   a.ent = reinterpret_cast<const int4*>(dt.rm_ent);
   a.check = checked_mode() ? 1 : 0;
   a.status = d->status;
-  const int64_t grid = std::min<int64_t>(a.n_tiles, (int64_t)d->sm_count * bps);
   void* args[] = {&a};
   e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(nt), args, smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
@@ -491,16 +507,23 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
       E_force = it->second.second;
     }
   }
-  const bool loe_ok = dtype == ACE_F32 && n_out == 1 && dt.rm_bound &&
-                      loe_smem(d->plan.n_slots, d->plan.n_g, grad, 1024) <= (size_t)d->smem_optin;
+  const bool loeg_ok = dtype == ACE_F32 && n_out == 1 && dt.rm_bound;
+  const bool loe_ok = loeg_ok && loe_smem(d->plan.n_slots, d->plan.n_g, grad, 1024) <= (size_t)d->smem_optin;
   if (choice == 2 && !loe_ok) return fail(ACE_ERR_UNSUPPORTED, "ACE_KERNEL=loe: graph or request does not fit");
-  if (loe_ok && choice != 1) return run_loe(d, dt, A, phibar, n_env, readout, phi, dA, grad, st);
-  if (!dt.col16) return fail(ACE_ERR_UNSUPPORTED, "more than 65535 stored values per environment");
+  if (choice == 3 && !loeg_ok) return fail(ACE_ERR_UNSUPPORTED, "ACE_KERNEL=loeg: FP32 one-channel requests only");
+  if (choice == 3) return run_loe(d, dt, A, phibar, n_env, readout, phi, dA, grad, true, st);
+  if (loe_ok && choice != 1) return run_loe(d, dt, A, phibar, n_env, readout, phi, dA, grad, false, st);
   int E = 0, nt = 0;
   size_t smem = 0;
   const void* k = nullptr;
   bool stage = false;
-  if ((s = choose_tile(d, dtype, npad, grad, n_env, E_force, &E, &nt, &smem, &k, &stage)) != ACE_OK) return s;
+  s = dt.col16 ? choose_tile(d, dtype, npad, grad, n_env, E_force, &E, &nt, &smem, &k, &stage)
+               : fail(ACE_ERR_UNSUPPORTED, "more than 65535 stored values per environment");
+  if (s != ACE_OK) {
+    // the stored values of one environment do not fit on chip: keep them in global memory
+    if (loeg_ok && choice != 1) return run_loe(d, dt, A, phibar, n_env, readout, phi, dA, grad, true, st);
+    return s;
+  }
   if (const char* v = std::getenv("ACE_STAGE")) stage = stage && v[0] != '0';  // ACE_STAGE=0: plain loads of A
   const int ro = dtype == ACE_F32 ? readout : 0;
   k = fused_kernel_ptr(dtype, E, npad, grad, ro, &nt);
@@ -750,6 +773,7 @@ void ace_dag_free(ace_dag* dag) {
     cudaGetDevice(&cur);
     cudaSetDevice(dag->device);
     for (void* p : dag->allocations) cudaFree(p);
+    if (dag->loe_ws) cudaFree(dag->loe_ws);
     for (DevTaskSet* t : {&dag->sym, &dag->one}) {
       if (t->vals) cudaFree(t->vals);
       if (t->lin) cudaFree(t->lin);
@@ -821,7 +845,7 @@ ace_status ace_dag_autotune(ace_dag* dag, int64_t n_env, int32_t n_out, int32_t 
   const int npad = nout_pad_of(n_out);
   const auto key = std::make_tuple((int)dtype, npad, grad ? 1 : 0);
   dag->tuned.erase(key);
-  std::vector<std::pair<int, int>> cands = {{2, 0}};
+  std::vector<std::pair<int, int>> cands = {{2, 0}, {3, 0}};
   for (int E : {1, 2, 4, 8, 16}) cands.push_back({1, E});
   cudaEvent_t a, b;
   cudaEventCreate(&a);

@@ -87,6 +87,7 @@ struct LoeArgs {
   const int4* thdr;   // {first entry, end entry, row coefficient bits (first task only), 0}
   int32_t n_tasks;
   const int4* ent;    // entry pairs {col0, coef0 bits, col1, coef1 bits}
+  float* ws;          // global-workspace variant: [gridDim.x][n_slots (+ n_g)][32] floats
   int32_t check;
   uint32_t* status;
 };

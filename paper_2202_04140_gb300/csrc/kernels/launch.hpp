@@ -14,8 +14,10 @@ namespace ace {
 const void* fused_kernel_ptr(int dtype, int E, int nout, bool grad, int readout, int* nt);
 
 // One-environment-per-lane variant (loe.cu): kernel, shared memory, entry binding.
-const void* loe_kernel_ptr(bool grad, int readout, int* nt);
+const void* loe_kernel_ptr(bool grad, int readout, bool global, int* nt);
 size_t loe_smem(int n_slots, int n_g, bool grad, int nt);
+size_t loe_global_smem(int nt);
+size_t loe_global_bytes_per_cta(int n_slots, int n_g, bool grad);
 cudaError_t launch_bind_rm(const float* c, const int32_t* col, const int32_t* ebasis, const uint8_t* ew2, int64_t n,
                            int2* ent, const int4* tasks, const int32_t* toff, const int32_t* slot_basis,
                            int32_t n_tasks, int4* thdr, cudaStream_t st);

@@ -32,15 +32,33 @@ __host__ __device__ inline size_t loe_smem_bytes(int n_slots, int n_g, bool grad
   return b;
 }
 
-template <bool GRAD, int RO, int NT>
+// GLOBAL = false: the stored values AA and adjoints G of the CTA's 32
+// environments live in shared memory, rows of 33 floats (conflict-free
+// transposed copies).  GLOBAL = true (graphs too large for shared memory, e.g.
+// millions of basis functions): they live in the CTA's slice of a global
+// workspace, rows of 32 floats (one 128-byte line per slot, every gather
+// coalesced), and the adjoint updates are global atomics.
+__host__ __device__ inline size_t loe_global_floats(int n_slots, int n_g, bool grad) {
+  return ((size_t)n_slots + (grad ? (size_t)n_g : 0)) * 32;
+}
+
+template <bool GRAD, int RO, int NT, bool GLOBAL>
 __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NW = NT / 32;
-  constexpr int S = kLoeStride;
-  float* AA = reinterpret_cast<float*>(smem_raw);
-  float* G = reinterpret_cast<float*>(smem_raw + align16((size_t)a.n_slots * S * 4));
-  float* pb = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(G) +
-                                       (GRAD ? align16((size_t)a.n_g * S * 4) : 0));
+  constexpr int S = GLOBAL ? 32 : kLoeStride;
+  float* AA;
+  float* G;
+  float* pb;
+  if constexpr (GLOBAL) {
+    AA = a.ws + (size_t)blockIdx.x * loe_global_floats(a.n_slots, a.n_g, GRAD);
+    G = AA + (size_t)a.n_slots * S;
+    pb = reinterpret_cast<float*>(smem_raw);
+  } else {
+    AA = reinterpret_cast<float*>(smem_raw);
+    G = reinterpret_cast<float*>(smem_raw + align16((size_t)a.n_slots * S * 4));
+    pb = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(G) + (GRAD ? align16((size_t)a.n_g * S * 4) : 0));
+  }
   double* red = reinterpret_cast<double*>(pb + 32);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = a.K;
@@ -217,22 +235,35 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
 
 }  // namespace dev
 
-const void* loe_kernel_ptr(bool grad, int readout, int* nt) {
+const void* loe_kernel_ptr(bool grad, int readout, bool global, int* nt) {
   *nt = 1024;
   using namespace dev;
-  if (grad) {
-    if (readout == 0) return (const void*)&loe_kernel<true, 0, 1024>;
-    if (readout == 1) return (const void*)&loe_kernel<true, 1, 1024>;
-    if (readout == 2) return (const void*)&loe_kernel<true, 2, 1024>;
-  } else {
-    if (readout == 0) return (const void*)&loe_kernel<false, 0, 1024>;
-    if (readout == 1) return (const void*)&loe_kernel<false, 1, 1024>;
-    if (readout == 2) return (const void*)&loe_kernel<false, 2, 1024>;
+#define ACE_LOE_PICK(G)                                                              \
+  if (grad) {                                                                        \
+    if (readout == 0) return (const void*)&loe_kernel<true, 0, 1024, G>;            \
+    if (readout == 1) return (const void*)&loe_kernel<true, 1, 1024, G>;            \
+    if (readout == 2) return (const void*)&loe_kernel<true, 2, 1024, G>;            \
+  } else {                                                                           \
+    if (readout == 0) return (const void*)&loe_kernel<false, 0, 1024, G>;           \
+    if (readout == 1) return (const void*)&loe_kernel<false, 1, 1024, G>;           \
+    if (readout == 2) return (const void*)&loe_kernel<false, 2, 1024, G>;           \
   }
+  if (global) {
+    ACE_LOE_PICK(true)
+  } else {
+    ACE_LOE_PICK(false)
+  }
+#undef ACE_LOE_PICK
   return nullptr;
 }
 
 size_t loe_smem(int n_slots, int n_g, bool grad, int nt) { return dev::loe_smem_bytes(n_slots, n_g, grad, nt); }
+
+size_t loe_global_smem(int nt) { return 32 * 4 + (size_t)(nt / 32) * 32 * sizeof(double); }
+
+size_t loe_global_bytes_per_cta(int n_slots, int n_g, bool grad) {
+  return dev::loe_global_floats(n_slots, n_g, grad) * sizeof(float);
+}
 
 __global__ void bind_rm_kernel(const float* __restrict__ c, const int32_t* __restrict__ col,
                                const int32_t* __restrict__ ebasis, const uint8_t* __restrict__ ew2, int64_t n,

@@ -88,6 +88,14 @@ WORKLOADS = {
         "50k environments of 10-60 neighbours in a ball of radius 5",
         nmin=1, nmax=8, lmax=6, nu_max=4, deg_max=16, n_env=50_000, grad=True,
         pooling=True),
+    "paper_degree_k810": Workload(
+        "paper_degree_k810", "forward + dphi/dA FP32, K=810, nu<=6, D=24 with the paper's degree n + l "
+        "(17.3 million basis functions), 16384 environments",
+        nmin=1, nmax=10, lmax=8, nu_max=6, deg_max=24, n_env=16_384, wl=1, grad=True),
+    "paper_degree_d20_k810": Workload(
+        "paper_degree_d20_k810", "forward + dphi/dA FP32, K=810, nu<=6, D=20 with the paper's degree n + l "
+        "(1.5 million basis functions), 16384 environments",
+        nmin=1, nmax=10, lmax=8, nu_max=6, deg_max=20, n_env=16_384, wl=1, grad=True),
     "species_forces_k375": Workload(
         "species_forces_k375", "pooling + forward + forces FP32 with an invariant feature per neighbour "
         "(3 species, phi_nlmk = R_n Y_lm T_k(mu), k <= 2, degree n + l + k), K=375, nu<=4, D=12, "
