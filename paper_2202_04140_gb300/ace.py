@@ -18,6 +18,7 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libace.so")
 
 ACE_OK = 0
+ACE_ERR_TIMEOUT, ACE_ERR_BOUNDS = -4, -5
 STATUS_NAMES = {0: "ACE_OK", -1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_OOM", -3: "ACE_ERR_CUDA",
                 -4: "ACE_ERR_TIMEOUT", -5: "ACE_ERR_BOUNDS", -6: "ACE_ERR_UNSUPPORTED",
                 -7: "ACE_ERR_NO_DEVICE"}

@@ -572,6 +572,9 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     a.lin = static_cast<const TT*>(dt.lin);
     a.check = checked_mode() ? 1 : 0;
     a.stage = stage ? 1 : 0;
+    // test hook for the bounded wait: the staged copies are waited for but never issued, so every
+    // CTA's first wait times out (about a second), reports ACE_ERR_TIMEOUT and reads A directly
+    if (const char* v = std::getenv("ACE_TEST_STAGE_TIMEOUT")) a.stage_no_issue = v[0] == '1' ? 1 : 0;
     a.status = d->status;
   };
   if (dtype == ACE_F32) {

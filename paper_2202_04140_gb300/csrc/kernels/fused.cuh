@@ -63,6 +63,7 @@ struct FusedArgs {
   const T* lin;   // [tasks][NOUT] row coefficient of each task (first task of a basis row), else 0
   int32_t check;
   int32_t stage;  // 1: bulk-copy staging of the next tile's A (needs 16-byte aligned A)
+  int32_t stage_no_issue;  // test hook: wait for copies that are never issued (exercises the time-out)
   uint32_t* status;
 };
 
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
   if (stage) {
     if (tid == 0) {
       mbar_init(mbar);
-      if (blockIdx.x < a.n_tiles) {
+      if (blockIdx.x < a.n_tiles && !a.stage_no_issue) {
         const StageWindow w = stage_window((int64_t)blockIdx.x * E, a.n_env, E, K, (int)sizeof(T));
         stage_issue(mbar, sbuf, Abytes + w.a0, (uint32_t)(w.a1 - w.a0));
       }
@@ -650,7 +651,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
     }
     __syncthreads();
     // the staging buffer is free again: start the copy of the next tile's rows
-    if (stage && tid == 0 && tile + gridDim.x < a.n_tiles) {
+    if (stage && tid == 0 && tile + gridDim.x < a.n_tiles && !a.stage_no_issue) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       const StageWindow w = stage_window((tile + gridDim.x) * E, a.n_env, E, K, (int)sizeof(T));
       stage_issue(mbar, sbuf, Abytes + w.a0, (uint32_t)(w.a1 - w.a0));

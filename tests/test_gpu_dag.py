@@ -292,3 +292,25 @@ def test_bulk_copy_staging_matches_plain_loads(dev, name, n_env, monkeypatch):
         ref, scale = grad_naive(sub, o, c32), grad_error_scale(sub, o, c32)
         for g in (g1, g0):
             assert normalized_error(g.cpu().numpy()[[0, 1, n_env - 1]], ref, scale) < TOL32
+
+
+def test_staging_wait_times_out_and_reports(dev, monkeypatch):
+    """The bounded wait of the staged copy: with the copies never issued (test hook), the first wait
+    of every CTA gives up after about a second, the kernel reads A directly, the results are still
+    right, and the status word reports the time-out (ACE_ERR_TIMEOUT) with the context usable."""
+    from paper_2202_04140_gb300 import ace as L
+    monkeypatch.setenv("ACE_KERNEL", "lon")
+    monkeypatch.setenv("ACE_TILE_E", "2")
+    monkeypatch.setenv("ACE_STAGE", "1")
+    w, o, d, A, c = setup("fwd_grad_k392", n_env=37)
+    A32, c32 = to_f32(A), to_f32(c)
+    At, ct = t(A32, torch.float32, dev), t(c32, torch.float32, dev)
+    monkeypatch.setenv("ACE_TEST_STAGE_TIMEOUT", "1")
+    phi, dA = d.evaluate_grad(At, ct)
+    assert L.ace_stream_status(d.handle, torch.cuda.current_stream().cuda_stream) == L.ACE_ERR_TIMEOUT
+    assert normalized_error(phi.cpu().numpy(), phi_naive(A32, o, c32), error_scale(A32, o, c32)) < TOL32
+    assert normalized_error(dA.cpu().numpy(), grad_naive(A32, o, c32), grad_error_scale(A32, o, c32)) < TOL32
+    monkeypatch.delenv("ACE_TEST_STAGE_TIMEOUT")
+    phi2, _ = d.evaluate_grad(At, ct)             # the context is usable and the status clean again
+    assert d.status() == 0
+    assert torch.equal(phi2, phi)
