@@ -51,21 +51,34 @@ void form_slices(const std::vector<Task>& tasks, const std::vector<int32_t>& ord
     if (head >= order.size()) break;
     std::vector<int32_t> sl;
     uint32_t used_b = 0;
-    size_t scanned = 0;
     // candidates stay within a length band of the slice's longest task (padding stays small)
     const int32_t band = len[order[head]] - std::max<int32_t>(1, len[order[head]] / 16);
-    for (size_t i = head; i < order.size() && sl.size() < 32 && scanned < (size_t)kWindow; ++i) {
+    std::vector<size_t> cand;
+    for (size_t i = head; i < order.size() && cand.size() < (size_t)kWindow; ++i) {
       if (taken[i]) continue;
       if (len[order[i]] < band) break;
-      ++scanned;
+      cand.push_back(i);
+    }
+    auto a_key = [&](int32_t ti) { return (tasks[ti].flags & 2) ? tasks[ti].pl : tasks[ti].row; };
+    auto take = [&](size_t i) {
       const Task& t = tasks[order[i]];
       if (atomics && (t.flags & 2)) {
-        uint32_t b = 1u << (t.pr & 31);
-        if (used_b & b) continue;
+        const uint32_t b = 1u << (t.pr & 31);
+        if (used_b & b) return false;
         used_b |= b;
       }
       taken[i] = 1;
       sl.push_back(order[i]);
+      return true;
+    };
+    // Fill in candidate order, but after each task first take the other candidates with the
+    // same first atomic target, so that equal targets form long runs (one atomic per run).
+    for (size_t ci = 0; ci < cand.size() && sl.size() < 32; ++ci) {
+      if (taken[cand[ci]] || !take(cand[ci])) continue;
+      if (!atomics) continue;
+      const int32_t key = a_key(order[cand[ci]]);
+      for (size_t cj = ci + 1; cj < cand.size() && sl.size() < 32; ++cj)
+        if (!taken[cand[cj]] && a_key(order[cand[cj]]) == key) take(cand[cj]);
     }
     for (size_t i = head; i < order.size() && sl.size() < 32; ++i) {
       if (taken[i]) continue;
