@@ -96,95 +96,101 @@ void form_slices(const std::vector<Task>& tasks, const std::vector<int32_t>& ord
   }
 }
 
-// Interleave the entries of one slice step by step.  At every step the lanes of
-// each phase (`phase_lanes` consecutive lanes, as served by one vector
-// shared-memory load of E values per lane) are matched to distinct bank groups
-// (bank group = column mod `bank_mod`) by a maximum bipartite matching between
-// lanes and the groups in which they still have entries: the most constrained
-// lanes are matched first, and a lane tries its most abundant groups first
-// (ties rotated by lane and step) so that choice remains for later steps.  A lane the matching cannot place takes
-// an entry from its most abundant group (a conflict); lanes without entries
-// left read a zero coefficient at a column in a group nobody uses.
-struct LaneBanks {
-  std::vector<std::vector<int32_t>> by_bank;  // entry indices per bank group
-  int32_t left = 0;
-};
-
-bool augment(int lane, const std::vector<LaneBanks>& lb, const std::vector<int>& lanes_in_phase,
-             std::vector<int>& bank_owner, std::vector<uint8_t>& seen, const std::vector<std::vector<int>>& pref) {
-  for (int b : pref[lane]) {
-    if (seen[b]) continue;
-    seen[b] = 1;
-    if (bank_owner[b] < 0 || augment(bank_owner[b], lb, lanes_in_phase, bank_owner, seen, pref)) {
-      bank_owner[b] = lane;
-      return true;
-    }
-  }
-  return false;
-}
-
+// Interleave the entries of one slice step by step.  The lanes of a phase
+// (`phase_lanes` consecutive lanes, served by one vector shared-memory load of E
+// values per lane) gather without bank conflict when, for every bank group
+// (column mod `bank_mod`), all of them read the same column: different columns
+// of one group cost one extra wavefront each, the same column is a broadcast.
+// So at every step each group is given at most one column: lanes are visited
+// most-constrained first (entries left against steps left); a lane reads a
+// column already given to its group if it has one, else opens a free group
+// with its column that most lanes of the phase still need (so that they can
+// share it), else, if it has no slack, takes a conflicting entry, and otherwise
+// waits a step.  A waiting or finished lane reads a zero coefficient at a
+// column already given out (a broadcast) or in a group nobody uses.
 void interleave(const std::vector<const std::vector<Entry>*>& lane_entries, int32_t steps, int phase_lanes,
                 int bank_mod, int32_t n_slots, int64_t off, TaskSet& ts) {
   const int nl = (int)lane_entries.size();
-  std::vector<LaneBanks> lb(32);
+  // remaining entries of every lane as (column, entry index), sorted by column
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> rem(32);
   for (int j = 0; j < nl; ++j) {
-    lb[j].by_bank.assign(bank_mod, {});
     const auto& v = *lane_entries[j];
-    for (int32_t q = (int32_t)v.size() - 1; q >= 0; --q) lb[j].by_bank[v[q].col % bank_mod].push_back(q);
-    lb[j].left = (int32_t)v.size();
+    for (int32_t q = 0; q < (int32_t)v.size(); ++q) rem[j].push_back({v[q].col, q});
+    std::sort(rem[j].begin(), rem[j].end());
   }
-  std::vector<std::vector<int>> pref(32);
+  std::vector<int32_t> chosen(bank_mod);
+  std::vector<int> order;
+  std::vector<std::pair<int32_t, int>> pop;  // (column, lanes of the phase still needing it)
   for (int32_t k = 0; k < steps; ++k) {
+    const int32_t steps_left = steps - k;
     for (int p0 = 0; p0 < 32; p0 += phase_lanes) {
-      std::vector<int> active;
-      for (int j = p0; j < p0 + phase_lanes; ++j)
-        if (j < nl && lb[j].left > 0) {
-          active.push_back(j);
-          pref[j].clear();
-          for (int b = 0; b < bank_mod; ++b)
-            if (!lb[j].by_bank[b].empty()) pref[j].push_back(b);
-          const int rot = (j + k) % bank_mod;  // ties: lane j at step k prefers group (j + k) mod n first
-          std::stable_sort(pref[j].begin(), pref[j].end(), [&](int x, int y) {
-            if (lb[j].by_bank[x].size() != lb[j].by_bank[y].size())
-              return lb[j].by_bank[x].size() > lb[j].by_bank[y].size();
-            return (x - rot + bank_mod) % bank_mod < (y - rot + bank_mod) % bank_mod;
-          });
-        }
-      std::stable_sort(active.begin(), active.end(), [&](int x, int y) { return pref[x].size() < pref[y].size(); });
-      std::vector<int> bank_owner(bank_mod, -1);
-      std::vector<uint8_t> seen(bank_mod);
-      for (int j : active) {
-        std::fill(seen.begin(), seen.end(), 0);
-        augment(j, lb, active, bank_owner, seen, pref);
+      std::fill(chosen.begin(), chosen.end(), -1);
+      pop.clear();
+      order.clear();
+      for (int j = p0; j < p0 + phase_lanes && j < nl; ++j) {
+        if (rem[j].empty()) continue;
+        order.push_back(j);
+        for (size_t t = 0; t < rem[j].size(); ++t)
+          if (t == 0 || rem[j][t].first != rem[j][t - 1].first) pop.push_back({rem[j][t].first, 1});
       }
-      std::vector<int> lane_bank(32, -1);
-      std::vector<uint8_t> used(bank_mod, 0);
-      for (int b = 0; b < bank_mod; ++b)
-        if (bank_owner[b] >= 0) {
-          lane_bank[bank_owner[b]] = b;
-          used[b] = 1;
+      std::sort(pop.begin(), pop.end());
+      {  // merge equal columns
+        size_t w = 0;
+        for (size_t t = 0; t < pop.size(); ++t) {
+          if (w > 0 && pop[w - 1].first == pop[t].first) pop[w - 1].second += pop[t].second;
+          else pop[w++] = pop[t];
         }
+        pop.resize(w);
+      }
+      auto popularity = [&](int32_t c) {
+        auto it = std::lower_bound(pop.begin(), pop.end(), std::make_pair(c, 0));
+        return (it != pop.end() && it->first == c) ? it->second : 0;
+      };
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const int32_t sx = (int32_t)rem[x].size() - steps_left, sy = (int32_t)rem[y].size() - steps_left;
+        if (sx != sy) return sx > sy;  // least slack first
+        return x < y;
+      });
+      std::vector<int32_t> lane_col(32, -1);
+      for (int j : order) {
+        const int32_t left = (int32_t)rem[j].size();
+        int pick = -1;
+        for (size_t t = 0; t < rem[j].size() && pick < 0; ++t)
+          if (chosen[rem[j][t].first % bank_mod] == rem[j][t].first) pick = (int)t;
+        if (pick < 0) {
+          int best_pop = -1;
+          for (size_t t = 0; t < rem[j].size(); ++t) {
+            const int32_t c = rem[j][t].first;
+            if (chosen[c % bank_mod] >= 0) continue;
+            const int pc = popularity(c);
+            if (pc > best_pop) {
+              best_pop = pc;
+              pick = (int)t;
+            }
+          }
+          if (pick >= 0) chosen[rem[j][pick].first % bank_mod] = rem[j][pick].first;
+        }
+        if (pick < 0 && left >= steps_left) pick = 0;  // no slack: a conflicting entry
+        if (pick < 0) continue;                         // wait a step
+        lane_col[j] = pick;
+      }
+      // a column already given out (broadcast), else a group nobody uses, for lanes without an entry
+      int32_t pad = -1;
+      for (int b = 0; b < bank_mod && pad < 0; ++b)
+        if (chosen[b] >= 0) pad = chosen[b];
+      if (pad < 0) pad = 0;
       for (int j = p0; j < p0 + phase_lanes; ++j) {
         const int64_t idx = off + (int64_t)k * 32 + j;
-        if (j < nl && lb[j].left > 0) {
-          int b = lane_bank[j];
-          if (b < 0) b = pref[j][0];  // no free group: take the most abundant one
-          const int32_t q = lb[j].by_bank[b].back();
-          lb[j].by_bank[b].pop_back();
-          --lb[j].left;
+        if (j < nl && lane_col[j] >= 0) {
+          const int t = lane_col[j];
+          const int32_t q = rem[j][t].second;
+          rem[j].erase(rem[j].begin() + t);
           const Entry& e = (*lane_entries[j])[q];
           ts.col[idx] = e.col;
           ts.ebasis[idx] = e.basis;
           ts.ew2[idx] = e.w2;
-        } else {  // padding: zero coefficient, in a group nobody uses if one is left
-          int32_t c = 0;
-          for (int b = 0; b < bank_mod && b < n_slots; ++b)
-            if (!used[b]) {
-              c = b;
-              used[b] = 1;
-              break;
-            }
-          ts.col[idx] = c;
+        } else {
+          ts.col[idx] = pad < n_slots ? pad : 0;
           ts.ebasis[idx] = -1;
           ts.ew2[idx] = 0;
         }
