@@ -139,8 +139,11 @@ ace_status ace_dag_export(const ace_dag* dag, int32_t* left, int32_t* right, int
 /* Plan statistics: n_slots (values stored per environment: leaves + operand
  * nodes), n_sinks (nodes of order >= 2 without consumers, folded into the
  * readout), n_entries (entries of the symmetric sink matrix), smem_bytes_f32
- * (shared memory per environment of the fused FP32 forward+adjoint kernel).
- * Any pointer may be NULL. */
+ * (shared memory per environment of the tile-per-lane FP32 forward+adjoint
+ * kernel, which keeps the plan's "stored" slots: when a graph's operands do
+ * not all fit a tile of four environments in shared memory, its least-used top
+ * operands are left out and read through their two factors; the
+ * "n_stored" plan array gives their number).  Any pointer may be NULL. */
 ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_sinks, int64_t* n_entries,
                              int64_t* smem_bytes_f32);
 
@@ -149,7 +152,11 @@ ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_si
  * "fwd_off", "rev_slot", "rev_l", "rev_r", "rev_off", and for the symmetric
  * ("sym_") and one-sided ("one_") sink forms: "tasks" (4 int32 per task: row,
  * flags, factor slots), "slice_off", "slice_steps", "col", "ebasis", "ew2", and
- * their row-major copies "rm_tasks", "rm_off", "rm_col", "rm_ebasis", "rm_ew2".
+ * their row-major copies "rm_tasks", "rm_off", "rm_col", "rm_ebasis", "rm_ew2",
+ * and the cold tasks "cold_tasks", "cold_slice_off", "cold_slice_steps",
+ * "cold_ca", "cold_cb" (factor slots of the operand read), "cold_ebasis",
+ * "cold_ew2"; also "n_stored" and the stored forward levels "fwd_stored_slot",
+ * "fwd_stored_l", "fwd_stored_r", "fwd_stored_off".
  * Every array is exported as int32.  *count receives the number of int32
  * values; out (host) may be NULL to query the size.  Errors: INVALID_ARG for an
  * unknown name. */

@@ -76,6 +76,16 @@ struct TaskSet {
   std::vector<int32_t> ebasis;        // [n_entries_padded] basis index (-1 padding)
   std::vector<uint8_t> ew2;           // [n_entries_padded] 1: weight 2 (diagonal of the symmetric form)
   int64_t n_entries = 0;              // real (unpadded) entries
+  // Cold entries: entries whose column is a top operand that the tile-per-lane
+  // kernel does not keep in shared memory (slots >= n_stored).  Such an entry
+  // reads the operand's two factor slots (ca, cb < n_g) and multiplies them.
+  // They form their own tasks (no row coefficient), sliced like the others,
+  // entry k of lane j at cold_slice_off[s] + 32 k + j.
+  std::vector<Task> cold_tasks;       // [n_cold_slices * 32]
+  std::vector<int32_t> cold_slice_off, cold_slice_steps;
+  std::vector<int32_t> cold_ca, cold_cb, cold_ebasis;
+  std::vector<uint8_t> cold_ew2;
+  int32_t n_cold_slices() const { return (int32_t)cold_slice_steps.size(); }
   // The same tasks with their entries contiguous (for the kernel in which a
   // whole warp works on one task, one environment per lane); every task's
   // entry count is padded to an even number (entries are read in pairs).
@@ -105,17 +115,26 @@ struct PullList {
 
 struct Plan {
   int32_t K = 0, n_slots = 0, n_g = 0;
+  // Slots [0, n_stored) are kept in shared memory by the tile-per-lane kernel:
+  // leaves, inner operands and the top operands used by the most sink entries;
+  // the rest (cold top operands) are read through their factors.  n_stored is
+  // chosen so that a tile of four environments fits in 227 KB of shared memory.
+  int32_t n_stored = 0;
   int64_t n_sinks = 0;
   std::vector<int32_t> node_slot;     // node id -> slot or -1
   std::vector<int32_t> slot_node;     // slot -> node id
   std::vector<int32_t> slot_basis;    // slot -> basis index or -1 (linear coefficient)
   LevelList fwd;                      // operand nodes by increasing order
+  LevelList fwd_stored;               // the same, restricted to slots < n_stored
   LevelList rev;                      // inner operand nodes by decreasing order
   PullList pull;                      // the same sweep, gathered per target
   TaskSet sym;                        // symmetric sink form (forward + adjoint)
   TaskSet one;                        // one-sided sink form (forward only)
 };
 
-ace_status build_plan(const Spec& spec, const Graph& g, int task_len, Plan& plan);
+// stored_limit(K, n_g): at most this many slots are kept for the tile-per-lane
+// kernel (0: no limit); see Plan::n_stored.
+using StoredLimitFn = int64_t (*)(int32_t K, int32_t n_g);
+ace_status build_plan(const Spec& spec, const Graph& g, int task_len, StoredLimitFn stored_limit, Plan& plan);
 
 }  // namespace ace

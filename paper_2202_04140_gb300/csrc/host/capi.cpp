@@ -54,6 +54,17 @@ struct DevTaskSet {
   int64_t n_pack = 0;  // packed entries (groups x 32 lanes x 4)
   void* vals4 = nullptr;
   size_t vals4_bytes = 0;
+  // cold tasks (entries read through the two factors of a top operand not kept on chip)
+  int4* cold_tasks = nullptr;
+  int32_t* cold_slice_off = nullptr;
+  int32_t* cold_slice_steps = nullptr;  // steps | (reduction rounds << 16)
+  uint32_t* cold_cab = nullptr;
+  int32_t* cold_ebasis = nullptr;
+  uint8_t* cold_ew2 = nullptr;
+  int32_t n_cold_slices = 0;
+  int64_t n_cold_pad = 0;
+  void* cold_vals = nullptr;
+  size_t cold_vals_bytes = 0;
   int32_t* ebasis = nullptr;
   uint8_t* ew2 = nullptr;
   int32_t n_slices = 0;
@@ -91,6 +102,7 @@ struct ace_dag {
   int device = -1;
   int sm_count = 0, smem_optin = 0;
   int32_t *fwd_slot = nullptr, *fwd_l = nullptr, *fwd_r = nullptr;
+  int32_t *fwds_slot = nullptr, *fwds_l = nullptr, *fwds_r = nullptr;  // stored slots only
   int32_t *rev_slot = nullptr, *rev_l = nullptr, *rev_r = nullptr;
   int4* pull = nullptr;  // {consumer slot, partner slot, target slot, 0}
   std::vector<int4> pull_host;
@@ -130,6 +142,22 @@ ace_status upload_vec(ace_dag* d, const std::vector<V>& v, V** out, cudaStream_t
   return ACE_OK;
 }
 
+// Rounds of the segmented warp sum a slice needs: ceil(log2) of its longest run
+// of lanes with equal "A" target (the row, or the first factor of a top operand).
+int reduction_rounds(const std::vector<Task>& tasks, size_t sl) {
+  int run = 1, longest = 1, prev_key = 0;
+  for (int j = 0; j < 32; ++j) {
+    const Task& t = tasks[sl * 32 + j];
+    const int key = t.row < 0 ? -1 - j : ((t.flags & 2) ? t.pl : t.row);
+    run = (j > 0 && key == prev_key) ? run + 1 : 1;
+    longest = std::max(longest, run);
+    prev_key = key;
+  }
+  int rounds = 0;
+  while ((1 << rounds) < longest) ++rounds;
+  return rounds;
+}
+
 ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStream_t st) {
   std::vector<int4> t4(ts.tasks.size());
   for (size_t i = 0; i < ts.tasks.size(); ++i)
@@ -142,20 +170,8 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   // (ceil(log2) of the longest run of equal targets among its 32 tasks), and per
   // task the basis index of its row's own coefficient (first task of a row only).
   std::vector<int32_t> steps_dev(ts.slice_steps.size()), tb(ts.tasks.size(), -1);
-  for (size_t sl = 0; sl < ts.slice_steps.size(); ++sl) {
-    int run = 1, longest = 1;
-    int prev_key = 0;
-    for (int j = 0; j < 32; ++j) {
-      const Task& t = ts.tasks[sl * 32 + j];
-      const int key = t.row < 0 ? -1 - j : ((t.flags & 2) ? t.pl : t.row);
-      run = (j > 0 && key == prev_key) ? run + 1 : 1;
-      longest = std::max(longest, run);
-      prev_key = key;
-    }
-    int rounds = 0;
-    while ((1 << rounds) < longest) ++rounds;
-    steps_dev[sl] = ts.slice_steps[sl] | (rounds << 16);
-  }
+  for (size_t sl = 0; sl < ts.slice_steps.size(); ++sl)
+    steps_dev[sl] = ts.slice_steps[sl] | (reduction_rounds(ts.tasks, sl) << 16);
   for (size_t i = 0; i < ts.tasks.size(); ++i) {
     const Task& t = ts.tasks[i];
     if (t.row >= 0 && (t.flags & 5) == 5) tb[i] = d->plan.slot_basis[t.row];
@@ -165,7 +181,7 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   d->staging32.push_back(std::move(tb));
   if ((s = upload_vec(d, d->staging32.back(), &dt.tbasis, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.col, &dt.col, st)) != ACE_OK) return s;
-  if (d->plan.n_slots <= 65535) {
+  if (d->plan.n_stored <= 65535) {
     d->staging16.emplace_back(ts.col.begin(), ts.col.end());
     if ((s = upload_vec(d, d->staging16.back(), &dt.col16, st)) != ACE_OK) return s;
     // packed copy: padding steps of a slice's last group get column 0 and no coefficient
@@ -201,6 +217,31 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   }
   if ((s = upload_vec(d, ts.ebasis, &dt.ebasis, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.ew2, &dt.ew2, st)) != ACE_OK) return s;
+  // cold tasks: slice headers with reduction rounds, factor pairs packed as ca | cb << 16
+  dt.n_cold_slices = ts.n_cold_slices();
+  dt.n_cold_pad = (int64_t)ts.cold_ca.size();
+  if (dt.n_cold_slices > 0) {
+    std::vector<int4> c4(ts.cold_tasks.size());
+    for (size_t i = 0; i < ts.cold_tasks.size(); ++i)
+      c4[i] = make_int4(ts.cold_tasks[i].row, ts.cold_tasks[i].flags, ts.cold_tasks[i].pl, ts.cold_tasks[i].pr);
+    std::vector<int32_t> hdr(ts.cold_slice_steps.size());
+    for (size_t sl = 0; sl < hdr.size(); ++sl)
+      hdr[sl] = ts.cold_slice_steps[sl] | (reduction_rounds(ts.cold_tasks, sl) << 16);
+    std::vector<int32_t> cab(ts.cold_ca.size());
+    for (size_t i = 0; i < cab.size(); ++i)
+      cab[i] = (int32_t)((uint32_t)ts.cold_ca[i] | ((uint32_t)ts.cold_cb[i] << 16));
+    d->staging_int4.push_back(std::move(c4));
+    if ((s = upload_vec(d, d->staging_int4.back(), &dt.cold_tasks, st)) != ACE_OK) return s;
+    d->staging32.push_back(std::move(hdr));
+    if ((s = upload_vec(d, d->staging32.back(), &dt.cold_slice_steps, st)) != ACE_OK) return s;
+    if ((s = upload_vec(d, ts.cold_slice_off, &dt.cold_slice_off, st)) != ACE_OK) return s;
+    d->staging32.push_back(std::move(cab));
+    int32_t* cab_dev = nullptr;
+    if ((s = upload_vec(d, d->staging32.back(), &cab_dev, st)) != ACE_OK) return s;
+    dt.cold_cab = reinterpret_cast<uint32_t*>(cab_dev);
+    if ((s = upload_vec(d, ts.cold_ebasis, &dt.cold_ebasis, st)) != ACE_OK) return s;
+    if ((s = upload_vec(d, ts.cold_ew2, &dt.cold_ew2, st)) != ACE_OK) return s;
+  }
   dt.n_slices = ts.n_slices();
   dt.n_pad = (int64_t)ts.col.size();
   std::vector<int4> r4(ts.rm_tasks.size());
@@ -226,6 +267,28 @@ ace_status validate_plan(const Plan& p) {
   for (size_t i = 0; i < p.rev.slot.size(); ++i)
     if (!in(p.rev.slot[i], p.n_g) || !in(p.rev.l[i], p.n_g) || !in(p.rev.r[i], p.n_g))
       return fail(ACE_ERR_BOUNDS, "plan: adjoint index out of range");
+  if (p.n_stored < p.n_g || p.n_stored > p.n_slots) return fail(ACE_ERR_BOUNDS, "plan: stored slot count");
+  for (size_t i = 0; i < p.fwd_stored.slot.size(); ++i)
+    if (!in(p.fwd_stored.slot[i], p.n_stored) || !in(p.fwd_stored.l[i], p.n_stored) ||
+        !in(p.fwd_stored.r[i], p.n_stored))
+      return fail(ACE_ERR_BOUNDS, "plan: stored forward index out of range");
+  for (const TaskSet* ts : {&p.sym, &p.one}) {
+    for (int32_t c : ts->col)
+      if (!in(c, p.n_stored)) return fail(ACE_ERR_BOUNDS, "plan: entry column not stored");
+    for (size_t i = 0; i < ts->cold_ca.size(); ++i)
+      if (!in(ts->cold_ca[i], p.n_g) || !in(ts->cold_cb[i], p.n_g))
+        return fail(ACE_ERR_BOUNDS, "plan: cold entry factor out of range");
+    for (const Task& t : ts->cold_tasks) {
+      if (t.row < 0) continue;
+      if (!in(t.row, p.n_slots) || (t.flags & 5)) return fail(ACE_ERR_BOUNDS, "plan: cold task row or flags");
+      if ((t.flags & 2) && (!in(t.pl, p.n_g) || !in(t.pr, p.n_g)))
+        return fail(ACE_ERR_BOUNDS, "plan: cold task factor out of range");
+      if (!(t.flags & 2) && !in(t.row, p.n_g)) return fail(ACE_ERR_BOUNDS, "plan: cold task row out of range");
+    }
+    if (ts->cold_slice_off.size() != ts->cold_slice_steps.size() + 1 ||
+        ts->cold_slice_off.back() != (int32_t)ts->cold_ca.size())
+      return fail(ACE_ERR_BOUNDS, "plan: cold slice offsets inconsistent");
+  }
   const PullList& q = p.pull;
   if (q.src.size() != q.par.size() || q.src.size() != q.tgt.size() || q.lvl.empty() ||
       q.lvl.back() != (int32_t)q.src.size())
@@ -243,6 +306,7 @@ ace_status validate_plan(const Plan& p) {
         return fail(ACE_ERR_BOUNDS, "plan: task factor out of range");
       if (ts == &p.sym && !(t.flags & 2) && !in(t.row, p.n_g))
         return fail(ACE_ERR_BOUNDS, "plan: adjoint row out of range");
+      if (!(t.flags & 2) && !in(t.row, p.n_stored)) return fail(ACE_ERR_BOUNDS, "plan: task row not stored");
     }
     for (int32_t c : ts->rm_col)
       if (!in(c, p.n_slots)) return fail(ACE_ERR_BOUNDS, "plan: row-major entry column out of range");
@@ -277,6 +341,9 @@ ace_status ensure_uploaded(ace_dag* d, cudaStream_t st) {
   if ((s = upload_vec(d, p.fwd.slot, &d->fwd_slot, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.fwd.l, &d->fwd_l, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.fwd.r, &d->fwd_r, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, p.fwd_stored.slot, &d->fwds_slot, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, p.fwd_stored.l, &d->fwds_l, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, p.fwd_stored.r, &d->fwds_r, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.rev.slot, &d->rev_slot, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.rev.l, &d->rev_l, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.rev.r, &d->rev_r, st)) != ACE_OK) return s;
@@ -345,6 +412,19 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
     e = launch_bind(dtype, c, n_out, 1, dt.ebasis4, dt.ew2_4, dt.n_pack, dt.vals4, nullptr, 0, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
   }
+  if (dt.n_cold_slices > 0) {
+    const size_t cb = std::max<size_t>((size_t)dt.n_cold_pad * npad * tsz, 16);
+    if (cb > dt.cold_vals_bytes) {
+      if (dt.cold_vals) cudaFree(dt.cold_vals);
+      dt.cold_vals = nullptr;
+      dt.cold_vals_bytes = 0;
+      if ((e = cudaMalloc(&dt.cold_vals, cb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      dt.cold_vals_bytes = cb;
+    }
+    e = launch_bind(dtype, c, n_out, npad, dt.cold_ebasis, dt.cold_ew2, dt.n_cold_pad, dt.cold_vals, nullptr, 0,
+                    nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
+  }
   dt.rm_bound = false;
   if (dtype == ACE_F32 && n_out == 1) {
     if (!dt.rm_ent) {
@@ -401,10 +481,10 @@ ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t
     if (!k) continue;
     // with the bulk-copy staging buffer when it fits, else without
     bool stage = true;
-    dev::SmemLayout L = dev::smem_layout(E, npad, grad, d->plan.n_slots, d->plan.n_g, nt, (int)tsz, d->K, true);
+    dev::SmemLayout L = dev::smem_layout(E, npad, grad, d->plan.n_stored, d->plan.n_g, nt, (int)tsz, d->K, true);
     if (L.total > (size_t)d->smem_optin) {
       stage = false;
-      L = dev::smem_layout(E, npad, grad, d->plan.n_slots, d->plan.n_g, nt, (int)tsz, d->K, false);
+      L = dev::smem_layout(E, npad, grad, d->plan.n_stored, d->plan.n_g, nt, (int)tsz, d->K, false);
     }
     if (L.total > (size_t)d->smem_optin) continue;
     *stage_out = stage;
@@ -546,17 +626,17 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     a.n_env = n_env;
     a.n_tiles = n_tiles;
     a.K = p.K;
-    a.n_slots = p.n_slots;
+    a.n_slots = p.n_stored;  // the slots this kernel keeps in shared memory
     a.n_g = p.n_g;
     a.n_out = n_out;
-    a.fwd_slot = d->fwd_slot;
-    a.fwd_l = d->fwd_l;
-    a.fwd_r = d->fwd_r;
+    a.fwd_slot = d->fwds_slot;
+    a.fwd_l = d->fwds_l;
+    a.fwd_r = d->fwds_r;
     a.pull = d->pull;
-    a.n_fwd_levels = (int32_t)p.fwd.off.size() - 1;
+    a.n_fwd_levels = (int32_t)p.fwd_stored.off.size() - 1;
     a.n_pull_levels = (int32_t)p.pull.lvl.size() - 1;
     for (int i = 0; i <= dev::kMaxLevels; ++i) {
-      a.fwd_off[i] = i < (int)p.fwd.off.size() ? p.fwd.off[i] : 0;
+      a.fwd_off[i] = i < (int)p.fwd_stored.off.size() ? p.fwd_stored.off[i] : 0;
       a.pull_lvl[i] = i < (int)p.pull.lvl.size() ? p.pull.lvl[i] : 0;
     }
     a.tasks = dt.tasks;
@@ -570,6 +650,12 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     a.gs = dev::g_stride(p.n_g);
     a.vals = static_cast<const TT*>(dt.vals);
     a.lin = static_cast<const TT*>(dt.lin);
+    a.cold_tasks = dt.cold_tasks;
+    a.cold_slice_off = dt.cold_slice_off;
+    a.cold_slice_steps = dt.cold_slice_steps;
+    a.n_cold_slices = dt.n_cold_slices;
+    a.cold_cab = dt.cold_cab;
+    a.cold_vals = static_cast<const TT*>(dt.cold_vals);
     a.check = checked_mode() ? 1 : 0;
     a.stage = stage ? 1 : 0;
     // test hook for the bounded wait: the staged copies are waited for but never issued, so every
@@ -647,6 +733,22 @@ ace_status ace_spec_tuples(const ace_spec* spec, int32_t* tuples, int32_t* deg) 
 
 void ace_spec_free(ace_spec* spec) { delete spec; }
 
+// Largest number of stored slots for which a tile of four environments (FP32,
+// one channel, forward + adjoint, 1024 threads, with the staging buffer) fits in
+// the 227 KB of shared memory a CTA can have on this GPU; ACE_PLAN_STORED=<n>
+// sets the limit directly (tests: forces entries to the cold path).
+int64_t stored_slot_limit(int32_t K, int32_t n_g) {
+  if (const char* v = std::getenv("ACE_PLAN_STORED")) return std::max<int64_t>(0, std::atoll(v));
+  constexpr size_t kSmemOptin = 232448;
+  int64_t lo = 0, hi = 65535;
+  while (lo < hi) {  // largest n with the layout inside the budget
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (dev::smem_layout(4, 1, true, (int)mid, n_g, 1024, 4, K, true).total <= kSmemOptin) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 ace_status ace_build_dag(const ace_spec* spec, int32_t algo, int32_t split_rule, int32_t n_split, ace_dag** out) {
   if (!spec || !out) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
@@ -656,7 +758,7 @@ ace_status ace_build_dag(const ace_spec* spec, int32_t algo, int32_t split_rule,
     if (st != ACE_OK) return st;
     int task_len = 64;
     if (const char* v = std::getenv("ACE_TASK_LEN")) task_len = std::max(1, std::atoi(v));
-    st = build_plan(*spec->s, d->g, task_len, d->plan);
+    st = build_plan(*spec->s, d->g, task_len, stored_slot_limit, d->plan);
     if (st != ACE_OK) return st;
     d->K = spec->s->K;
     d->n_basis = spec->s->n_basis();
@@ -708,7 +810,7 @@ ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_si
   if (n_slots) *n_slots = p.n_slots;
   if (n_sinks) *n_sinks = p.n_sinks;
   if (n_entries) *n_entries = p.sym.n_entries;
-  if (smem_bytes_f32) *smem_bytes_f32 = (int64_t)(p.n_slots + p.n_g) * 4;
+  if (smem_bytes_f32) *smem_bytes_f32 = (int64_t)(p.n_stored + p.n_g) * 4;
   return ACE_OK;
 }
 
@@ -732,6 +834,17 @@ ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out
     } else if (field == "rm_tasks") {
       for (const Task& t : ts.rm_tasks) tmp.insert(tmp.end(), {t.row, t.flags, t.pl, t.pr});
       v = &tmp;
+    } else if (field == "cold_tasks") {
+      for (const Task& t : ts.cold_tasks) tmp.insert(tmp.end(), {t.row, t.flags, t.pl, t.pr});
+      v = &tmp;
+    } else if (field == "cold_slice_off") v = &ts.cold_slice_off;
+    else if (field == "cold_slice_steps") v = &ts.cold_slice_steps;
+    else if (field == "cold_ca") v = &ts.cold_ca;
+    else if (field == "cold_cb") v = &ts.cold_cb;
+    else if (field == "cold_ebasis") v = &ts.cold_ebasis;
+    else if (field == "cold_ew2") {
+      tmp.assign(ts.cold_ew2.begin(), ts.cold_ew2.end());
+      v = &tmp;
     } else if (field == "rm_off") v = &ts.rm_off;
     else if (field == "rm_col") v = &ts.rm_col;
     else if (field == "rm_ebasis") v = &ts.rm_ebasis;
@@ -754,6 +867,13 @@ ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out
   else if (n == "rev_l") v = &p.rev.l;
   else if (n == "rev_r") v = &p.rev.r;
   else if (n == "rev_off") v = &p.rev.off;
+  else if (n == "n_stored") {
+    tmp = {p.n_stored};
+    v = &tmp;
+  } else if (n == "fwd_stored_slot") v = &p.fwd_stored.slot;
+  else if (n == "fwd_stored_l") v = &p.fwd_stored.l;
+  else if (n == "fwd_stored_r") v = &p.fwd_stored.r;
+  else if (n == "fwd_stored_off") v = &p.fwd_stored.off;
   else if (n == "pull_tgt") v = &p.pull.tgt;
   else if (n == "pull_src") v = &p.pull.src;
   else if (n == "pull_par") v = &p.pull.par;
@@ -781,6 +901,7 @@ void ace_dag_free(ace_dag* dag) {
       if (t->vals) cudaFree(t->vals);
       if (t->lin) cudaFree(t->lin);
       if (t->vals4) cudaFree(t->vals4);
+      if (t->cold_vals) cudaFree(t->cold_vals);
       if (t->rm_ent) cudaFree(t->rm_ent);
       if (t->rm_thdr) cudaFree(t->rm_thdr);
     }

@@ -199,76 +199,148 @@ void interleave(const std::vector<const std::vector<Entry>*>& lane_entries, int3
   }
 }
 
-void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<int32_t>& slot_basis,
-                 int32_t n_g, bool sym, const std::vector<int32_t>& slot_l, const std::vector<int32_t>& slot_r,
-                 int task_len, TaskSet& ts) {
-  struct Proto {
-    int32_t begin, len;
-  };
-  std::vector<Task> tasks;
-  std::vector<Proto> protos;
+// Task protos of a set of rows: each row with entries (or, if with_lin, a row
+// coefficient) is cut into equal pieces of at most task_len entries.
+struct Proto {
+  int32_t begin, len;
+};
+
+void make_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<int32_t>& slot_basis, int32_t n_g,
+                bool with_lin, const std::vector<int32_t>& slot_l, const std::vector<int32_t>& slot_r, int task_len,
+                std::vector<Task>& tasks, std::vector<Proto>& protos) {
   const int32_t n_slots = (int32_t)rows.size();
   for (int32_t s = 0; s < n_slots; ++s) {
     const auto& r = rows[s];
-    const bool lin = slot_basis[s] >= 0;
+    const bool lin = with_lin && slot_basis[s] >= 0;
     if (r.empty() && !lin) continue;
-    const bool top = sym && s >= n_g;
+    // a top operand's value is the product of its factors (adjoint: pushed to them)
+    const bool top = s >= n_g;
     const int32_t n = (int32_t)r.size();
-    // equal pieces of at most task_len entries
     const int32_t pieces = std::max<int32_t>(1, (n + task_len - 1) / task_len);
     for (int32_t p = 0; p < pieces; ++p) {
       const int32_t b = (int32_t)((int64_t)n * p / pieces), e = (int32_t)((int64_t)n * (p + 1) / pieces);
       Task t;
       t.row = s;
-      t.flags = (p == 0 ? 1 : 0) | (top ? 2 : 0) | (lin ? 4 : 0);
+      t.flags = (p == 0 && with_lin ? 1 : 0) | (top ? 2 : 0) | (lin ? 4 : 0);
       t.pl = top ? slot_l[s] : -1;
       t.pr = top ? slot_r[s] : -1;
       tasks.push_back(t);
       protos.push_back({b, e - b});
     }
   }
+}
+
+// Slices of the protos, longest first.
+void slice_tasks(const std::vector<Task>& tasks, const std::vector<Proto>& protos, bool sym,
+                 std::vector<std::vector<int32_t>>& slices, std::vector<int32_t>& steps) {
   std::vector<int32_t> order(tasks.size());
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return protos[a].len > protos[b].len; });
-  std::vector<std::vector<int32_t>> slices;
   std::vector<int32_t> lens(protos.size());
   for (size_t i = 0; i < protos.size(); ++i) lens[i] = protos[i].len;
   form_slices(tasks, order, lens, sym, slices);
-  const int32_t n_slices = (int32_t)slices.size();
+  steps.assign(slices.size(), 0);
+  for (size_t s = 0; s < slices.size(); ++s)
+    for (int32_t ti : slices[s]) steps[s] = std::max(steps[s], protos[ti].len);
+}
+
+void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<int32_t>& slot_basis, int32_t n_g,
+                 int32_t n_stored, bool sym, const std::vector<int32_t>& slot_l, const std::vector<int32_t>& slot_r,
+                 int task_len, TaskSet& ts) {
+  const int32_t n_slots = (int32_t)rows.size();
   ts = TaskSet();
-  ts.tasks.resize((size_t)n_slices * 32, Task{-1, 0, -1, -1});
-  ts.slice_off.assign(n_slices + 1, 0);
-  ts.slice_steps.assign(n_slices, 0);
-  int64_t off = 0;
-  for (int32_t s = 0; s < n_slices; ++s) {
-    int32_t steps = 0;
-    for (int32_t ti : slices[s]) steps = std::max(steps, protos[ti].len);
-    ts.slice_off[s] = (int32_t)off;
-    ts.slice_steps[s] = steps;
-    off += (int64_t)steps * 32;
-  }
-  ts.slice_off[n_slices] = (int32_t)off;
-  ts.col.assign(off, 0);
-  ts.ebasis.assign(off, -1);
-  ts.ew2.assign(off, 0);
-  ts.n_entries = 0;
-  std::vector<std::vector<Entry>> lane_store(32);
-  for (int32_t s = 0; s < n_slices; ++s) {
-    std::vector<const std::vector<Entry>*> lanes;
-    for (size_t j = 0; j < slices[s].size(); ++j) {
-      const int32_t ti = slices[s][j];
-      ts.tasks[(size_t)s * 32 + j] = tasks[ti];
-      const auto& r = rows[tasks[ti].row];
-      lane_store[j].assign(r.begin() + protos[ti].begin, r.begin() + protos[ti].begin + protos[ti].len);
-      lanes.push_back(&lane_store[j]);
-      ts.n_entries += protos[ti].len;
+  // hot entries (column kept in shared memory) and cold ones
+  std::vector<std::vector<Entry>> hot(n_slots), cold(n_slots);
+  for (int32_t s = 0; s < n_slots; ++s)
+    for (const Entry& e : rows[s]) (e.col < n_stored ? hot : cold)[s].push_back(e);
+
+  // ---- hot tasks: interleaved, bank-scheduled entries
+  {
+    std::vector<Task> tasks;
+    std::vector<Proto> protos;
+    make_tasks(hot, slot_basis, n_g, true, slot_l, slot_r, task_len, tasks, protos);
+    std::vector<std::vector<int32_t>> slices;
+    std::vector<int32_t> steps;
+    slice_tasks(tasks, protos, sym, slices, steps);
+    const int32_t n_slices = (int32_t)slices.size();
+    ts.tasks.resize((size_t)n_slices * 32, Task{-1, 0, -1, -1});
+    ts.slice_off.assign(n_slices + 1, 0);
+    ts.slice_steps = steps;
+    int64_t off = 0;
+    for (int32_t s = 0; s < n_slices; ++s) {
+      ts.slice_off[s] = (int32_t)off;
+      off += (int64_t)steps[s] * 32;
     }
-    interleave(lanes, ts.slice_steps[s], 16, 16, n_slots, ts.slice_off[s], ts);
+    ts.slice_off[n_slices] = (int32_t)off;
+    ts.col.assign(off, 0);
+    ts.ebasis.assign(off, -1);
+    ts.ew2.assign(off, 0);
+    ts.n_entries = 0;
+    std::vector<std::vector<Entry>> lane_store(32);
+    for (int32_t s = 0; s < n_slices; ++s) {
+      std::vector<const std::vector<Entry>*> lanes;
+      for (size_t j = 0; j < slices[s].size(); ++j) {
+        const int32_t ti = slices[s][j];
+        ts.tasks[(size_t)s * 32 + j] = tasks[ti];
+        const auto& r = hot[tasks[ti].row];
+        lane_store[j].assign(r.begin() + protos[ti].begin, r.begin() + protos[ti].begin + protos[ti].len);
+        lanes.push_back(&lane_store[j]);
+        ts.n_entries += protos[ti].len;
+      }
+      interleave(lanes, ts.slice_steps[s], 16, 16, n_stored, ts.slice_off[s], ts);
+    }
   }
-  // row-major copy (same tasks, same order)
-  ts.rm_off.push_back(0);
-  for (int32_t s = 0; s < n_slices; ++s)
-    for (int32_t ti : slices[s]) {
+
+  // ---- cold tasks: the operand's two factors per entry, entries in task order
+  {
+    std::vector<Task> tasks;
+    std::vector<Proto> protos;
+    make_tasks(cold, slot_basis, n_g, false, slot_l, slot_r, task_len, tasks, protos);
+    std::vector<std::vector<int32_t>> slices;
+    std::vector<int32_t> steps;
+    slice_tasks(tasks, protos, sym, slices, steps);
+    const int32_t n_slices = (int32_t)slices.size();
+    ts.cold_tasks.resize((size_t)n_slices * 32, Task{-1, 0, -1, -1});
+    ts.cold_slice_off.assign(n_slices + 1, 0);
+    ts.cold_slice_steps = steps;
+    int64_t off = 0;
+    for (int32_t s = 0; s < n_slices; ++s) {
+      ts.cold_slice_off[s] = (int32_t)off;
+      off += (int64_t)steps[s] * 32;
+    }
+    ts.cold_slice_off[n_slices] = (int32_t)off;
+    ts.cold_ca.assign(off, 0);
+    ts.cold_cb.assign(off, 0);
+    ts.cold_ebasis.assign(off, -1);
+    ts.cold_ew2.assign(off, 0);
+    for (int32_t s = 0; s < n_slices; ++s)
+      for (size_t j = 0; j < slices[s].size(); ++j) {
+        const int32_t ti = slices[s][j];
+        ts.cold_tasks[(size_t)s * 32 + j] = tasks[ti];
+        const auto& r = cold[tasks[ti].row];
+        for (int32_t q = 0; q < protos[ti].len; ++q) {
+          const Entry& e = r[protos[ti].begin + q];
+          const int64_t idx = (int64_t)ts.cold_slice_off[s] + (int64_t)q * 32 + (int64_t)j;
+          ts.cold_ca[idx] = slot_l[e.col];
+          ts.cold_cb[idx] = slot_r[e.col];
+          ts.cold_ebasis[idx] = e.basis;
+          ts.cold_ew2[idx] = e.w2;
+          ++ts.n_entries;
+        }
+      }
+  }
+
+  // ---- row-major copy of all entries (kernels that keep every slot), longest tasks first
+  {
+    std::vector<Task> tasks;
+    std::vector<Proto> protos;
+    make_tasks(rows, slot_basis, n_g, true, slot_l, slot_r, task_len, tasks, protos);
+    std::vector<int32_t> order(tasks.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return protos[a].len > protos[b].len; });
+    ts.rm_off.push_back(0);
+    for (int32_t ti : order) {
       ts.rm_tasks.push_back(tasks[ti]);
       const auto& r = rows[tasks[ti].row];
       for (int32_t q = protos[ti].begin; q < protos[ti].begin + protos[ti].len; ++q) {
@@ -283,11 +355,12 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
       }
       ts.rm_off.push_back((int32_t)ts.rm_col.size());
     }
+  }
 }
 
 }  // namespace
 
-ace_status build_plan(const Spec& spec, const Graph& g, int task_len, Plan& plan) {
+ace_status build_plan(const Spec& spec, const Graph& g, int task_len, StoredLimitFn stored_limit_fn, Plan& plan) {
   if (task_len < 1) return fail(ACE_ERR_INVALID_ARG, "task_len must be >= 1");
   const int32_t K = g.K;
   const int64_t N = g.n_nodes();
@@ -327,6 +400,30 @@ ace_status build_plan(const Spec& spec, const Graph& g, int task_len, Plan& plan
     plan.slot_node.push_back(id);
   }
   plan.n_g = (int32_t)plan.slot_node.size();
+  // Stored slots for the tile-per-lane kernel: when not every top operand fits,
+  // keep those that appear in the most sink entries (entries are symmetric:
+  // a sink [p, q] is an entry of row p in column q and of row q in column p).
+  {
+    const int64_t n_all = (int64_t)plan.n_g + (int64_t)top_ids.size();
+    const int64_t stored_limit = stored_limit_fn ? stored_limit_fn(K, plan.n_g) : 0;
+    int64_t keep = (int64_t)top_ids.size();
+    if (stored_limit > 0 && n_all > stored_limit && stored_limit > plan.n_g && n_all <= 65535)
+      keep = stored_limit - plan.n_g;
+    if (keep < (int64_t)top_ids.size()) {
+      std::vector<int32_t> deg(N, 0);
+      for (int64_t i = K; i < N; ++i) {
+        if (operand[i] || g.node_basis[i] < 0) continue;
+        deg[g.left[i]]++;
+        if (g.right[i] != g.left[i]) deg[g.right[i]]++;
+      }
+      std::vector<int32_t> by_use = top_ids;
+      std::stable_sort(by_use.begin(), by_use.end(), [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
+      std::vector<uint8_t> hot(N, 0);
+      for (int64_t t = 0; t < keep; ++t) hot[by_use[t]] = 1;
+      std::stable_partition(top_ids.begin(), top_ids.end(), [&](int32_t id) { return hot[id] != 0; });
+    }
+    plan.n_stored = (int32_t)(plan.n_g + keep);
+  }
   for (int32_t id : top_ids) {
     plan.node_slot[id] = (int32_t)plan.slot_node.size();
     plan.slot_node.push_back(id);
@@ -368,10 +465,12 @@ ace_status build_plan(const Spec& spec, const Graph& g, int task_len, Plan& plan
     }
     L.off.push_back((int32_t)L.slot.size());
   };
-  std::vector<int32_t> all_ops, inner_slots;
+  std::vector<int32_t> all_ops, stored_ops, inner_slots;
   for (int32_t s = K; s < n_slots; ++s) all_ops.push_back(s);
+  for (int32_t s = K; s < plan.n_stored; ++s) stored_ops.push_back(s);
   for (int32_t s = K; s < plan.n_g; ++s) inner_slots.push_back(s);
   fill_levels(all_ops, plan.fwd, false);
+  fill_levels(stored_ops, plan.fwd_stored, false);
   fill_levels(inner_slots, plan.rev, true);
   if ((int)plan.fwd.off.size() - 1 > nu_max || (int)plan.rev.off.size() - 1 > nu_max)
     return fail(ACE_ERR_INVALID_ARG, "internal: too many levels");
@@ -442,8 +541,8 @@ ace_status build_plan(const Spec& spec, const Graph& g, int task_len, Plan& plan
     }
     one_rows[row].push_back({other, s.b, 0});
   }
-  build_tasks(sym_rows, plan.slot_basis, plan.n_g, true, slot_l, slot_r, task_len, plan.sym);
-  build_tasks(one_rows, plan.slot_basis, plan.n_g, false, slot_l, slot_r, task_len, plan.one);
+  build_tasks(sym_rows, plan.slot_basis, plan.n_g, plan.n_stored, true, slot_l, slot_r, task_len, plan.sym);
+  build_tasks(one_rows, plan.slot_basis, plan.n_g, plan.n_stored, false, slot_l, slot_r, task_len, plan.one);
   return ACE_OK;
 }
 

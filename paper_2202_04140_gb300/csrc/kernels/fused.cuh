@@ -6,7 +6,9 @@
 //  1. A rows -> AA[k][e] (leaves), transposed so that the E values of one slot
 //     are contiguous (one vector load per slot).
 //  2. Operand nodes level by level (correlation order ascending):
-//     AA_i = AA_l * AA_r  (Eq. 4).
+//     AA_i = AA_l * AA_r  (Eq. 4), for the stored slots; a graph too large for
+//     shared memory leaves its least-used top operands out ("cold"), and the
+//     entries that need them read their two factors instead.
 //  3. Sink contraction: each lane owns one task (a piece of one row s of the
 //     sink matrix), streams its (column, coefficient) entries, and forms
 //     u = sum_j S_sj AA_j.  Its epilogue adds AA_s (c_s + u/2) (symmetric form)
@@ -40,7 +42,7 @@ struct FusedArgs {
   T* dA;            // adjoint output (GRAD)
   int64_t n_env;
   int64_t n_tiles;
-  int32_t K, n_slots, n_g, n_out;
+  int32_t K, n_slots, n_g, n_out;  // n_slots: slots kept in shared memory (leaves, inner, stored top)
   int32_t gs;  // stride between environments in G (n_g rounded up to 32)
   const int32_t* fwd_slot;
   const int32_t* fwd_l;
@@ -61,6 +63,13 @@ struct FusedArgs {
   const void* vals4;
   const T* vals;  // [entries][NOUT]
   const T* lin;   // [tasks][NOUT] row coefficient of each task (first task of a basis row), else 0
+  // cold tasks (entries read through the two factors of a top operand not in shared memory)
+  const int4* cold_tasks;
+  const int32_t* cold_slice_off;
+  const int32_t* cold_slice_steps;  // steps | (reduction rounds << 16)
+  int32_t n_cold_slices;
+  const uint32_t* cold_cab;         // factor slots ca | cb << 16
+  const T* cold_vals;               // [cold entries][NOUT]
   int32_t check;
   int32_t stage;  // 1: bulk-copy staging of the next tile's A (needs 16-byte aligned A)
   int32_t stage_no_issue;  // test hook: wait for copies that are never issued (exercises the time-out)
@@ -442,13 +451,94 @@ __device__ __forceinline__ void task_entries_packed(const FusedArgs<float>& a, c
   }
 }
 
+// Epilogue of one task (row s, partial row sum u in acc): phi += AA_s (lin +
+// half u), and in the adjoint form g = phibar . (lin + u) goes to the row's
+// accumulator or, for a top operand, to its factors (segmented warp sums over
+// equal "A" targets, one shared-memory update per run).  Called by all lanes.
+template <typename T, int E, int NOUT, bool GRAD, int RO, bool CHECK>
+__device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
+                                              const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT],
+                                              const int4 task, const T (&acc)[E][NOUT], const T (&lin)[NOUT],
+                                              const int rounds, const int lane) {
+  const int gs = a.gs;
+  const bool top = (task.y & 2) != 0;
+  bool valid = task.x >= 0;
+  if constexpr (CHECK) {
+    bool bad = valid && !top && (unsigned)task.x >= (unsigned)a.n_slots;
+    if (valid && top) bad |= (unsigned)task.z >= (unsigned)a.n_g || (unsigned)task.w >= (unsigned)a.n_g;
+    if (GRAD && valid && !top) bad |= (unsigned)task.x >= (unsigned)a.n_g;
+    if (bad) {
+      atomicOr(a.status, kStatusBounds);
+      valid = false;
+    }
+  }
+  const int row = valid ? task.x : 0;
+  // factors of a top operand; its value is their product (a top operand may not be stored)
+  const int pl = (valid && top) ? task.z : 0, pr = (valid && top) ? task.w : 0;
+  T xl[E], xr[E], ap[E];
+  if (top) {
+    load_slot<T, E>(AA + (size_t)pl * E, xl);
+    load_slot<T, E>(AA + (size_t)pr * E, xr);
+#pragma unroll
+    for (int e = 0; e < E; ++e) ap[e] = xl[e] * xr[e];
+  } else {
+    load_slot<T, E>(AA + (size_t)row * E, ap);
+#pragma unroll
+    for (int e = 0; e < E; ++e) xl[e] = xr[e] = T(0);
+  }
+  const T half = GRAD ? T(0.5) : T(1);
+  if (valid) {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) phiacc[e][c].add(ap[e] * fma_t(half, acc[e][c], lin[c]));
+  }
+  if constexpr (GRAD) {
+    // g = phibar . (c_s + u): the adjoint of this task's stored value
+    T g[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) s = fma_t(pb[e * NOUT + c], acc[e][c] + lin[c], s);
+      g[e] = valid ? s : T(0);
+    }
+    // "A" target: the row itself, or the first factor of a top operand.  Lanes
+    // are ordered by A target, so equal targets form runs; a segmented suffix
+    // sum leaves each run's total in its first lane, which does one atomic.
+    int key = valid ? (top ? pl : row) : -1 - lane;
+    T va[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) va[e] = top ? g[e] * xr[e] : g[e];
+    for (int r = 0, d = 1; r < rounds; ++r, d <<= 1) {  // rounds: warp-uniform, from the plan
+      const int k2 = __shfl_down_sync(0xffffffffu, key, d);
+      const bool same = (lane + d < 32) && (k2 == key);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const T y = __shfl_down_sync(0xffffffffu, va[e], d);
+        if (same) va[e] += y;
+      }
+    }
+    const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || kprev != key;
+    if (valid && head) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * gs + key, va[e]);
+    }
+    // "B" target: the second factor of a top operand, one atomic per lane
+    if (valid && top) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * gs + pr, g[e] * xl[e]);
+    }
+  }
+}
+
 template <typename T, int E, int NOUT, bool GRAD, int RO, int NT, bool CHECK>
 __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
                                           const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT]) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
-  const int gs = a.gs;
   // The header of the warp's next slice (its tasks, length and entry offset) is
   // loaded while the current slice runs.
   // slice_steps holds the entry steps in its low 16 bits and the number of
@@ -505,77 +595,55 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
     } else {
       task_entries<T, E, NOUT, CHECK>(a, AA, off, steps, lane, acc);
     }
-    const bool top = (task.y & 2) != 0;
-    bool valid = task.x >= 0;
-    if constexpr (CHECK) {
-      bool bad = valid && (unsigned)task.x >= (unsigned)a.n_slots;
-      if (GRAD && valid && top) bad |= (unsigned)task.z >= (unsigned)a.n_g || (unsigned)task.w >= (unsigned)a.n_g;
-      if (GRAD && valid && !top) bad |= (unsigned)task.x >= (unsigned)a.n_g;
-      if (bad) {
-        atomicOr(a.status, kStatusBounds);
-        valid = false;
-      }
-    }
-    const int row = valid ? task.x : 0;
     if constexpr (NOUT > 1) load_vals<T, NOUT>(a.lin + ((size_t)sl * 32 + lane) * NOUT, lin);
-    // factors of a top operand (adjoint form); AA of the row is their product
-    const int pl = (GRAD && valid && top) ? task.z : 0, pr = (GRAD && valid && top) ? task.w : 0;
-    T xl[E], xr[E], ap[E];
-    if (GRAD && top) {
-      load_slot<T, E>(AA + (size_t)pl * E, xl);
-      load_slot<T, E>(AA + (size_t)pr * E, xr);
+    task_epilogue<T, E, NOUT, GRAD, RO, CHECK>(a, AA, G, pb, phiacc, task, acc, lin, rounds, lane);
+  }
+}
+
+// The cold tasks: entries whose column is a top operand not kept in shared
+// memory read that operand's two factors (ca, cb) and use their product.  Same
+// epilogue as the other tasks (no row coefficient).
+template <typename T, int E, int NOUT, bool GRAD, int RO, int NT, bool CHECK>
+__device__ __forceinline__ void run_cold_tasks(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
+                                               const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT]) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  for (int sl = warp; sl < a.n_cold_slices; sl += NW) {
+    const int4 task = __ldg(a.cold_tasks + (size_t)sl * 32 + lane);
+    const int hdr = __ldg(a.cold_slice_steps + sl);
+    const int steps = hdr & 0xffff, rounds = hdr >> 16;
+    const int32_t off = __ldg(a.cold_slice_off + sl);
+    T acc[E][NOUT];
 #pragma unroll
-      for (int e = 0; e < E; ++e) ap[e] = xl[e] * xr[e];
-    } else {
-      load_slot<T, E>(AA + (size_t)row * E, ap);
+    for (int e = 0; e < E; ++e)
 #pragma unroll
-      for (int e = 0; e < E; ++e) xl[e] = xr[e] = T(0);
-    }
-    const T half = GRAD ? T(0.5) : T(1);
-    if (valid) {
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-#pragma unroll
-        for (int c = 0; c < NOUT; ++c) phiacc[e][c].add(ap[e] * fma_t(half, acc[e][c], lin[c]));
-    }
-    if constexpr (GRAD) {
-      // g = phibar . (c_s + u): the adjoint of this task's stored value
-      T g[E];
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        T s = T(0);
-#pragma unroll
-        for (int c = 0; c < NOUT; ++c) s = fma_t(pb[e * NOUT + c], acc[e][c] + lin[c], s);
-        g[e] = valid ? s : T(0);
-      }
-      // "A" target: the row itself, or the first factor of a top operand.  Lanes
-      // are ordered by A target, so equal targets form runs; a segmented suffix
-      // sum leaves each run's total in its first lane, which does one atomic.
-      int key = valid ? (top ? pl : row) : -1 - lane;
-      T va[E];
-#pragma unroll
-      for (int e = 0; e < E; ++e) va[e] = top ? g[e] * xr[e] : g[e];
-      for (int r = 0, d = 1; r < rounds; ++r, d <<= 1) {  // rounds: warp-uniform, from the plan
-        const int k2 = __shfl_down_sync(0xffffffffu, key, d);
-        const bool same = (lane + d < 32) && (k2 == key);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const T y = __shfl_down_sync(0xffffffffu, va[e], d);
-          if (same) va[e] += y;
+      for (int c = 0; c < NOUT; ++c) acc[e][c] = T(0);
+    for (int k = 0; k < steps; ++k) {
+      const size_t idx = (size_t)off + (size_t)k * 32 + lane;
+      const uint32_t q = __ldg(a.cold_cab + idx);
+      int ca = (int)(q & 0xffffu), cb = (int)(q >> 16);
+      if constexpr (CHECK) {
+        if ((unsigned)ca >= (unsigned)a.n_slots || (unsigned)cb >= (unsigned)a.n_slots) {
+          atomicOr(a.status, kStatusBounds);
+          ca = cb = 0;
         }
       }
-      const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-      const bool head = lane == 0 || kprev != key;
-      if (valid && head) {
+      T v[NOUT], xa[E], xb[E];
+      load_vals<T, NOUT>(a.cold_vals + idx * NOUT, v);
+      load_slot<T, E>(AA + (size_t)ca * E, xa);
+      load_slot<T, E>(AA + (size_t)cb * E, xb);
 #pragma unroll
-        for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * gs + key, va[e]);
-      }
-      // "B" target: the second factor of a top operand, one atomic per lane
-      if (valid && top) {
+      for (int e = 0; e < E; ++e) {
+        const T x = xa[e] * xb[e];
 #pragma unroll
-        for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * gs + pr, g[e] * xl[e]);
+        for (int c = 0; c < NOUT; ++c) acc[e][c] = fma_t(v[c], x, acc[e][c]);
       }
     }
+    T lin[NOUT];
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) lin[c] = T(0);
+    task_epilogue<T, E, NOUT, GRAD, RO, CHECK>(a, AA, G, pb, phiacc, task, acc, lin, rounds, lane);
   }
 }
 
@@ -690,8 +758,13 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
     }
     // 3. sink contraction + readout (+ adjoint seeds)
     Acc<T, RO> phiacc[E][NOUT];
-    if (a.check) run_tasks<T, E, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc);
-    else run_tasks<T, E, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc);
+    if (a.check) {
+      run_tasks<T, E, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc);
+      run_cold_tasks<T, E, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc);
+    } else {
+      run_tasks<T, E, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc);
+      run_cold_tasks<T, E, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc);
+    }
     __syncthreads();
     // 4. adjoint through the inner operand nodes, order descending: one lane per
     //    (consumer i, partner p, target x) triple forms G_i AA_p; triples of equal

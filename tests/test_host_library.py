@@ -112,11 +112,14 @@ def test_workload_digests(name):
 
 def plan_arrays(dag, mode):
     P = {k: L.ace_dag_plan_array(dag.handle, k) for k in
-         ["slot_node", "slot_basis", "n_g", "fwd_slot", "fwd_l", "fwd_r", "fwd_off", "rev_slot", "rev_l", "rev_r",
-          "rev_off", "pull_tgt", "pull_src", "pull_par", "pull_lvl"]}
-    for k in ["tasks", "slice_off", "slice_steps", "col", "ebasis", "ew2"]:
+         ["slot_node", "slot_basis", "n_g", "n_stored", "fwd_slot", "fwd_l", "fwd_r", "fwd_off", "rev_slot",
+          "rev_l", "rev_r", "rev_off", "pull_tgt", "pull_src", "pull_par", "pull_lvl", "fwd_stored_slot",
+          "fwd_stored_l", "fwd_stored_r", "fwd_stored_off"]}
+    for k in ["tasks", "slice_off", "slice_steps", "col", "ebasis", "ew2", "cold_tasks", "cold_slice_off",
+              "cold_slice_steps", "cold_ca", "cold_cb", "cold_ebasis", "cold_ew2"]:
         P[k] = L.ace_dag_plan_array(dag.handle, f"{mode}_{k}")
     P["tasks"] = P["tasks"].reshape(-1, 4)
+    P["cold_tasks"] = P["cold_tasks"].reshape(-1, 4)
     return P
 
 
@@ -125,32 +128,47 @@ def emulate(dag, mode, A, c, phibar=None, sweep="push"):
     n_env, K = A.shape
     n_slots = len(P["slot_node"])
     n_g = int(P["n_g"][0])
+    n_stored = int(P["n_stored"][0])
     c = c.reshape(dag.n_basis, -1)
-    AA = np.zeros((n_env, n_slots))
+    # the tile-per-lane kernel's view: only stored slots are computed, by the stored levels
+    AA = np.full((n_env, n_slots), np.nan)
     AA[:, :K] = A
-    off = P["fwd_off"]
+    off = P["fwd_stored_off"]
     for lv in range(len(off) - 1):
         s = slice(off[lv], off[lv + 1])
-        AA[:, P["fwd_slot"][s]] = AA[:, P["fwd_l"][s]] * AA[:, P["fwd_r"][s]]
-    eb = P["ebasis"]
-    vals = np.where(eb[:, None] >= 0, c[np.maximum(eb, 0)], 0.0) * np.where(P["ew2"] > 0, 2.0, 1.0)[:, None]
+        AA[:, P["fwd_stored_slot"][s]] = AA[:, P["fwd_stored_l"][s]] * AA[:, P["fwd_stored_r"][s]]
+    assert not np.isnan(AA[:, :n_stored]).any()
     lin = np.where(P["slot_basis"][:, None] >= 0, c[np.maximum(P["slot_basis"], 0)], 0.0)
-    n_tasks = P["tasks"].shape[0]
-    task_of = np.zeros(len(eb), dtype=np.int64)
-    for s_ in range(len(P["slice_steps"])):
-        o, st = P["slice_off"][s_], P["slice_steps"][s_]
-        idx = o + np.arange(32 * st)
-        task_of[idx] = s_ * 32 + (np.arange(32 * st) % 32)
-    u = np.zeros((n_env, n_tasks, c.shape[1]))
-    for ch in range(c.shape[1]):
-        M = sp.csr_matrix((vals[:, ch], (task_of, np.arange(len(eb)))), shape=(n_tasks, len(eb)))
-        u[:, :, ch] = (M @ AA[:, P["col"]].T).T
-    T = P["tasks"]
+
+    def sums(pre, cols):
+        """Per task and channel: the sum over its entries of coefficient x column value."""
+        eb = P[pre + "ebasis"]
+        vals = np.where(eb[:, None] >= 0, c[np.maximum(eb, 0)], 0.0) * np.where(P[pre + "ew2"] > 0, 2.0, 1.0)[:, None]
+        n_tasks = P[pre + "tasks"].shape[0]
+        task_of = np.zeros(len(eb), dtype=np.int64)
+        for s_ in range(len(P[pre + "slice_steps"])):
+            o, st = P[pre + "slice_off"][s_], P[pre + "slice_steps"][s_]
+            idx = o + np.arange(32 * st)
+            task_of[idx] = s_ * 32 + (np.arange(32 * st) % 32)
+        u = np.zeros((n_env, n_tasks, c.shape[1]))
+        for ch in range(c.shape[1]):
+            M = sp.csr_matrix((vals[:, ch], (task_of, np.arange(len(eb)))), shape=(n_tasks, len(eb)))
+            u[:, :, ch] = (M @ cols.T).T
+        return u
+
+    ucold = sums("cold_", np.nan_to_num(AA[:, P["cold_ca"]]) * np.nan_to_num(AA[:, P["cold_cb"]]))
+    assert not np.isnan(AA[:, P["col"]]).any()
+    u = np.concatenate([sums("", AA[:, P["col"]]), ucold], axis=1)
+    T = np.concatenate([P["tasks"], P["cold_tasks"]], axis=0)
+    assert np.all((T[len(P["tasks"]):, 1] & 5) == 0)          # cold tasks carry no row coefficient
     valid = T[:, 0] >= 0
     row, first, top = T[:, 0], (T[:, 1] & 1) > 0, (T[:, 1] & 2) > 0
     linr = np.where((valid & first)[:, None], lin[np.maximum(row, 0)], 0.0)
     half = 0.5 if mode == "sym" else 1.0
-    ap = AA[:, np.maximum(row, 0)]
+    # a top operand's value from its factors (it may not be stored)
+    ap = np.where(top[None, :], AA[:, np.maximum(T[:, 2], 0)] * AA[:, np.maximum(T[:, 3], 0)],
+                  AA[:, np.maximum(row, 0)])
+    ap = np.where(valid[None, :], ap, 0.0)
     phi = np.einsum("et,etc->ec", ap * valid, linr[None] + half * u)
     if mode == "one":
         return phi, None
@@ -181,13 +199,27 @@ def emulate(dag, mode, A, c, phibar=None, sweep="push"):
     return phi, G[:, :K]
 
 
-@pytest.mark.parametrize("name,n_out,rule", [("plain_fp64_k64", 1, "balanced"), ("fwd_grad_k392", 1, "balanced"),
-                                             ("fwd_grad_k392", 3, "peel"), ("uneven_16ch_k392", 16, "balanced")])
-def test_plan_emulation_matches_oracle(name, n_out, rule):
+@pytest.mark.parametrize("name,n_out,rule,stored", [("plain_fp64_k64", 1, "balanced", None),
+                                                    ("fwd_grad_k392", 1, "balanced", None),
+                                                    ("fwd_grad_k392", 3, "peel", None),
+                                                    ("uneven_16ch_k392", 16, "balanced", None),
+                                                    ("fwd_grad_k392", 1, "balanced", 600),
+                                                    ("plain_fp64_k64", 2, "peel", 70)])
+def test_plan_emulation_matches_oracle(name, n_out, rule, stored, monkeypatch):
+    """The tile-per-lane kernel's arithmetic on the exported plan; with `stored` the plan keeps only
+    that many slots and reads the other top operands through their factors (cold tasks)."""
+    if stored is not None:
+        monkeypatch.setenv("ACE_PLAN_STORED", str(stored))
     w = W.WORKLOADS[name]
     o = workload_index_set(w)
     s = Spec.from_workload(w)
     dag = Dag(s, rule=rule)
+    n_stored = int(L.ace_dag_plan_array(dag.handle, "n_stored")[0])
+    if stored is not None:
+        assert n_stored == stored < dag.n_slots
+        assert len(L.ace_dag_plan_array(dag.handle, "sym_cold_ca")) > 0
+    else:
+        assert n_stored == dag.n_slots
     A = W.draw_A(4, s.K, env_scale=w.env_scale)
     c = W.draw_c(o.deg, n_out)
     pb = np.random.default_rng(9).standard_normal((4, n_out))
