@@ -42,6 +42,15 @@ struct Entry {
 // slice that cannot be completed without a collision takes the next tasks.
 constexpr int kWindow = 512;
 
+// Bank schedule of the entries: the tile-per-lane kernel gathers E values per
+// lane and entry; with E >= 4 (16 bytes or more per lane) a warp's load is
+// served a quarter-warp at a time, 8 lanes over 8 groups of 16-byte banks, so
+// the schedule keeps the columns of every 8 consecutive lanes in distinct
+// groups (column mod 8) or equal (broadcast).  Tiles of 4 environments are the
+// target of the plan (see Plan::n_stored).
+constexpr int kPhaseLanes = 8;
+constexpr int kBankGroups = 8;
+
 void form_slices(const std::vector<Task>& tasks, const std::vector<int32_t>& order, const std::vector<int32_t>& len,
                  bool atomics, std::vector<std::vector<int32_t>>& slices) {
   std::vector<uint8_t> taken(order.size(), 0);
@@ -287,7 +296,7 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
         lanes.push_back(&lane_store[j]);
         ts.n_entries += protos[ti].len;
       }
-      interleave(lanes, ts.slice_steps[s], 16, 16, n_stored, ts.slice_off[s], ts);
+      interleave(lanes, ts.slice_steps[s], kPhaseLanes, kBankGroups, n_stored, ts.slice_off[s], ts);
     }
   }
 
