@@ -347,9 +347,21 @@ ace_status ensure_uploaded(ace_dag* d, cudaStream_t st) {
   if ((s = upload_vec(d, p.rev.slot, &d->rev_slot, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.rev.l, &d->rev_l, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.rev.r, &d->rev_r, st)) != ACE_OK) return s;
+  // {consumer, partner, target, rounds}: rounds of the segmented warp sum of the 32-triple chunk
+  // (counted from the level's first triple, as the kernel walks them) holding the triple
   d->pull_host.resize(p.pull.src.size());
-  for (size_t j = 0; j < p.pull.src.size(); ++j)
-    d->pull_host[j] = make_int4(p.pull.src[j], p.pull.par[j], p.pull.tgt[j], 0);
+  for (size_t lv = 0; lv + 1 < p.pull.lvl.size(); ++lv)
+    for (int32_t c0 = p.pull.lvl[lv]; c0 < p.pull.lvl[lv + 1]; c0 += 32) {
+      const int32_t c1 = std::min<int32_t>(c0 + 32, p.pull.lvl[lv + 1]);
+      int run = 1, longest = 1;
+      for (int32_t j = c0 + 1; j < c1; ++j) {
+        run = p.pull.tgt[j] == p.pull.tgt[j - 1] ? run + 1 : 1;
+        longest = std::max(longest, run);
+      }
+      int rounds = 0;
+      while ((1 << rounds) < longest) ++rounds;
+      for (int32_t j = c0; j < c1; ++j) d->pull_host[j] = make_int4(p.pull.src[j], p.pull.par[j], p.pull.tgt[j], rounds);
+    }
   if ((s = upload_vec(d, d->pull_host, &d->pull, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, d->g.left, &d->node_left, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, d->g.right, &d->node_right, st)) != ACE_OK) return s;

@@ -47,7 +47,7 @@ struct FusedArgs {
   const int32_t* fwd_slot;
   const int32_t* fwd_l;
   const int32_t* fwd_r;
-  const int4* pull;  // adjoint sweep: {inner consumer, partner factor, target, 0} by target level
+  const int4* pull;  // adjoint sweep: {inner consumer, partner factor, target, rounds} by target level
   int32_t fwd_off[kMaxLevels + 1];
   int32_t pull_lvl[kMaxLevels + 1];
   int32_t n_fwd_levels, n_pull_levels;
@@ -324,6 +324,7 @@ struct Acc<double, kReadPlain> : AccD<double> {};
 constexpr int kBatch = 4;
 // Operand nodes per thread whose indices are loaded together in the level loops.
 constexpr int kNodeBatch = 4;
+constexpr int kFwdBatch = 8;  // the tile-per-lane kernel's forward levels
 
 template <typename T, int E, int NOUT, bool CHECK>
 __device__ __forceinline__ void use_entry(const FusedArgs<T>& a, const T* __restrict__ AA, int j, const T (&v)[NOUT],
@@ -727,11 +728,11 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
     // 2. operand nodes, order ascending (Eq. 4)
     for (int lv = 0; lv < a.n_fwd_levels; ++lv) {
       const int b = a.fwd_off[lv], eidx = a.fwd_off[lv + 1];
-      // kNodeBatch nodes per thread at a time, their indices loaded together
-      for (int i0 = b + tid; i0 < eidx; i0 += NT * kNodeBatch) {
-        int s[kNodeBatch], l[kNodeBatch], r[kNodeBatch];
+      // kFwdBatch nodes per thread at a time, their indices loaded together
+      for (int i0 = b + tid; i0 < eidx; i0 += NT * kFwdBatch) {
+        int s[kFwdBatch], l[kFwdBatch], r[kFwdBatch];
 #pragma unroll
-        for (int u = 0; u < kNodeBatch; ++u) {
+        for (int u = 0; u < kFwdBatch; ++u) {
           const int i = i0 + u * NT;
           const bool in = i < eidx;
           s[u] = in ? __ldg(a.fwd_slot + i) : -1;
@@ -739,7 +740,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
           r[u] = in ? __ldg(a.fwd_r + i) : 0;
         }
 #pragma unroll
-        for (int u = 0; u < kNodeBatch; ++u) {
+        for (int u = 0; u < kFwdBatch; ++u) {
           if (s[u] < 0) continue;
           if (a.check && ((unsigned)s[u] >= (unsigned)a.n_slots || (unsigned)l[u] >= (unsigned)a.n_slots ||
                           (unsigned)r[u] >= (unsigned)a.n_slots)) {
@@ -772,9 +773,14 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
     if constexpr (GRAD) {
       for (int lv = 0; lv < a.n_pull_levels; ++lv) {
         const int end = a.pull_lvl[lv + 1];
+        // the next chunk's triples load while this chunk is summed
+        int4 qn = a.pull_lvl[lv] + warp * 32 + lane < end ? __ldg(a.pull + a.pull_lvl[lv] + warp * 32 + lane)
+                                                          : make_int4(0, 0, -1, 0);
         for (int j0 = a.pull_lvl[lv] + warp * 32; j0 < end; j0 += NT) {
-          const int j = j0 + lane;
-          int4 q = j < end ? __ldg(a.pull + j) : make_int4(0, 0, -1, 0);
+          int4 q = qn;
+          if (j0 + NT < end) qn = j0 + NT + lane < end ? __ldg(a.pull + j0 + NT + lane) : make_int4(0, 0, -1, 0);
+          // rounds of the segmented sum: stored by the plan with every triple of the chunk
+          const int rounds = __shfl_sync(0xffffffffu, q.w, 0);
           bool valid = q.z >= 0;
           if (a.check && valid &&
               ((unsigned)q.x >= (unsigned)a.n_g || (unsigned)q.y >= (unsigned)a.n_g || (unsigned)q.z >= (unsigned)a.n_g)) {
@@ -787,8 +793,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = valid ? G[(size_t)e * a.gs + q.x] * xp[e] : T(0);
           const int key = q.z;
-#pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
+          for (int r = 0, d = 1; r < rounds; ++r, d <<= 1) {
             const int k2 = __shfl_down_sync(0xffffffffu, key, d);
             const bool same = (lane + d < 32) && (k2 == key);
 #pragma unroll
