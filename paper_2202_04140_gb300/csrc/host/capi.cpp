@@ -467,7 +467,10 @@ bool checked_mode() {
 // Environments per CTA: the largest compiled E whose shared-memory tile fits,
 // with E * NOUT <= 64 accumulators per lane, and not so large that fewer tiles
 // than SMs remain.
-ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t n_env, int E_force, int* E_out,
+// The shared-memory layout depends on the thread count of the exact kernel that
+// will run (its phi partials take one row per warp), so the lookup uses the
+// request's readout mode.
+ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int ro, int64_t n_env, int E_force, int* E_out,
                        int* nt_out, size_t* smem_out, const void** kern_out, bool* stage_out) {
   const int cands_f32_1[] = {16, 8, 4, 2, 1};
   const int cands_f32_16[] = {4, 2, 1};
@@ -489,7 +492,7 @@ ace_status choose_tile(const ace_dag* d, int dtype, int npad, bool grad, int64_t
     if (E_force > 0 && E != E_force) continue;
     if (E_force <= 0 && E > 1 && E > per_sm) continue;
     int nt = 0;
-    const void* k = fused_kernel_ptr(dtype, E, npad, grad, 0, &nt);
+    const void* k = fused_kernel_ptr(dtype, E, npad, grad, ro, &nt);
     if (!k) continue;
     // with the bulk-copy staging buffer when it fits, else without
     bool stage = true;
@@ -609,7 +612,8 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
   size_t smem = 0;
   const void* k = nullptr;
   bool stage = false;
-  s = dt.col16 ? choose_tile(d, dtype, npad, grad, n_env, E_force, &E, &nt, &smem, &k, &stage)
+  const int ro = dtype == ACE_F32 ? readout : 0;
+  s = dt.col16 ? choose_tile(d, dtype, npad, grad, ro, n_env, E_force, &E, &nt, &smem, &k, &stage)
                : fail(ACE_ERR_UNSUPPORTED, "more than 65535 stored values per environment");
   if (s != ACE_OK) {
     // the stored values of one environment do not fit on chip: keep them in global memory
@@ -617,8 +621,6 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     return s;
   }
   if (const char* v = std::getenv("ACE_STAGE")) stage = stage && v[0] != '0';  // ACE_STAGE=0: plain loads of A
-  const int ro = dtype == ACE_F32 ? readout : 0;
-  k = fused_kernel_ptr(dtype, E, npad, grad, ro, &nt);
   if (!k) return fail(ACE_ERR_UNSUPPORTED, "no kernel for this readout mode");
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");

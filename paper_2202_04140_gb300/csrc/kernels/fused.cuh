@@ -343,10 +343,11 @@ __device__ __forceinline__ void use_entry(const FusedArgs<T>& a, const T* __rest
     for (int c = 0; c < NOUT; ++c) acc[e][c] = fma_t(v[c], x[e], acc[e][c]);
 }
 
-template <typename T, int E, int NOUT, bool CHECK, typename C>
+template <typename T, int E, int NOUT, int NS, bool CHECK, typename C>
 __device__ __forceinline__ void task_entries_impl(const FusedArgs<T>& a, const T* __restrict__ AA,
                                                   const C* __restrict__ colp, const T* __restrict__ valp, int steps,
                                                   T (&acc)[E][NOUT]) {
+  // NOUT channels of an entry, at valp + entry * NS (NS: channels stored per entry)
   // colp / valp point at this lane's first entry; entry k is 32 k further on.
   // Whole batches of kBatch entries run without per-entry guards, the loads of
   // batch b + 1 in flight while batch b is used; the last steps % kBatch
@@ -365,7 +366,7 @@ __device__ __forceinline__ void task_entries_impl(const FusedArgs<T>& a, const T
       T vn[kBatch][NOUT];
       if (b + 1 < nb) {
         const C* cp = colp + (size_t)(b + 1) * kBatch * 32;
-        const T* vp = valp + (size_t)(b + 1) * kBatch * 32 * NOUT;
+        const T* vp = valp + (size_t)(b + 1) * kBatch * 32 * NS;
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           nxt[u] = (int)__ldg(cp + u * 32);
@@ -374,7 +375,7 @@ __device__ __forceinline__ void task_entries_impl(const FusedArgs<T>& a, const T
       }
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
-        if constexpr (NOUT > 1) load_vals<T, NOUT>(valp + ((size_t)b * kBatch + u) * 32 * NOUT, vc[u]);
+        if constexpr (NOUT > 1) load_vals<T, NOUT>(valp + ((size_t)b * kBatch + u) * 32 * NS, vc[u]);
         use_entry<T, E, NOUT, CHECK>(a, AA, cur[u], vc[u], acc);
       }
 #pragma unroll
@@ -390,19 +391,19 @@ __device__ __forceinline__ void task_entries_impl(const FusedArgs<T>& a, const T
     if (done + u < steps) {
       const int j = (int)__ldg(colp + (size_t)(done + u) * 32);
       T v[NOUT];
-      load_vals<T, NOUT>(valp + (size_t)(done + u) * 32 * NOUT, v);
+      load_vals<T, NOUT>(valp + (size_t)(done + u) * 32 * NS, v);
       use_entry<T, E, NOUT, CHECK>(a, AA, j, v, acc);
     }
   }
 }
 
-template <typename T, int E, int NOUT, bool CHECK>
+template <typename T, int E, int NOUT, int NS, bool CHECK>
 __device__ __forceinline__ void task_entries(const FusedArgs<T>& a, const T* __restrict__ AA, int32_t off,
-                                             int steps, int lane, T (&acc)[E][NOUT]) {
+                                             int steps, int lane, int c0, T (&acc)[E][NOUT]) {
   // 16-bit columns: a graph whose stored values per environment exceed 65535
   // could not hold one environment in shared memory anyway.
-  const T* valp = a.vals + ((size_t)off + lane) * NOUT;
-  task_entries_impl<T, E, NOUT, CHECK>(a, AA, a.col16 + off + lane, valp, steps, acc);
+  const T* valp = a.vals + ((size_t)off + lane) * NS + c0;
+  task_entries_impl<T, E, NOUT, NS, CHECK>(a, AA, a.col16 + off + lane, valp, steps, acc);
 }
 
 // Four packed entries of one lane: the first n (warp-uniform) are used.
@@ -456,11 +457,13 @@ __device__ __forceinline__ void task_entries_packed(const FusedArgs<float>& a, c
 // half u), and in the adjoint form g = phibar . (lin + u) goes to the row's
 // accumulator or, for a top operand, to its factors (segmented warp sums over
 // equal "A" targets, one shared-memory update per run).  Called by all lanes.
-template <typename T, int E, int NOUT, bool GRAD, int RO, bool CHECK>
+template <typename T, int E, int NOUT, int NS, bool GRAD, int RO, bool CHECK>
 __device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
                                               const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT],
                                               const int4 task, const T (&acc)[E][NOUT], const T (&lin)[NOUT],
-                                              const int rounds, const int lane) {
+                                              const int rounds, const int lane, const int c0) {
+  // channels c0 .. c0 + NOUT of NS; the adjoint seed g sums over them (the blocks of a
+  // request add up in the accumulators)
   const int gs = a.gs;
   const bool top = (task.y & 2) != 0;
   bool valid = task.x >= 0;
@@ -501,7 +504,7 @@ __device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __
     for (int e = 0; e < E; ++e) {
       T s = T(0);
 #pragma unroll
-      for (int c = 0; c < NOUT; ++c) s = fma_t(pb[e * NOUT + c], acc[e][c] + lin[c], s);
+      for (int c = 0; c < NOUT; ++c) s = fma_t(pb[e * NS + c0 + c], acc[e][c] + lin[c], s);
       g[e] = valid ? s : T(0);
     }
     // "A" target: the row itself, or the first factor of a top operand.  Lanes
@@ -534,9 +537,9 @@ __device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __
   }
 }
 
-template <typename T, int E, int NOUT, bool GRAD, int RO, int NT, bool CHECK>
+template <typename T, int E, int NOUT, int NS, bool GRAD, int RO, int NT, bool CHECK>
 __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
-                                          const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT]) {
+                                          const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT], const int c0) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
@@ -547,7 +550,7 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
   // FP32 with one channel reads the packed entry groups, whose offsets replace
   // the entry offsets; the first group of the next slice is loaded before the
   // current slice's epilogue.
-  constexpr bool PACK = sizeof(T) == 4 && NOUT == 1;
+  constexpr bool PACK = sizeof(T) == 4 && NS == 1;
   const int32_t* offs = PACK ? a.off4 : a.slice_off;
   int4 task_n = make_int4(-1, 0, -1, -1);
   int hdr_n = 0;
@@ -559,7 +562,7 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
     task_n = __ldg(a.tasks + (size_t)warp * 32 + lane);
     hdr_n = __ldg(a.slice_steps + warp);
     off_n = __ldg(offs + warp);
-    if constexpr (NOUT == 1) lin_n = __ldg(a.lin + (size_t)warp * 32 + lane);
+    if constexpr (NS == 1) lin_n = __ldg(a.lin + (size_t)warp * 32 + lane);
     if constexpr (PACK) {
       if ((hdr_n & 0xffff) > 0) {
         c_n = __ldg(a.col4 + off_n + lane);
@@ -572,15 +575,15 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
     const int steps = hdr_n & 0xffff, rounds = hdr_n >> 16;
     const int32_t off = off_n;
     T lin[NOUT];
-    if constexpr (NOUT == 1) lin[0] = lin_n;
-    const uint2 c0 = c_n;
-    const float4 v0 = v_n;
+    if constexpr (NS == 1) lin[0] = lin_n;
+    const uint2 grp_c = c_n;  // the slice's first packed entry group
+    const float4 grp_v = v_n;
     const bool has_next = sl + NW < a.n_slices;
     if (has_next) {
       task_n = __ldg(a.tasks + (size_t)(sl + NW) * 32 + lane);
       hdr_n = __ldg(a.slice_steps + sl + NW);
       off_n = __ldg(offs + sl + NW);
-      if constexpr (NOUT == 1) lin_n = __ldg(a.lin + (size_t)(sl + NW) * 32 + lane);
+      if constexpr (NS == 1) lin_n = __ldg(a.lin + (size_t)(sl + NW) * 32 + lane);
     }
     T acc[E][NOUT];
 #pragma unroll
@@ -588,25 +591,26 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) acc[e][c] = T(0);
     if constexpr (PACK) {
-      task_entries_packed<E, CHECK>(a, AA, off, steps, lane, c0, v0, acc);
+      task_entries_packed<E, CHECK>(a, AA, off, steps, lane, grp_c, grp_v, acc);
       if (has_next && (hdr_n & 0xffff) > 0) {
         c_n = __ldg(a.col4 + off_n + lane);
         v_n = __ldg(static_cast<const float4*>(a.vals4) + off_n + lane);
       }
     } else {
-      task_entries<T, E, NOUT, CHECK>(a, AA, off, steps, lane, acc);
+      task_entries<T, E, NOUT, NS, CHECK>(a, AA, off, steps, lane, c0, acc);
     }
-    if constexpr (NOUT > 1) load_vals<T, NOUT>(a.lin + ((size_t)sl * 32 + lane) * NOUT, lin);
-    task_epilogue<T, E, NOUT, GRAD, RO, CHECK>(a, AA, G, pb, phiacc, task, acc, lin, rounds, lane);
+    if constexpr (NS > 1) load_vals<T, NOUT>(a.lin + ((size_t)sl * 32 + lane) * NS + c0, lin);
+    task_epilogue<T, E, NOUT, NS, GRAD, RO, CHECK>(a, AA, G, pb, phiacc, task, acc, lin, rounds, lane, c0);
   }
 }
 
 // The cold tasks: entries whose column is a top operand not kept in shared
 // memory read that operand's two factors (ca, cb) and use their product.  Same
 // epilogue as the other tasks (no row coefficient).
-template <typename T, int E, int NOUT, bool GRAD, int RO, int NT, bool CHECK>
+template <typename T, int E, int NOUT, int NS, bool GRAD, int RO, int NT, bool CHECK>
 __device__ __forceinline__ void run_cold_tasks(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
-                                               const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT]) {
+                                               const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT],
+                                               const int c0) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
@@ -631,7 +635,7 @@ __device__ __forceinline__ void run_cold_tasks(const FusedArgs<T>& a, const T* _
         }
       }
       T v[NOUT], xa[E], xb[E];
-      load_vals<T, NOUT>(a.cold_vals + idx * NOUT, v);
+      load_vals<T, NOUT>(a.cold_vals + idx * NS + c0, v);
       load_slot<T, E>(AA + (size_t)ca * E, xa);
       load_slot<T, E>(AA + (size_t)cb * E, xb);
 #pragma unroll
@@ -644,7 +648,7 @@ __device__ __forceinline__ void run_cold_tasks(const FusedArgs<T>& a, const T* _
     T lin[NOUT];
 #pragma unroll
     for (int c = 0; c < NOUT; ++c) lin[c] = T(0);
-    task_epilogue<T, E, NOUT, GRAD, RO, CHECK>(a, AA, G, pb, phiacc, task, acc, lin, rounds, lane);
+    task_epilogue<T, E, NOUT, NS, GRAD, RO, CHECK>(a, AA, G, pb, phiacc, task, acc, lin, rounds, lane, c0);
   }
 }
 
@@ -757,14 +761,29 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
       }
       __syncthreads();
     }
-    // 3. sink contraction + readout (+ adjoint seeds)
-    Acc<T, RO> phiacc[E][NOUT];
-    if (a.check) {
-      run_tasks<T, E, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc);
-      run_cold_tasks<T, E, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc);
-    } else {
-      run_tasks<T, E, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc);
-      run_cold_tasks<T, E, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc);
+    // 3. sink contraction + readout (+ adjoint seeds), in blocks of NB channels: the
+    //    accumulators of a block live in registers; each block's per-warp phi partials
+    //    go to shared memory.  Plain and FP64-partial readouts take blocks of 8 (fewer
+    //    registers, more warps); the compensated readout keeps all channels in one pass
+    //    (measured faster: its second pass costs more than the registers it frees).
+    constexpr int NB = (NOUT > 8 && RO != kReadComp) ? 8 : NOUT;
+    for (int c0 = 0; c0 < NOUT; c0 += NB) {
+      Acc<T, RO> phiacc[E][NB];
+      if (a.check) {
+        run_tasks<T, E, NB, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc, c0);
+        run_cold_tasks<T, E, NB, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc, c0);
+      } else {
+        run_tasks<T, E, NB, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc, c0);
+        run_cold_tasks<T, E, NB, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc, c0);
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+#pragma unroll
+          for (int d = 16; d >= 1; d >>= 1) phiacc[e][c].shfl_down_add(d);
+          if (lane == 0) red[(warp * E + e) * NOUT + c0 + c] = phiacc[e][c].value();
+        }
     }
     __syncthreads();
     // 4. adjoint through the inner operand nodes, order descending: one lane per
@@ -816,17 +835,8 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
         if (env < a.n_env) a.dA[env * K + k] = G[(size_t)e * a.gs + k];
       }
     }
-    // 5. phi: warp reduction, then the warps in fixed order
+    // 5. phi: the per-warp partials (already in shared memory) summed in fixed warp order
     if (a.phi) {
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-#pragma unroll
-        for (int c = 0; c < NOUT; ++c) {
-#pragma unroll
-          for (int d = 16; d >= 1; d >>= 1) phiacc[e][c].shfl_down_add(d);
-          if (lane == 0) red[(warp * E + e) * NOUT + c] = phiacc[e][c].value();
-        }
-      __syncthreads();
       for (int i = tid; i < E * NOUT; i += NT) {
         const int e = i / NOUT, c = i - e * NOUT;
         double s = 0.0;
