@@ -117,14 +117,17 @@ void form_slices(const std::vector<Task>& tasks, const std::vector<int32_t>& ord
 // share it), else, if it has no slack, takes a conflicting entry, and otherwise
 // waits a step.  A waiting or finished lane reads a zero coefficient at a
 // column already given out (a broadcast) or in a group nobody uses.
+// key(entry) is the slot the entry gathers (the scheduled column); emit(lane j,
+// step k, entry or nullptr, padding column) writes the schedule.
+template <typename Key, typename Emit>
 void interleave(const std::vector<const std::vector<Entry>*>& lane_entries, int32_t steps, int phase_lanes,
-                int bank_mod, int32_t n_slots, int64_t off, TaskSet& ts) {
+                int bank_mod, int32_t n_slots, Key key, Emit emit) {
   const int nl = (int)lane_entries.size();
   // remaining entries of every lane as (column, entry index), sorted by column
   std::vector<std::vector<std::pair<int32_t, int32_t>>> rem(32);
   for (int j = 0; j < nl; ++j) {
     const auto& v = *lane_entries[j];
-    for (int32_t q = 0; q < (int32_t)v.size(); ++q) rem[j].push_back({v[q].col, q});
+    for (int32_t q = 0; q < (int32_t)v.size(); ++q) rem[j].push_back({key(v[q]), q});
     std::sort(rem[j].begin(), rem[j].end());
   }
   std::vector<int32_t> chosen(bank_mod);
@@ -189,19 +192,13 @@ void interleave(const std::vector<const std::vector<Entry>*>& lane_entries, int3
         if (chosen[b] >= 0) pad = chosen[b];
       if (pad < 0) pad = 0;
       for (int j = p0; j < p0 + phase_lanes; ++j) {
-        const int64_t idx = off + (int64_t)k * 32 + j;
         if (j < nl && lane_col[j] >= 0) {
           const int t = lane_col[j];
           const int32_t q = rem[j][t].second;
           rem[j].erase(rem[j].begin() + t);
-          const Entry& e = (*lane_entries[j])[q];
-          ts.col[idx] = e.col;
-          ts.ebasis[idx] = e.basis;
-          ts.ew2[idx] = e.w2;
+          emit(j, k, &(*lane_entries[j])[q], 0);
         } else {
-          ts.col[idx] = pad < n_slots ? pad : 0;
-          ts.ebasis[idx] = -1;
-          ts.ew2[idx] = 0;
+          emit(j, k, nullptr, pad < n_slots ? pad : 0);
         }
       }
     }
@@ -296,7 +293,15 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
         lanes.push_back(&lane_store[j]);
         ts.n_entries += protos[ti].len;
       }
-      interleave(lanes, ts.slice_steps[s], kPhaseLanes, kBankGroups, n_stored, ts.slice_off[s], ts);
+      const int64_t base = ts.slice_off[s];
+      interleave(
+          lanes, ts.slice_steps[s], kPhaseLanes, kBankGroups, n_stored, [](const Entry& e) { return e.col; },
+          [&](int j, int32_t k, const Entry* e, int32_t pad) {
+            const int64_t idx = base + (int64_t)k * 32 + j;
+            ts.col[idx] = e ? e->col : pad;
+            ts.ebasis[idx] = e ? e->basis : -1;
+            ts.ew2[idx] = e ? e->w2 : 0;
+          });
     }
   }
 
@@ -322,21 +327,29 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
     ts.cold_cb.assign(off, 0);
     ts.cold_ebasis.assign(off, -1);
     ts.cold_ew2.assign(off, 0);
-    for (int32_t s = 0; s < n_slices; ++s)
+    // entries scheduled on their first factor (the second factor's banks are left to chance)
+    std::vector<std::vector<Entry>> lane_store(32);
+    for (int32_t s = 0; s < n_slices; ++s) {
+      std::vector<const std::vector<Entry>*> lanes;
       for (size_t j = 0; j < slices[s].size(); ++j) {
         const int32_t ti = slices[s][j];
         ts.cold_tasks[(size_t)s * 32 + j] = tasks[ti];
         const auto& r = cold[tasks[ti].row];
-        for (int32_t q = 0; q < protos[ti].len; ++q) {
-          const Entry& e = r[protos[ti].begin + q];
-          const int64_t idx = (int64_t)ts.cold_slice_off[s] + (int64_t)q * 32 + (int64_t)j;
-          ts.cold_ca[idx] = slot_l[e.col];
-          ts.cold_cb[idx] = slot_r[e.col];
-          ts.cold_ebasis[idx] = e.basis;
-          ts.cold_ew2[idx] = e.w2;
-          ++ts.n_entries;
-        }
+        lane_store[j].assign(r.begin() + protos[ti].begin, r.begin() + protos[ti].begin + protos[ti].len);
+        lanes.push_back(&lane_store[j]);
+        ts.n_entries += protos[ti].len;
       }
+      const int64_t base = ts.cold_slice_off[s];
+      interleave(
+          lanes, steps[s], kPhaseLanes, kBankGroups, n_g, [&](const Entry& e) { return slot_l[e.col]; },
+          [&](int j, int32_t k, const Entry* e, int32_t pad) {
+            const int64_t idx = base + (int64_t)k * 32 + j;
+            ts.cold_ca[idx] = e ? slot_l[e->col] : pad;
+            ts.cold_cb[idx] = e ? slot_r[e->col] : pad;
+            ts.cold_ebasis[idx] = e ? e->basis : -1;
+            ts.cold_ew2[idx] = e ? e->w2 : 0;
+          });
+    }
   }
 
   // ---- row-major copy of all entries (kernels that keep every slot), longest tasks first
@@ -480,6 +493,59 @@ ace_status build_plan(const Spec& spec, const Graph& g, int task_len, StoredLimi
   for (int32_t s = K; s < plan.n_g; ++s) inner_slots.push_back(s);
   fill_levels(all_ops, plan.fwd, false);
   fill_levels(stored_ops, plan.fwd_stored, false);
+  // Within each stored level, order the nodes so that every 8 consecutive ones (a
+  // quarter-warp of the 16-byte loads and stores of 4-environment tiles) read and
+  // write distinct bank groups (slot mod 8), or read the same slot (a broadcast).
+  {
+    LevelList& F = plan.fwd_stored;
+    constexpr int kGroup = 8, kLook = 256;
+    for (size_t lv = 0; lv + 1 < F.off.size(); ++lv) {
+      const int32_t b = F.off[lv], e = F.off[lv + 1];
+      std::vector<int32_t> pool;
+      for (int32_t i = b; i < e; ++i) pool.push_back(i);
+      std::vector<int32_t> out;
+      out.reserve(pool.size());
+      std::vector<uint8_t> used(pool.size(), 0);
+      size_t head = 0;
+      while (out.size() < pool.size()) {
+        int32_t gl[kGroup], gr[kGroup], gs[kGroup];
+        int n = 0;
+        for (size_t t = head; t < pool.size() && n < kGroup && t < head + kLook; ++t) {
+          if (used[t]) continue;
+          const int32_t i = pool[t];
+          bool ok = true;
+          for (int q = 0; q < n && ok; ++q) {
+            ok &= (F.l[i] % kGroup != gl[q] % kGroup) || F.l[i] == gl[q];
+            ok &= (F.r[i] % kGroup != gr[q] % kGroup) || F.r[i] == gr[q];
+            ok &= F.slot[i] % kGroup != gs[q] % kGroup;
+          }
+          if (!ok) continue;
+          used[t] = 1;
+          gl[n] = F.l[i];
+          gr[n] = F.r[i];
+          gs[n] = F.slot[i];
+          ++n;
+          out.push_back(i);
+        }
+        for (size_t t = head; t < pool.size() && n < kGroup; ++t)  // no fit in the window: next nodes
+          if (!used[t]) {
+            used[t] = 1;
+            ++n;
+            out.push_back(pool[t]);
+          }
+        while (head < pool.size() && used[head]) ++head;
+      }
+      std::vector<int32_t> ns(out.size()), nl(out.size()), nr(out.size());
+      for (size_t q = 0; q < out.size(); ++q) {
+        ns[q] = F.slot[out[q]];
+        nl[q] = F.l[out[q]];
+        nr[q] = F.r[out[q]];
+      }
+      std::copy(ns.begin(), ns.end(), F.slot.begin() + b);
+      std::copy(nl.begin(), nl.end(), F.l.begin() + b);
+      std::copy(nr.begin(), nr.end(), F.r.begin() + b);
+    }
+  }
   fill_levels(inner_slots, plan.rev, true);
   if ((int)plan.fwd.off.size() - 1 > nu_max || (int)plan.rev.off.size() - 1 > nu_max)
     return fail(ACE_ERR_INVALID_ARG, "internal: too many levels");
