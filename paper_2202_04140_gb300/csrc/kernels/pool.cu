@@ -45,27 +45,36 @@ __constant__ float c_dfac[kPoolLmax + 2];               // (2m-1)!!
 
 __device__ __forceinline__ int qidx(int l, int m) { return l * (l + 1) / 2 + m; }
 
-// Neighbour geometry.  r, 2r/rc - 1 and 1 - r/rc are formed in FP64 from the
-// exact FP32 coordinates, so that 1 - r/rc keeps full FP32 relative accuracy
-// next to the cutoff (in FP32 it loses digits to cancellation there).
+// Neighbour geometry from the exact FP32 coordinates, with a handful of FP64
+// operations where FP32 loses accuracy (FP64 runs at a small fraction of the FP32
+// rate on this GPU, so nothing else uses it):
+//  * r^2 and rc^2 - r^2 in FP64 (the squares of FP32 values are exact in FP64), so
+//    1 - r/rc = (rc^2 - r^2) / ((rc + r) rc) keeps its digits next to the cutoff;
+//  * 1/r from the FP32 reciprocal square root refined by one Newton-Raphson step
+//    y <- y (3 - r^2 y^2) / 2 in FP64, and the unit vector from it in FP64, each
+//    component rounded once to FP32 (high-l harmonics amplify direction errors);
+//  * 2r/rc - 1 in FP64 (2/rc computed once per thread), rounded once.
 struct Geo {
   bool ok;
   float ir, xh, yh, u, t, w;
 };
 
-__device__ __forceinline__ void geometry(float x, float y, float z, float rc, Geo& g) {
-  const double xd = x, yd = y, zd = z;
+__device__ __forceinline__ void geometry(float x, float y, float z, float rc, double two_over_rc, Geo& g) {
+  const double xd = x, yd = y, zd = z, rcd = rc;
   const double r2 = xd * xd + yd * yd + zd * zd;
-  const double r = sqrt(r2);
-  const double rcd = rc;
-  g.ok = r > 0.0 && r < rcd;
-  const double ir = g.ok ? 1.0 / r : 0.0;
+  const double d2 = rcd * rcd - r2;  // rc^2 - r^2, no cancellation
+  const float r2f = (float)r2;
+  g.ok = r2f >= 1e-30f && d2 > 0.0;  // a neighbour at the centre or beyond rc adds nothing
+  const double y0 = (double)rsqrtf(g.ok ? r2f : 1.f);
+  const double ir = g.ok ? y0 * (1.5 - 0.5 * r2 * y0 * y0) : 0.0;
   g.ir = (float)ir;
   g.xh = (float)(xd * ir);
   g.yh = (float)(yd * ir);
   g.u = (float)(zd * ir);
-  g.t = (float)(2.0 * r / rcd - 1.0);
-  g.w = (float)(1.0 - r / rcd);
+  const double rd = r2 * ir;
+  const float r = (float)rd;
+  g.w = g.ok ? (float)d2 / ((rc + r) * rc) : 0.f;  // 1 - r/rc
+  g.t = (float)(rd * two_over_rc - 1.0);            // 2r/rc - 1, rounded once (T_n(t) has slope n^2)
 }
 
 // Q[qidx(l,m)] = Q_l^m(u) for 0 <= m <= l <= lmax.
@@ -102,6 +111,7 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
   __shared__ float sR[kPoolWarps][kPoolChunk][kPoolMaxR];
   __shared__ float sY[kPoolWarps][kPoolChunk][NL];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double two_over_rc = 2.0 / (double)rc;
   const int nR0 = nmax - nmin + 1;
   const int nR = nR0 * kf;  // radial x feature factors
   const int K = nR * NL;
@@ -118,7 +128,7 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
       if (lane < cnt) {
         const float x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
         Geo g;
-        geometry(x, y, z, rc, g);
+        geometry(x, y, z, rc, two_over_rc, g);
         const bool ok = g.ok;
         const float xh = g.xh, yh = g.yh, u = g.u, t = g.t;
         const float env2 = ok ? g.w * g.w : 0.f;
@@ -200,6 +210,7 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
   constexpr int NL = (LMAX + 1) * (LMAX + 1);
   __shared__ float sG[kPoolWarps][kPoolMaxR * NL];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double two_over_rc = 2.0 / (double)rc;
   const int nR = nmax - nmin + 1;
   const int K = nR * kf * NL;
   for (int64_t env = blockIdx.x * (int64_t)kPoolWarps + warp; env < n_env; env += (int64_t)gridDim.x * kPoolWarps) {
@@ -210,7 +221,7 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
     for (int64_t j = j0 + lane; j < j1; j += 32) {
       const float x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
       Geo geo;
-      geometry(x, y, z, rc, geo);
+      geometry(x, y, z, rc, two_over_rc, geo);
       if (!geo.ok) {
         dpos[3 * j] = 0.f;
         dpos[3 * j + 1] = 0.f;
