@@ -104,17 +104,26 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
     Acc<float, RO> phiacc;
     const float half = GRAD ? 0.5f : 1.f;
     const float pbl = GRAD ? pb[lane] : 0.f;
-    // The header of the warp's next task is loaded while the current task runs.
+    // Most tasks hold at most 2 kPairBatch entries: the header and the first
+    // kPairBatch entry pairs of the warp's next task are loaded while the current
+    // task runs (the pairs once its header has arrived, before the epilogue).
     int t = warp;
     int4 task = make_int4(-1, 0, 0, 0);
     int q0 = 0, q1 = 0;
     float lin = 0.f;
+    int4 cur[kPairBatch];
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u) cur[u] = make_int4(0, 0, 0, 0);
     if (t < a.n_tasks) {
       task = __ldg(a.tasks + t);
       const int4 h = __ldg(a.thdr + t);
       q0 = h.x;
       q1 = h.y;
       lin = __int_as_float(h.z);
+      const int np0 = (q1 - q0) >> 1;
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u)
+        if (u < np0) cur[u] = __ldg(a.ent + (q0 >> 1) + u);
     }
     while (t < a.n_tasks) {
       const int tn = t + NW;
@@ -128,21 +137,13 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
         q1n = h.y;
         lin_n = __int_as_float(h.z);
       }
-      // entry pairs in batches of kPairBatch, the next batch loading while this one is used
       const int4* ep = a.ent + (q0 >> 1);
       const int np = (q1 - q0) >> 1;
       float acc0 = 0.f, acc1 = 0.f;
-      int4 cur[kPairBatch];
+      // the first batch, already loaded
 #pragma unroll
-      for (int u = 0; u < kPairBatch; ++u) cur[u] = u < np ? __ldg(ep + u) : make_int4(0, 0, 0, 0);
-      for (int b = 0; b < np; b += kPairBatch) {
-        int4 nxt[kPairBatch];
-#pragma unroll
-        for (int u = 0; u < kPairBatch; ++u)
-          nxt[u] = b + kPairBatch + u < np ? __ldg(ep + b + kPairBatch + u) : make_int4(0, 0, 0, 0);
-#pragma unroll
-        for (int u = 0; u < kPairBatch; ++u) {
-          if (b + u >= np) break;
+      for (int u = 0; u < kPairBatch; ++u) {
+        if (u < np) {
           int j0 = cur[u].x, j1 = cur[u].z;
           if (a.check && ((unsigned)j0 >= (unsigned)a.n_slots || (unsigned)j1 >= (unsigned)a.n_slots)) {
             if (lane == 0) atomicOr(a.status, kStatusBounds);
@@ -151,8 +152,31 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
           acc0 = __fmaf_rn(__int_as_float(cur[u].y), AA[j0 * S + lane], acc0);
           acc1 = __fmaf_rn(__int_as_float(cur[u].w), AA[j1 * S + lane], acc1);
         }
+      }
+      // longer tasks: further batches, loaded together
+      for (int b = kPairBatch; b < np; b += kPairBatch) {
+        int4 bt[kPairBatch];
 #pragma unroll
-        for (int u = 0; u < kPairBatch; ++u) cur[u] = nxt[u];
+        for (int u = 0; u < kPairBatch; ++u) bt[u] = b + u < np ? __ldg(ep + b + u) : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < kPairBatch; ++u) {
+          if (b + u < np) {
+            int j0 = bt[u].x, j1 = bt[u].z;
+            if (a.check && ((unsigned)j0 >= (unsigned)a.n_slots || (unsigned)j1 >= (unsigned)a.n_slots)) {
+              if (lane == 0) atomicOr(a.status, kStatusBounds);
+              j0 = j1 = 0;
+            }
+            acc0 = __fmaf_rn(__int_as_float(bt[u].y), AA[j0 * S + lane], acc0);
+            acc1 = __fmaf_rn(__int_as_float(bt[u].w), AA[j1 * S + lane], acc1);
+          }
+        }
+      }
+      // the next task's first batch
+      {
+        const int npn = (q1n - q0n) >> 1;
+#pragma unroll
+        for (int u = 0; u < kPairBatch; ++u)
+          cur[u] = u < npn ? __ldg(a.ent + (q0n >> 1) + u) : make_int4(0, 0, 0, 0);
       }
       const float acc = acc0 + acc1;
       const int row = task.x;
