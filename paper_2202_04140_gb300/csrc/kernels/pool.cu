@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "launch.hpp"
+#include "pool_geometry.cuh"
 
 namespace ace {
 namespace dev {
@@ -44,38 +45,6 @@ __constant__ float c_rb[kPoolLmax + 1][kPoolLmax + 1];  // (l+m-1)/(l-m)
 __constant__ float c_dfac[kPoolLmax + 2];               // (2m-1)!!
 
 __device__ __forceinline__ int qidx(int l, int m) { return l * (l + 1) / 2 + m; }
-
-// Neighbour geometry from the exact FP32 coordinates, with a handful of FP64
-// operations where FP32 loses accuracy (FP64 runs at a small fraction of the FP32
-// rate on this GPU, so nothing else uses it):
-//  * r^2 and rc^2 - r^2 in FP64 (the squares of FP32 values are exact in FP64), so
-//    1 - r/rc = (rc^2 - r^2) / ((rc + r) rc) keeps its digits next to the cutoff;
-//  * 1/r from the FP32 reciprocal square root refined by one Newton-Raphson step
-//    y <- y (3 - r^2 y^2) / 2 in FP64, and the unit vector from it in FP64, each
-//    component rounded once to FP32 (high-l harmonics amplify direction errors);
-//  * 2r/rc - 1 in FP64 (2/rc computed once per thread), rounded once.
-struct Geo {
-  bool ok;
-  float ir, xh, yh, u, t, w;
-};
-
-__device__ __forceinline__ void geometry(float x, float y, float z, float rc, double two_over_rc, Geo& g) {
-  const double xd = x, yd = y, zd = z, rcd = rc;
-  const double r2 = xd * xd + yd * yd + zd * zd;
-  const double d2 = rcd * rcd - r2;  // rc^2 - r^2, no cancellation
-  const float r2f = (float)r2;
-  g.ok = r2f >= 1e-30f && d2 > 0.0;  // a neighbour at the centre or beyond rc adds nothing
-  const double y0 = (double)rsqrtf(g.ok ? r2f : 1.f);
-  const double ir = g.ok ? y0 * (1.5 - 0.5 * r2 * y0 * y0) : 0.0;
-  g.ir = (float)ir;
-  g.xh = (float)(xd * ir);
-  g.yh = (float)(yd * ir);
-  g.u = (float)(zd * ir);
-  const double rd = r2 * ir;
-  const float r = (float)rd;
-  g.w = g.ok ? (float)d2 / ((rc + r) * rc) : 0.f;  // 1 - r/rc
-  g.t = (float)(rd * two_over_rc - 1.0);            // 2r/rc - 1, rounded once (T_n(t) has slope n^2)
-}
 
 // Q[qidx(l,m)] = Q_l^m(u) for 0 <= m <= l <= lmax.
 template <int LMAX>
@@ -100,6 +69,11 @@ __device__ __forceinline__ void feature_poly(float mu, int kf, float (&Tf)[kPool
   (void)kf;
 }
 
+// Slot of radial factor n of staged neighbour jj in sR: the four 16-byte groups of a
+// row are permuted by (jj / 2) mod 4, so that the 32 lanes writing factor n of their own
+// neighbours hit 8 banks (4-way) instead of 2, while a row stays readable as float4s.
+__device__ __forceinline__ int rslot(int jj, int n) { return ((((n >> 2) ^ (jj >> 1)) & 3) << 2) | (n & 3); }
+
 template <int LMAX>
 __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __restrict__ pos,
                                                                const float* __restrict__ mu,
@@ -108,10 +82,10 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
                                                                float* __restrict__ A) {
   constexpr int NL = (LMAX + 1) * (LMAX + 1);
   constexpr int NI = (NL + 31) / 32;
-  __shared__ float sR[kPoolWarps][kPoolChunk][kPoolMaxR];
+  __shared__ __align__(16) float sR[kPoolWarps][kPoolChunk][kPoolMaxR];
   __shared__ float sY[kPoolWarps][kPoolChunk][NL];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double two_over_rc = 2.0 / (double)rc;
+  const geo::Cut cut = geo::make_cut(rc);
   const int nR0 = nmax - nmin + 1;
   const int nR = nR0 * kf;  // radial x feature factors
   const int K = nR * NL;
@@ -127,27 +101,26 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
       const int cnt = (int)((j1 - jb) < kPoolChunk ? (j1 - jb) : kPoolChunk);
       if (lane < cnt) {
         const float x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
-        Geo g;
-        geometry(x, y, z, rc, two_over_rc, g);
+        const geo::Geo g = geo::geometry(x, y, z, cut);
         const bool ok = g.ok;
         const float xh = g.xh, yh = g.yh, u = g.u, t = g.t;
         const float env2 = ok ? g.w * g.w : 0.f;
         float Tm1 = 1.f, T = t;
         for (int n = 1; n <= nmax; ++n) {
-          if (n >= nmin) sR[warp][lane][n - nmin] = T * env2;
+          if (n >= nmin) sR[warp][lane][rslot(lane, n - nmin)] = T * env2;
           const float Tn = 2.f * t * T - Tm1;
           Tm1 = T;
           T = Tn;
         }
-        if (nmin == 0) sR[warp][lane][0] = env2;
+        if (nmin == 0) sR[warp][lane][rslot(lane, 0)] = env2;
         if (kf > 1) {  // expand R_n into R_n T_k(mu_j), in place from the last factor down
           float Tf[kPoolMaxF];
           feature_poly(mu[j], kf, Tf);
           for (int i = nR0 - 1; i >= 0; --i) {
-            const float rn = sR[warp][lane][i];
+            const float rn = sR[warp][lane][rslot(lane, i)];
 #pragma unroll
             for (int k = kPoolMaxF - 1; k >= 0; --k)
-              if (k < kf) sR[warp][lane][i * kf + k] = rn * Tf[k];
+              if (k < kf) sR[warp][lane][rslot(lane, i * kf + k)] = rn * Tf[k];
           }
         }
         float Q[kPoolQ];
@@ -175,12 +148,16 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
         float y[NI];
 #pragma unroll
         for (int i = 0; i < NI; ++i) y[i] = (lane + 32 * i < NL) ? sY[warp][jj][lane + 32 * i] : 0.f;
+        // factors n >= nR of the last group are stale; their sums are never stored
 #pragma unroll
-        for (int n = 0; n < kPoolMaxR; ++n) {
-          if (n < nR) {
-            const float rn = sR[warp][jj][n];
+        for (int q = 0; q < kPoolMaxR / 4; ++q) {
+          if (4 * q < nR) {
+            const float4 rv = *reinterpret_cast<const float4*>(&sR[warp][jj][rslot(jj, 4 * q)]);
+            const float r4[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
-            for (int i = 0; i < NI; ++i) acc[i][n] = __fmaf_rn(rn, y[i], acc[i][n]);
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int i = 0; i < NI; ++i) acc[i][4 * q + c] = __fmaf_rn(r4[c], y[i], acc[i][4 * q + c]);
           }
         }
       }
@@ -199,7 +176,14 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
   }
 }
 
-// Adjoint: one warp per environment, one lane per neighbour.
+// Adjoint: one warp per environment, one lane per neighbour.  With
+// G_q,lm = dphi/dA_q,lm (q the radial x feature factor) the force on neighbour j is
+// built from
+//   h_lm = sum_q G_q,lm R_q(r_j),   hd_lm = sum_q G_q,lm dR_q/dr(r_j)
+// (49 + 49 values per lane for lmax = 6, held in registers; the radial index runs
+// outside, each row of G read with 16-byte broadcast loads), then
+//   dphi/dr_j = rh sum_lm hd_lm Y_lm + (grad_u - rh (rh . grad_u)) / r,
+//   grad_u = sum_lm h_lm dY_lm/d(unit vector).
 template <int LMAX>
 __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float* __restrict__ pos,
                                                                     const float* __restrict__ mu,
@@ -208,53 +192,80 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
                                                                     int kf, const float* __restrict__ dA,
                                                                     float alpha, float* __restrict__ dpos) {
   constexpr int NL = (LMAX + 1) * (LMAX + 1);
-  __shared__ float sG[kPoolWarps][kPoolMaxR * NL];
+  constexpr int NL4 = (NL + 3) / 4;  // 16-byte groups per row of G
+  constexpr int NLP = 4 * NL4;       // row stride in shared memory
+  __shared__ __align__(16) float sG[kPoolWarps][kPoolMaxR * NLP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double two_over_rc = 2.0 / (double)rc;
+  const geo::Cut cut = geo::make_cut(rc);
+  const float two_over_rc = 2.f / rc;
   const int nR = nmax - nmin + 1;
   const int K = nR * kf * NL;
   for (int64_t env = blockIdx.x * (int64_t)kPoolWarps + warp; env < n_env; env += (int64_t)gridDim.x * kPoolWarps) {
     __syncwarp();
-    for (int i = lane; i < K; i += 32) sG[warp][i] = dA[env * K + i];
+    for (int i = lane; i < K; i += 32) {
+      const int row = i / NL;
+      sG[warp][row * NLP + (i - row * NL)] = dA[env * K + i];
+    }
     __syncwarp();
     const int64_t j0 = offsets[env], j1 = offsets[env + 1];
     for (int64_t j = j0 + lane; j < j1; j += 32) {
       const float x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
-      Geo geo;
-      geometry(x, y, z, rc, two_over_rc, geo);
-      if (!geo.ok) {
+      const geo::Geo gm = geo::geometry(x, y, z, cut);
+      if (!gm.ok) {
         dpos[3 * j] = 0.f;
         dpos[3 * j + 1] = 0.f;
         dpos[3 * j + 2] = 0.f;
         continue;
       }
-      const float ir = geo.ir;
-      const float xh = geo.xh, yh = geo.yh, u = geo.u, t = geo.t;
-      const float w = geo.w;
+      const float ir = gm.ir;
+      const float xh = gm.xh, yh = gm.yh, u = gm.u, t = gm.t;
+      const float w = gm.w;
       const float env2 = w * w, denv = -2.f * w / rc;
-      float R[kPoolMaxR], dR[kPoolMaxR];
-      {
-        float Tm1 = 1.f, T = t, dTm1 = 0.f, dT = 1.f;
-        if (nmin == 0) {
-          R[0] = env2;
-          dR[0] = denv;
-        }
-#pragma unroll
-        for (int n = 1; n <= kPoolMaxR; ++n) {
-          if (n >= nmin && n <= nmax) {
-            R[n - nmin] = T * env2;
-            dR[n - nmin] = dT * (2.f / rc) * env2 + T * denv;
-          }
-          const float Tn = 2.f * t * T - Tm1;
-          const float dTn = 2.f * T + 2.f * t * dT - dTm1;
-          Tm1 = T;
-          T = Tn;
-          dTm1 = dT;
-          dT = dTn;
-        }
-      }
       float Tf[kPoolMaxF];
       feature_poly(kf > 1 ? mu[j] : 0.f, kf, Tf);
+      float h[NL], hd[NL];
+#pragma unroll
+      for (int i = 0; i < NL; ++i) {
+        h[i] = 0.f;
+        hd[i] = 0.f;
+      }
+      // T_n(t) and T_n'(t) from n = 0 upwards; R_n = T_n env2, dR_n/dr = (2/rc) T_n' env2 + T_n denv.
+      float T = 1.f, dT = 0.f, Tm1 = 0.f, dTm1 = 0.f;
+      for (int n = 0; n <= nmax; ++n) {
+        if (n >= nmin) {
+          const float rn = T * env2, drn = dT * two_over_rc * env2 + T * denv;
+          const float4* row = reinterpret_cast<const float4*>(&sG[warp][(n - nmin) * kf * NLP]);
+#pragma unroll
+          for (int q = 0; q < NL4; ++q) {
+            float4 v = row[q];
+            if (kf > 1) {  // sum the feature degrees with weights T_k(mu_j)
+#pragma unroll
+              for (int k = 1; k < kPoolMaxF; ++k)
+                if (k < kf) {
+                  const float4 vk = row[k * NL4 + q];
+                  v.x = __fmaf_rn(vk.x, Tf[k], v.x);
+                  v.y = __fmaf_rn(vk.y, Tf[k], v.y);
+                  v.z = __fmaf_rn(vk.z, Tf[k], v.z);
+                  v.w = __fmaf_rn(vk.w, Tf[k], v.w);
+                }
+            }
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (4 * q + c < NL) {
+                h[4 * q + c] = __fmaf_rn(vv[c], rn, h[4 * q + c]);
+                hd[4 * q + c] = __fmaf_rn(vv[c], drn, hd[4 * q + c]);
+              }
+          }
+        }
+        // advance: T_{n+1} = 2t T_n - T_{n-1} (T_1 = t), T'_{n+1} = 2 T_n + 2t T'_n - T'_{n-1}
+        const float Tn = n == 0 ? t : 2.f * t * T - Tm1;
+        const float dTn = n == 0 ? 1.f : 2.f * T + 2.f * t * dT - dTm1;
+        Tm1 = T;
+        T = Tn;
+        dTm1 = dT;
+        dT = dTn;
+      }
       float Q[kPoolQ];
       legendre_q<LMAX>(u, Q);
       float gx = 0.f, gy = 0.f, gz = 0.f, ys = 0.f;
@@ -266,36 +277,17 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
           const float kq = c_norm[l][m] * Q[qidx(l, m)];
           const float kq1 = (m + 1 <= l) ? c_norm[l][m] * Q[qidx(l, m + 1)] : 0.f;
           const int base = l * l + l;
-          float h = 0.f, hd = 0.f, h2 = 0.f, hd2 = 0.f;
-          for (int n = 0; n < nR; ++n) {
-            // dA of (n, l, m) summed over the feature degrees with weights T_k(mu_j)
-            float ga = sG[warp][n * kf * NL + base + m];
-            float gb = m > 0 ? sG[warp][n * kf * NL + base - m] : 0.f;
-            if (kf > 1) {
-#pragma unroll
-              for (int k = 1; k < kPoolMaxF; ++k)
-                if (k < kf) {
-                  ga = __fmaf_rn(sG[warp][(n * kf + k) * NL + base + m], Tf[k], ga);
-                  if (m > 0) gb = __fmaf_rn(sG[warp][(n * kf + k) * NL + base - m], Tf[k], gb);
-                }
-            }
-            h = __fmaf_rn(ga, R[n], h);
-            hd = __fmaf_rn(ga, dR[n], hd);
-            if (m > 0) {
-              h2 = __fmaf_rn(gb, R[n], h2);
-              hd2 = __fmaf_rn(gb, dR[n], hd2);
-            }
-          }
           if (m == 0) {
-            ys = __fmaf_rn(hd, kq, ys);
-            gz = __fmaf_rn(h, kq1, gz);
+            ys = __fmaf_rn(hd[base], kq, ys);
+            gz = __fmaf_rn(h[base], kq1, gz);
           } else {
             const float fm = (float)m;
+            const float h1 = h[base + m], hd1 = hd[base + m], h2 = h[base - m], hd2 = hd[base - m];
             // cos part
-            ys = __fmaf_rn(hd, kq * C, ys);
-            gx = __fmaf_rn(h, kq * fm * Cp, gx);
-            gy = __fmaf_rn(h, -kq * fm * Sp, gy);
-            gz = __fmaf_rn(h, kq1 * C, gz);
+            ys = __fmaf_rn(hd1, kq * C, ys);
+            gx = __fmaf_rn(h1, kq * fm * Cp, gx);
+            gy = __fmaf_rn(h1, -kq * fm * Sp, gy);
+            gz = __fmaf_rn(h1, kq1 * C, gz);
             // sin part
             ys = __fmaf_rn(hd2, kq * S, ys);
             gx = __fmaf_rn(h2, kq * fm * Sp, gx);
