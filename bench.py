@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="stress_k810", choices=sorted(W.WORKLOADS))
     ap.add_argument("--readout", default="compensated", choices=["plain", "compensated", "fp64"])
+    ap.add_argument("--algo", type=int, default=1, choices=[1, 2],
+                    help="graph insertion heuristic: Algorithm 1 or Algorithm 2 (section 3.3)")
+    ap.add_argument("--n-split", type=int, default=2, help="parameter n of Algorithm 2")
     ap.add_argument("--no-baselines", action="store_true", help="skip the plain-FP64 GPU and CPU oracle legs")
     ap.add_argument("--n-env", type=int, default=None, help="override the environment count (small profiling cases)")
     ap.add_argument("--no-graph", action="store_true", help="launch every step directly instead of replaying "
@@ -341,7 +344,7 @@ def main():
 
     w = W.workload(args.workload, **({"n_env": args.n_env} if args.n_env else {}))
     spec = Spec.from_workload(w)
-    dag = Dag(spec)
+    dag = Dag(spec, algo=args.algo, n_split=args.n_split)
     # kernel form and environments per CTA chosen by the autotuner for exactly this request
     tuned = dag.autotune(w.n_env, w.n_out, torch.float32, w.grad, args.readout)
     n_ge2 = dag.n_nodes - dag.K
@@ -513,6 +516,7 @@ def main():
                        "K": dag.K, "nu_max": w.nu_max, "deg_max": w.deg_max, "n_basis": dag.n_basis,
                        "n_nodes": dag.n_nodes, "n_aux": dag.n_aux, "n_operands": dag.n_operands,
                        "n_sinks": dag.n_sinks, "mode": mode, "readout": args.readout,
+                       "graph": {"algorithm": args.algo, **({"n": args.n_split} if args.algo == 2 else {})},
                        "kernel_config": {"kernel": tuned["kernel"], "E": tuned["E"], "by": "autotuner"},
                        "launch": "direct" if args.no_graph else "CUDA graph replay (one graph per buffer set)",
                        "l2": f"inputs larger than L2: {n_sets} rotating buffer sets of {per_set / 1e6:.0f} MB"},
