@@ -66,6 +66,9 @@ struct Task {
   int32_t pl, pr; // factor slots of a top operand row, else -1
 };
 
+// Warps per CTA of the one-environment-per-lane kernel (1024 threads).
+constexpr int kLoeWarps = 32;
+
 struct TaskSet {
   // Tasks grouped in slices of 32 (one per lane); entries of a slice are
   // interleaved: entry k of lane j sits at slice_off[s] + 32 k + j.
@@ -93,6 +96,12 @@ struct TaskSet {
   std::vector<int32_t> rm_off;        // [n_rm + 1]
   std::vector<int32_t> rm_col, rm_ebasis;
   std::vector<uint8_t> rm_ew2;
+  // Their layout as one stream per warp of that kernel (kLoeWarps warps per CTA;
+  // warp w takes tasks w, w + kLoeWarps, ...): each task is a 16-byte header
+  // followed by its entry pairs (16 bytes each), contiguous.  Positions count
+  // 16-byte items.
+  std::vector<int32_t> loe_wbeg;      // [kLoeWarps + 1] first item of each warp's stream
+  std::vector<int32_t> loe_hpos;      // [n_rm] item of each task's header (its pairs follow)
   int32_t n_slices() const { return (int32_t)slice_steps.size(); }
 };
 

@@ -77,8 +77,10 @@ struct DevTaskSet {
   uint8_t* rm_ew2 = nullptr;
   int32_t n_rm = 0;
   int64_t n_rm_ent = 0;
-  int2* rm_ent = nullptr;     // bound {column, coefficient} entries (FP32, one channel)
-  int4* rm_thdr = nullptr;    // bound per-task header {first, end, row coefficient, 0}
+  int32_t* loe_hpos = nullptr;  // item of each task's header in the per-warp streams
+  int32_t loe_wbeg[kLoeWarps + 1] = {};
+  int64_t n_loe_items = 0;
+  int4* loe_stream = nullptr;   // bound streams: headers and {column, coefficient} pairs (FP32, one channel)
   bool rm_bound = false;
   // coefficients bound into this task set
   void* vals = nullptr;
@@ -255,6 +257,9 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   if ((s = upload_vec(d, ts.rm_ew2, &dt.rm_ew2, st)) != ACE_OK) return s;
   dt.n_rm = (int32_t)ts.rm_tasks.size();
   dt.n_rm_ent = (int64_t)ts.rm_col.size();
+  if ((s = upload_vec(d, ts.loe_hpos, &dt.loe_hpos, st)) != ACE_OK) return s;
+  for (int w = 0; w <= kLoeWarps; ++w) dt.loe_wbeg[w] = ts.loe_wbeg[w];
+  dt.n_loe_items = ts.loe_wbeg[kLoeWarps];
   return ACE_OK;
 }
 
@@ -320,6 +325,18 @@ ace_status validate_plan(const Plan& p) {
         return fail(ACE_ERR_BOUNDS, "plan: row-major task factor out of range");
       if (ts == &p.sym && !(t.flags & 2) && !in(t.row, p.n_g))
         return fail(ACE_ERR_BOUNDS, "plan: row-major adjoint row out of range");
+    }
+    // per-warp streams: every task's header and pairs inside its warp's stream, no overlap
+    if (ts->loe_wbeg.size() != (size_t)kLoeWarps + 1 || ts->loe_hpos.size() != ts->rm_tasks.size() ||
+        ts->loe_wbeg[0] != 0)
+      return fail(ACE_ERR_BOUNDS, "plan: per-warp stream sizes");
+    for (int w = 0; w < kLoeWarps; ++w) {
+      int32_t pos = ts->loe_wbeg[w];
+      for (size_t t = (size_t)w; t < ts->rm_tasks.size(); t += kLoeWarps) {
+        if (ts->loe_hpos[t] != pos) return fail(ACE_ERR_BOUNDS, "plan: per-warp stream header position");
+        pos += 1 + (ts->rm_off[t + 1] - ts->rm_off[t]) / 2;
+      }
+      if (pos != ts->loe_wbeg[w + 1]) return fail(ACE_ERR_BOUNDS, "plan: per-warp stream extent");
     }
   }
   return ACE_OK;
@@ -439,17 +456,15 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
   }
   dt.rm_bound = false;
   if (dtype == ACE_F32 && n_out == 1) {
-    if (!dt.rm_ent) {
+    if (!dt.loe_stream) {
       void* p = nullptr;
-      if ((e = cudaMalloc(&p, std::max<size_t>((size_t)dt.n_rm_ent * sizeof(int2), 16))) != cudaSuccess)
-        return cuda_fail(e, "cudaMalloc");
-      dt.rm_ent = static_cast<int2*>(p);
-      if ((e = cudaMalloc(&p, std::max<size_t>((size_t)dt.n_rm * sizeof(int4), 16))) != cudaSuccess)
-        return cuda_fail(e, "cudaMalloc");
-      dt.rm_thdr = static_cast<int4*>(p);
+      const size_t bytes = ((size_t)dt.n_loe_items + dev::kLoeStreamPad) * sizeof(int4);
+      if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      dt.loe_stream = static_cast<int4*>(p);
+      if ((e = cudaMemsetAsync(p, 0, bytes, st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     }
-    e = launch_bind_rm(static_cast<const float*>(c), dt.rm_col, dt.rm_ebasis, dt.rm_ew2, dt.n_rm_ent, dt.rm_ent,
-                       dt.rm_tasks, dt.rm_off, d->slot_basis, dt.n_rm, dt.rm_thdr, st);
+    e = launch_bind_loe(static_cast<const float*>(c), dt.rm_tasks, dt.rm_off, dt.rm_col, dt.rm_ebasis, dt.rm_ew2,
+                        d->slot_basis, dt.loe_hpos, dt.n_rm, dt.loe_stream, st);
     if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
     dt.rm_bound = true;
   }
@@ -573,10 +588,9 @@ ace_status run_loe(ace_dag* d, DevTaskSet& dt, const void* A, const void* phibar
     a.fwd_off[i] = i < (int)p.fwd.off.size() ? p.fwd.off[i] : 0;
     a.rev_off[i] = i < (int)p.rev.off.size() ? p.rev.off[i] : 0;
   }
-  a.tasks = dt.rm_tasks;
-  a.thdr = dt.rm_thdr;
-  a.n_tasks = dt.n_rm;
-  a.ent = reinterpret_cast<const int4*>(dt.rm_ent);
+  static_assert(kLoeWarps == dev::kLoeStreamWarps, "per-warp stream layout and kernel disagree");
+  a.stream = dt.loe_stream;
+  for (int w = 0; w <= kLoeWarps; ++w) a.wbeg[w] = dt.loe_wbeg[w];
   a.check = checked_mode() ? 1 : 0;
   a.status = d->status;
   void* args[] = {&a};
@@ -861,6 +875,8 @@ ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out
       v = &tmp;
     } else if (field == "rm_off") v = &ts.rm_off;
     else if (field == "rm_col") v = &ts.rm_col;
+    else if (field == "loe_wbeg") v = &ts.loe_wbeg;
+    else if (field == "loe_hpos") v = &ts.loe_hpos;
     else if (field == "rm_ebasis") v = &ts.rm_ebasis;
     else if (field == "rm_ew2") {
       tmp.assign(ts.rm_ew2.begin(), ts.rm_ew2.end());
@@ -916,8 +932,7 @@ void ace_dag_free(ace_dag* dag) {
       if (t->lin) cudaFree(t->lin);
       if (t->vals4) cudaFree(t->vals4);
       if (t->cold_vals) cudaFree(t->cold_vals);
-      if (t->rm_ent) cudaFree(t->rm_ent);
-      if (t->rm_thdr) cudaFree(t->rm_thdr);
+      if (t->loe_stream) cudaFree(t->loe_stream);
     }
     cudaSetDevice(cur);
   }

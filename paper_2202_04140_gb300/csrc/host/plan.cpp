@@ -377,6 +377,19 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
       }
       ts.rm_off.push_back((int32_t)ts.rm_col.size());
     }
+    // per-warp streams: warp w's tasks in rm order, each header then its pairs
+    const int32_t n_rm = (int32_t)ts.rm_tasks.size();
+    ts.loe_hpos.assign(n_rm, 0);
+    ts.loe_wbeg.assign(kLoeWarps + 1, 0);
+    int32_t pos = 0;
+    for (int w = 0; w < kLoeWarps; ++w) {
+      ts.loe_wbeg[w] = pos;
+      for (int32_t t = w; t < n_rm; t += kLoeWarps) {
+        ts.loe_hpos[t] = pos;
+        pos += 1 + (ts.rm_off[t + 1] - ts.rm_off[t]) / 2;
+      }
+    }
+    ts.loe_wbeg[kLoeWarps] = pos;
   }
 }
 

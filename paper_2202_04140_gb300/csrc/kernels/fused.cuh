@@ -30,6 +30,11 @@ namespace ace {
 namespace dev {
 
 constexpr int kMaxLevels = 8;
+// Warps per CTA of the one-environment-per-lane kernel (its task streams are laid
+// out per warp).
+constexpr int kLoeStreamWarps = 32;
+// Zero items allocated after the last stream (the kernel reads up to this many items ahead).
+constexpr int kLoeStreamPad = 8;
 
 enum : int { kReadPlain = 0, kReadComp = 1, kReadF64 = 2 };
 enum : uint32_t { kStatusBounds = 1u, kStatusTimeout = 2u };
@@ -93,10 +98,11 @@ struct LoeArgs {
   int32_t fwd_off[kMaxLevels + 1];
   int32_t rev_off[kMaxLevels + 1];
   int32_t n_fwd_levels, n_rev_levels;
-  const int4* tasks;  // {row, flags, factor slots}
-  const int4* thdr;   // {first entry, end entry, row coefficient bits (first task only), 0}
-  int32_t n_tasks;
-  const int4* ent;    // entry pairs {col0, coef0 bits, col1, coef1 bits}
+  // One stream per warp: each task is a header {target slot, (entry pairs << 8) |
+  // flags, second factor slot (top operands), row coefficient bits} followed by
+  // its entry pairs {col0, coef0 bits, col1, coef1 bits}.
+  const int4* stream;                 // followed by kLoeStreamPad zero items
+  int32_t wbeg[kLoeStreamWarps + 1];  // first item of each warp's stream
   float* ws;          // global-workspace variant: [gridDim.x][n_slots (+ n_g)][32] floats
   int32_t check;
   uint32_t* status;
@@ -280,26 +286,29 @@ struct Acc<float, kReadPlain> {
   __device__ __forceinline__ void shfl_down_add(int d) { s += __shfl_down_sync(0xffffffffu, s, d); }
 };
 
-// TwoSum (Knuth): s + e holds the running sum exactly up to one rounding per
-// combination of two compensated values.
+// Kahan's compensated summation: c holds the negated low-order part that the
+// running sum s lost, and is subtracted from the next term (four additions per
+// term).  The error of the sum of x_1..x_n is at most (2u + O(n u^2)) sum |x_i|,
+// u = 2^-24, whatever the order; each x here is a per-task partial, so the bound is
+// a small multiple of u times the condition-aware scale sum_k |c_k| |AA_k|.
 template <>
 struct Acc<float, kReadComp> {
-  float s = 0.f, e = 0.f;
+  float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float x) {
-    float t = s + x;
-    float z = t - s;
-    e += (s - (t - z)) + (x - z);
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
     s = t;
   }
   __device__ __forceinline__ void add_acc(const Acc& o) {
     add(o.s);
-    e += o.e;
+    add(-o.c);
   }
-  __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
   __device__ __forceinline__ void shfl_down_add(int d) {
     Acc o;
     o.s = __shfl_down_sync(0xffffffffu, s, d);
-    o.e = __shfl_down_sync(0xffffffffu, e, d);
+    o.c = __shfl_down_sync(0xffffffffu, c, d);
     add_acc(o);
   }
 };

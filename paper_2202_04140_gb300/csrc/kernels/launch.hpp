@@ -18,9 +18,12 @@ const void* loe_kernel_ptr(bool grad, int readout, bool global, int* nt);
 size_t loe_smem(int n_slots, int n_g, bool grad, int nt);
 size_t loe_global_smem(int nt);
 size_t loe_global_bytes_per_cta(int n_slots, int n_g, bool grad);
-cudaError_t launch_bind_rm(const float* c, const int32_t* col, const int32_t* ebasis, const uint8_t* ew2, int64_t n,
-                           int2* ent, const int4* tasks, const int32_t* toff, const int32_t* slot_basis,
-                           int32_t n_tasks, int4* thdr, cudaStream_t st);
+// Fill the per-warp task streams of the one-environment-per-lane kernel with the
+// coefficients c (FP32, one channel): task t's header at item hpos[t], its entry
+// pairs (entries toff[t] .. toff[t+1], an even count) in the items after it.
+cudaError_t launch_bind_loe(const float* c, const int4* tasks, const int32_t* toff, const int32_t* col,
+                            const int32_t* ebasis, const uint8_t* ew2, const int32_t* slot_basis,
+                            const int32_t* hpos, int32_t n_tasks, int4* stream, cudaStream_t st);
 
 cudaError_t launch_bind(int dtype, const void* c, int n_out, int nout_pad, const int32_t* ebasis, const uint8_t* ew2,
                         int64_t n_entries, void* vals, const int32_t* lin_basis, int64_t n_lin, void* lin,

@@ -42,6 +42,100 @@ __host__ __device__ inline size_t loe_global_floats(int n_slots, int n_g, bool g
   return ((size_t)n_slots + (grad ? (size_t)n_g : 0)) * 32;
 }
 
+// u += c_j0 AA_j0 and c_j1 AA_j1 for one entry pair {j0, c0, j1, c1}.
+template <int S, bool CHECK>
+__device__ __forceinline__ void loe_pair(const LoeArgs& a, const float* AA, const int4 q, const int lane,
+                                         float& acc0, float& acc1) {
+  int j0 = q.x, j1 = q.z;
+  if (CHECK && ((unsigned)j0 >= (unsigned)a.n_slots || (unsigned)j1 >= (unsigned)a.n_slots)) {
+    if (lane == 0) atomicOr(a.status, kStatusBounds);
+    j0 = j1 = 0;
+  }
+  acc0 = __fmaf_rn(__int_as_float(q.y), AA[j0 * S + lane], acc0);
+  acc1 = __fmaf_rn(__int_as_float(q.w), AA[j1 * S + lane], acc1);
+}
+
+// The sink tasks of one warp (step 3 of the kernel).  Its stream holds, per task,
+// a header h = {x, (pairs << 8) | flags, z, row coefficient} and the task's entry
+// pairs right after it.  x is the row s, or for a top operand (flags bit 1) its
+// first factor with z the second: the top operand's value is then formed from
+// its factors and its adjoint pushed to them (its own adjoint is not kept).
+// Epilogue: phi += AA_s (lin + half u); adjoint g = phibar (lin + u) to G_s, or
+// G_x += g AA_z, G_z += g AA_x.  While a task runs, the next header and the
+// items after it (the next task's first pairs, when it has that many) are loaded.
+template <bool GRAD, int RO, int S, bool CHECK>
+__device__ __forceinline__ void loe_tasks(const LoeArgs& a, float* AA, float* G, const float pbl,
+                                          Acc<float, RO>& phiacc, const int warp, const int lane) {
+  // The stream is followed by kLoeStreamPad zero items, so every item read ahead
+  // here (the next header, up to kPairBatch items after it, the last batch of a
+  // task) lies inside the allocation; items past a task are loaded but not used.
+  const int4* p = a.stream + a.wbeg[warp];
+  const int4* const pend = a.stream + a.wbeg[warp + 1];
+  if (p >= pend) return;
+  const float half = GRAD ? 0.5f : 1.f;
+  int4 h = __ldg(p);
+  int4 cur[kPairBatch];
+#pragma unroll
+  for (int u = 0; u < kPairBatch; ++u) cur[u] = __ldg(p + 1 + u);
+  while (true) {
+    const int np = h.y >> 8;
+    const int4* const pn = p + 1 + np;  // the next header
+    const bool more = pn < pend;
+    const int4 hn = __ldg(pn);
+    float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u)
+      if (u < np) loe_pair<S, CHECK>(a, AA, cur[u], lane, acc0, acc1);
+    // the next task's first pairs: the items after its header
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u) cur[u] = __ldg(pn + 1 + u);
+    // longer tasks: further batches, loaded together
+    for (int b = kPairBatch; b < np; b += kPairBatch) {
+      int4 bt[kPairBatch];
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u) bt[u] = __ldg(p + 1 + b + u);
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u)
+        if (b + u < np) loe_pair<S, CHECK>(a, AA, bt[u], lane, acc0, acc1);
+    }
+    const float acc = acc0 + acc1;
+    const bool top = (h.y & 2) != 0;
+    int x = h.x, z = h.z;
+    bool ok = true;
+    if (CHECK) {
+      const unsigned lim = GRAD ? (unsigned)a.n_g : (unsigned)a.n_slots;
+      if ((unsigned)x >= lim || (top && (unsigned)z >= lim)) {
+        if (lane == 0) atomicOr(a.status, kStatusBounds);
+        ok = false;
+      }
+    }
+    if (ok) {
+      float ap, xl = 0.f, xr = 0.f;
+      if (top) {
+        xl = AA[x * S + lane];
+        xr = AA[z * S + lane];
+        ap = xl * xr;
+      } else {
+        ap = AA[x * S + lane];
+      }
+      const float lin = __int_as_float(h.w);
+      phiacc.add(ap * __fmaf_rn(half, acc, lin));
+      if constexpr (GRAD) {
+        const float g = pbl * (acc + lin);
+        if (top) {
+          atomicAdd(G + x * S + lane, g * xr);
+          atomicAdd(G + z * S + lane, g * xl);
+        } else {
+          atomicAdd(G + x * S + lane, g);
+        }
+      }
+    }
+    if (!more) break;
+    p = pn;
+    h = hn;
+  }
+}
+
 template <bool GRAD, int RO, int NT, bool GLOBAL>
 __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -100,118 +194,13 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
       }
       __syncthreads();
     }
-    // 3. tasks: one task per warp
+    // 3. tasks: each warp walks its own stream, one task at a time
     Acc<float, RO> phiacc;
-    const float half = GRAD ? 0.5f : 1.f;
     const float pbl = GRAD ? pb[lane] : 0.f;
-    // Most tasks hold at most 2 kPairBatch entries: the header and the first
-    // kPairBatch entry pairs of the warp's next task are loaded while the current
-    // task runs (the pairs once its header has arrived, before the epilogue).
-    int t = warp;
-    int4 task = make_int4(-1, 0, 0, 0);
-    int q0 = 0, q1 = 0;
-    float lin = 0.f;
-    int4 cur[kPairBatch];
-#pragma unroll
-    for (int u = 0; u < kPairBatch; ++u) cur[u] = make_int4(0, 0, 0, 0);
-    if (t < a.n_tasks) {
-      task = __ldg(a.tasks + t);
-      const int4 h = __ldg(a.thdr + t);
-      q0 = h.x;
-      q1 = h.y;
-      lin = __int_as_float(h.z);
-      const int np0 = (q1 - q0) >> 1;
-#pragma unroll
-      for (int u = 0; u < kPairBatch; ++u)
-        if (u < np0) cur[u] = __ldg(a.ent + (q0 >> 1) + u);
-    }
-    while (t < a.n_tasks) {
-      const int tn = t + NW;
-      int4 task_n = make_int4(-1, 0, 0, 0);
-      int q0n = 0, q1n = 0;
-      float lin_n = 0.f;
-      if (tn < a.n_tasks) {
-        task_n = __ldg(a.tasks + tn);
-        const int4 h = __ldg(a.thdr + tn);
-        q0n = h.x;
-        q1n = h.y;
-        lin_n = __int_as_float(h.z);
-      }
-      const int4* ep = a.ent + (q0 >> 1);
-      const int np = (q1 - q0) >> 1;
-      float acc0 = 0.f, acc1 = 0.f;
-      // the first batch, already loaded
-#pragma unroll
-      for (int u = 0; u < kPairBatch; ++u) {
-        if (u < np) {
-          int j0 = cur[u].x, j1 = cur[u].z;
-          if (a.check && ((unsigned)j0 >= (unsigned)a.n_slots || (unsigned)j1 >= (unsigned)a.n_slots)) {
-            if (lane == 0) atomicOr(a.status, kStatusBounds);
-            j0 = j1 = 0;
-          }
-          acc0 = __fmaf_rn(__int_as_float(cur[u].y), AA[j0 * S + lane], acc0);
-          acc1 = __fmaf_rn(__int_as_float(cur[u].w), AA[j1 * S + lane], acc1);
-        }
-      }
-      // longer tasks: further batches, loaded together
-      for (int b = kPairBatch; b < np; b += kPairBatch) {
-        int4 bt[kPairBatch];
-#pragma unroll
-        for (int u = 0; u < kPairBatch; ++u) bt[u] = b + u < np ? __ldg(ep + b + u) : make_int4(0, 0, 0, 0);
-#pragma unroll
-        for (int u = 0; u < kPairBatch; ++u) {
-          if (b + u < np) {
-            int j0 = bt[u].x, j1 = bt[u].z;
-            if (a.check && ((unsigned)j0 >= (unsigned)a.n_slots || (unsigned)j1 >= (unsigned)a.n_slots)) {
-              if (lane == 0) atomicOr(a.status, kStatusBounds);
-              j0 = j1 = 0;
-            }
-            acc0 = __fmaf_rn(__int_as_float(bt[u].y), AA[j0 * S + lane], acc0);
-            acc1 = __fmaf_rn(__int_as_float(bt[u].w), AA[j1 * S + lane], acc1);
-          }
-        }
-      }
-      // the next task's first batch
-      {
-        const int npn = (q1n - q0n) >> 1;
-#pragma unroll
-        for (int u = 0; u < kPairBatch; ++u)
-          cur[u] = u < npn ? __ldg(a.ent + (q0n >> 1) + u) : make_int4(0, 0, 0, 0);
-      }
-      const float acc = acc0 + acc1;
-      const int row = task.x;
-      const bool top = (task.y & 2) != 0;
-      bool ok = true;
-      if (a.check && (unsigned)row >= (unsigned)a.n_slots) {
-        if (lane == 0) atomicOr(a.status, kStatusBounds);
-        ok = false;
-      }
-      if (ok) {
-        float ap, xl = 0.f, xr = 0.f;
-        if (GRAD && top) {
-          xl = AA[task.z * S + lane];
-          xr = AA[task.w * S + lane];
-          ap = xl * xr;
-        } else {
-          ap = AA[row * S + lane];
-        }
-        phiacc.add(ap * __fmaf_rn(half, acc, lin));
-        if constexpr (GRAD) {
-          const float g = pbl * (acc + lin);
-          if (top) {
-            atomicAdd(G + task.z * S + lane, g * xr);
-            atomicAdd(G + task.w * S + lane, g * xl);
-          } else {
-            atomicAdd(G + row * S + lane, g);
-          }
-        }
-      }
-      t = tn;
-      task = task_n;
-      q0 = q0n;
-      q1 = q1n;
-      lin = lin_n;
-    }
+    if (a.check)
+      loe_tasks<GRAD, RO, S, true>(a, AA, G, pbl, phiacc, warp, lane);
+    else
+      loe_tasks<GRAD, RO, S, false>(a, AA, G, pbl, phiacc, warp, lane);
     __syncthreads();
     // 4. adjoint through the inner operand nodes, order descending
     if constexpr (GRAD) {
@@ -289,38 +278,41 @@ size_t loe_global_bytes_per_cta(int n_slots, int n_g, bool grad) {
   return dev::loe_global_floats(n_slots, n_g, grad) * sizeof(float);
 }
 
-__global__ void bind_rm_kernel(const float* __restrict__ c, const int32_t* __restrict__ col,
-                               const int32_t* __restrict__ ebasis, const uint8_t* __restrict__ ew2, int64_t n,
-                               int2* __restrict__ ent) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t b = ebasis[i];
-    const float v = b >= 0 ? c[b] * (ew2[i] ? 2.f : 1.f) : 0.f;
-    ent[i] = make_int2(col[i], __float_as_int(v));
-  }
-}
-
-// thdr[t] = {first entry, end entry, coefficient bits, 0}: the coefficient is c of
-// task t's row when t is the row's first task and the row is a basis function, else 0
-__global__ void bind_thdr_kernel(const float* __restrict__ c, const int4* __restrict__ tasks,
-                                 const int32_t* __restrict__ toff, const int32_t* __restrict__ slot_basis, int32_t n,
-                                 int4* __restrict__ thdr) {
+// One thread per task: its header {target, (pairs << 8) | flags, second factor,
+// row coefficient} and its entry pairs {column, c of the entry's basis function
+// (doubled on the diagonal of the symmetric form; 0 for padding)}.  The target of
+// a top operand is its first factor (the kernel forms its value from both
+// factors and pushes adjoints to them), otherwise the row itself; the row
+// coefficient is c of the row when the task is the row's first and the row is a
+// basis function.
+__global__ void bind_loe_kernel(const float* __restrict__ c, const int4* __restrict__ tasks,
+                                const int32_t* __restrict__ toff, const int32_t* __restrict__ col,
+                                const int32_t* __restrict__ ebasis, const uint8_t* __restrict__ ew2,
+                                const int32_t* __restrict__ slot_basis, const int32_t* __restrict__ hpos, int32_t n,
+                                int4* __restrict__ stream) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int4 t = tasks[i];
+    const int32_t q0 = toff[i], q1 = toff[i + 1];
     const int32_t b = slot_basis[t.x];
     const float lin = ((t.y & 5) == 5 && b >= 0) ? c[b] : 0.f;
-    thdr[i] = make_int4(toff[i], toff[i + 1], __float_as_int(lin), 0);
+    const bool top = (t.y & 2) != 0;
+    int4* h = stream + hpos[i];
+    *h = make_int4(top ? t.z : t.x, (((q1 - q0) >> 1) << 8) | (t.y & 0xff), top ? t.w : 0, __float_as_int(lin));
+    int2* e = reinterpret_cast<int2*>(h + 1);
+    for (int32_t q = q0; q < q1; ++q) {
+      const int32_t eb = ebasis[q];
+      const float v = eb >= 0 ? c[eb] * (ew2[q] ? 2.f : 1.f) : 0.f;
+      e[q - q0] = make_int2(col[q], __float_as_int(v));
+    }
   }
 }
 
-cudaError_t launch_bind_rm(const float* c, const int32_t* col, const int32_t* ebasis, const uint8_t* ew2, int64_t n,
-                           int2* ent, const int4* tasks, const int32_t* toff, const int32_t* slot_basis,
-                           int32_t n_tasks, int4* thdr, cudaStream_t st) {
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-  if (blocks < 1) blocks = 1;
-  bind_rm_kernel<<<blocks, 256, 0, st>>>(c, col, ebasis, ew2, n, ent);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || n_tasks == 0) return e;
-  bind_thdr_kernel<<<(n_tasks + 255) / 256, 256, 0, st>>>(c, tasks, toff, slot_basis, n_tasks, thdr);
+cudaError_t launch_bind_loe(const float* c, const int4* tasks, const int32_t* toff, const int32_t* col,
+                            const int32_t* ebasis, const uint8_t* ew2, const int32_t* slot_basis,
+                            const int32_t* hpos, int32_t n_tasks, int4* stream, cudaStream_t st) {
+  if (n_tasks == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>(((int64_t)n_tasks + 255) / 256, 4096);
+  bind_loe_kernel<<<blocks, 256, 0, st>>>(c, tasks, toff, col, ebasis, ew2, slot_basis, hpos, n_tasks, stream);
   return cudaGetLastError();
 }
 

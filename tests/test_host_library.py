@@ -300,6 +300,110 @@ def test_row_major_plan_emulation_matches_oracle(name):
     assert np.all(R % 2 == 0)
 
 
+def loe_streams(dag, mode, c):
+    """The per-warp task streams as the binding writes them: a header (x, pairs << 8 | flags, z, lin)
+    then the task's pairs, task t of the row-major copy in warp t mod 32 at item loe_hpos[t]."""
+    P = plan_arrays(dag, mode)
+    R = {k: L.ace_dag_plan_array(dag.handle, f"{mode}_rm_{k}") for k in ["tasks", "off", "col", "ebasis", "ew2"]}
+    wbeg = L.ace_dag_plan_array(dag.handle, f"{mode}_loe_wbeg")
+    hpos = L.ace_dag_plan_array(dag.handle, f"{mode}_loe_hpos")
+    T = R["tasks"].reshape(-1, 4)
+    c = c.reshape(-1)
+    items = [None] * int(wbeg[-1])
+    for t, (row, flags, pl, pr) in enumerate(T):
+        q0, q1 = R["off"][t], R["off"][t + 1]
+        b = P["slot_basis"][row]
+        lin = c[b] if ((flags & 5) == 5 and b >= 0) else 0.0
+        top = (flags & 2) > 0
+        assert items[hpos[t]] is None
+        items[hpos[t]] = ("h", pl if top else row, ((q1 - q0) // 2) << 8 | flags, pr if top else 0, lin)
+        for k in range(q0, q1, 2):
+            v = [c[R["ebasis"][q]] * (2.0 if R["ew2"][q] else 1.0) if R["ebasis"][q] >= 0 else 0.0 for q in (k, k + 1)]
+            j = hpos[t] + 1 + (k - q0) // 2
+            assert items[j] is None
+            items[j] = ("p", R["col"][k], v[0], R["col"][k + 1], v[1])
+    assert all(it is not None for it in items)
+    return wbeg, items, T
+
+
+def emulate_loe_streams(dag, mode, A, c, phibar=None):
+    """The one-environment-per-lane kernel's task loop: every warp walks its stream header by header."""
+    P = plan_arrays(dag, mode)
+    wbeg, items, T = loe_streams(dag, mode, c)
+    n_env, K = A.shape
+    n_g = int(P["n_g"][0])
+    AA = np.zeros((n_env, len(P["slot_node"])))
+    AA[:, :K] = A
+    off = P["fwd_off"]
+    for lv in range(len(off) - 1):
+        s = slice(off[lv], off[lv + 1])
+        AA[:, P["fwd_slot"][s]] = AA[:, P["fwd_l"][s]] * AA[:, P["fwd_r"][s]]
+    phi = np.zeros(n_env)
+    G = np.zeros((n_env, n_g))
+    pb = np.ones(n_env) if phibar is None else phibar.reshape(-1)
+    half = 0.5 if mode == "sym" else 1.0
+    seen = 0
+    for w in range(len(wbeg) - 1):
+        p = wbeg[w]
+        while p < wbeg[w + 1]:
+            kind, x, y, z, lin = items[p]
+            assert kind == "h"
+            npair, top = y >> 8, (y & 2) > 0
+            u = np.zeros(n_env)
+            for q in range(p + 1, p + 1 + npair):
+                kind2, j0, c0, j1, c1 = items[q]
+                assert kind2 == "p"
+                u += c0 * AA[:, j0] + c1 * AA[:, j1]
+            ap = AA[:, x] * AA[:, z] if top else AA[:, x]
+            phi += ap * (lin + half * u)
+            if mode == "sym":
+                g = pb * (u + lin)
+                if top:
+                    G[:, x] += g * AA[:, z]
+                    G[:, z] += g * AA[:, x]
+                else:
+                    G[:, x] += g
+            p += 1 + npair
+            seen += 1
+    assert seen == len(T)
+    if mode == "one":
+        return phi, None
+    off = P["rev_off"]
+    for lv in range(len(off) - 1):
+        for i in range(off[lv], off[lv + 1]):
+            s_, l_, r_ = P["rev_slot"][i], P["rev_l"][i], P["rev_r"][i]
+            gs = G[:, s_].copy()
+            G[:, l_] += gs * AA[:, r_]
+            G[:, r_] += gs * AA[:, l_]
+    return phi, G[:, :K]
+
+
+@pytest.mark.parametrize("name", ["plain_fp64_k64", "fwd_grad_k392"])
+def test_per_warp_stream_emulation_matches_oracle(name):
+    w = W.WORKLOADS[name]
+    o = workload_index_set(w)
+    s = Spec.from_workload(w)
+    dag = Dag(s)
+    A = W.draw_A(3, s.K)
+    c = W.draw_c(o.deg, 1)
+    pb = np.random.default_rng(3).standard_normal((3, 1))
+    ref = phi_naive(A, o, c)
+    for mode in ["one", "sym"]:
+        phi, _ = emulate_loe_streams(dag, mode, A, c, pb)
+        assert normalized_error(phi[:, None], ref, error_scale(A, o, c)) < 1e-12
+    _, dA = emulate_loe_streams(dag, "sym", A, c, pb)
+    assert normalized_error(dA, grad_naive(A, o, c, pb), grad_error_scale(A, o, c, pb)) < 1e-12
+    # warp w holds tasks w, w + 32, ... in order
+    hpos = L.ace_dag_plan_array(dag.handle, "sym_loe_hpos")
+    wbeg = L.ace_dag_plan_array(dag.handle, "sym_loe_wbeg")
+    assert len(wbeg) == 33
+    for t in range(len(hpos)):
+        wv = t % 32
+        assert wbeg[wv] <= hpos[t] < wbeg[wv + 1]
+        if t + 32 < len(hpos):
+            assert hpos[t + 32] > hpos[t]
+
+
 def test_plan_emulation_stress_sample():
     """Largest workload (K = 810, nu <= 6): plan arithmetic against the oracle on 2 environments."""
     w = W.WORKLOADS["stress_k810"]
