@@ -156,7 +156,11 @@ ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_si
  * and the cold tasks "cold_tasks", "cold_slice_off", "cold_slice_steps",
  * "cold_ca", "cold_cb" (factor slots of the operand read), "cold_ebasis",
  * "cold_ew2"; also "n_stored" and the stored forward levels "fwd_stored_slot",
- * "fwd_stored_l", "fwd_stored_r", "fwd_stored_off".
+ * "fwd_stored_l", "fwd_stored_r", "fwd_stored_off"; and per sink form the layout
+ * of the row-major tasks as one stream per warp of the one-environment-per-lane
+ * kernel: "loe_wbeg" (33 values: first 16-byte item of each of the 32 warps'
+ * streams, then the total) and "loe_hpos" (item of each task's header; task t
+ * belongs to warp t mod 32 and its entry pairs follow its header).
  * Every array is exported as int32.  *count receives the number of int32
  * values; out (host) may be NULL to query the size.  Errors: INVALID_ARG for an
  * unknown name. */
@@ -178,8 +182,8 @@ ace_status ace_dag_upload(ace_dag* dag, void* stream);
  *        coefficients bound by the previous call with the same n_out and dtype.
  *  phi : dev [n_env][n_out] in dtype, written.
  *  n_out in {1, 2, 4, 8, 16}.  readout: ACE_READOUT_PLAIN (FP32 sums),
- *  ACE_READOUT_COMPENSATED (per-task partial sums in FP32, combined with
- *  compensated (TwoSum) FP32 accumulation), ACE_READOUT_FP64_FINAL (partials
+ *  ACE_READOUT_COMPENSATED (per-task partial sums in FP32, combined by Kahan's
+ *  compensated FP32 summation), ACE_READOUT_FP64_FINAL (partials
  *  combined in FP64).  For ACE_F64 all arithmetic is FP64 and readout is ignored.
  * Kernel forms (chosen by the autotuner's result, else automatically): one
  * environment per lane with the stored values of 32 environments in shared

@@ -6,11 +6,13 @@
 // owns environment e, and a whole warp works on one task at a time.  The
 // stored values of the tile are AA[slot][e] with a row stride of 33 floats, so
 // that a warp reading slot j touches 32 consecutive banks (no conflicts) and
-// the transposed copies of A in and dA out hit distinct banks too.  Entries
-// {column, coefficient} are read two at a time with one warp-uniform 16-byte
-// load (a broadcast), so metadata costs half a shared-memory-pipe wavefront per
-// entry and 32 environments; the gather is one conflict-free wavefront.  Used
-// when 32 environments of stored values (and adjoints) fit in shared memory.
+// the transposed copies of A in and dA out hit distinct banks too.  Every warp
+// reads its own contiguous stream of 16-byte items (a task header, then the
+// task's entries {column, coefficient} two per item), each item one warp-uniform
+// load (a broadcast): metadata costs half a load per entry and 32 environments,
+// the gather one conflict-free wavefront.  Used when 32 environments of stored
+// values (and adjoints) fit in shared memory; otherwise the same code keeps them
+// in a global workspace.
 #include <cstdint>
 #include <cuda_runtime.h>
 

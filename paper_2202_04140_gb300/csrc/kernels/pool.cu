@@ -30,12 +30,12 @@ namespace ace {
 namespace dev {
 
 constexpr int kPoolLmax = 8;
-constexpr int kPoolNL = (kPoolLmax + 1) * (kPoolLmax + 1);
 constexpr int kPoolMaxR = 16;  // radial x feature factors per neighbour
 constexpr int kPoolMaxF = 4;   // feature degrees 0..3
 constexpr int kPoolQ = (kPoolLmax + 2) * (kPoolLmax + 3) / 2;  // Q_l^m for 0 <= m <= l+1 <= lmax+1
 constexpr int kPoolWarps = 4;
 constexpr int kPoolChunk = 32;  // neighbours staged per pass
+constexpr int kPoolGroupEnvs = 4;  // adjoint: consecutive environments per warp, neighbours walked as one list
 
 // K_lm (sqrt2 N_lm for m > 0, N_l0 for m = 0) and the recurrence coefficients,
 // filled once from the host in double precision.
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
   }
 }
 
-// Adjoint: one warp per environment, one lane per neighbour.  With
+// Adjoint: one warp per group of environments, one lane per neighbour.  With
 // G_q,lm = dphi/dA_q,lm (q the radial x feature factor) the force on neighbour j is
 // built from
 //   h_lm = sum_q G_q,lm R_q(r_j),   hd_lm = sum_q G_q,lm dR_q/dr(r_j)
@@ -184,6 +184,10 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_kernel(const float* __re
 // outside, each row of G read with 16-byte broadcast loads), then
 //   dphi/dr_j = rh sum_lm hd_lm Y_lm + (grad_u - rh (rh . grad_u)) / r,
 //   grad_u = sum_lm h_lm dY_lm/d(unit vector).
+// A warp takes kPoolGroupEnvs consecutive environments at a time and walks their
+// neighbours as one list (lane i: neighbour i, i + 32, ...), so that short
+// neighbour lists do not leave most lanes of a second pass idle; G of the group
+// is staged in dynamic shared memory, [warp][environment][q][NLP].
 template <int LMAX>
 __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float* __restrict__ pos,
                                                                     const float* __restrict__ mu,
@@ -194,21 +198,34 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
   constexpr int NL = (LMAX + 1) * (LMAX + 1);
   constexpr int NL4 = (NL + 3) / 4;  // 16-byte groups per row of G
   constexpr int NLP = 4 * NL4;       // row stride in shared memory
-  __shared__ __align__(16) float sG[kPoolWarps][kPoolMaxR * NLP];
+  extern __shared__ __align__(16) float pool_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const geo::Cut cut = geo::make_cut(rc);
   const float two_over_rc = 2.f / rc;
   const int nR = nmax - nmin + 1;
   const int K = nR * kf * NL;
-  for (int64_t env = blockIdx.x * (int64_t)kPoolWarps + warp; env < n_env; env += (int64_t)gridDim.x * kPoolWarps) {
+  const int env_floats = nR * kf * NLP;
+  float* const sGw = pool_smem + (size_t)warp * kPoolGroupEnvs * env_floats;
+  const int64_t n_groups = (n_env + kPoolGroupEnvs - 1) / kPoolGroupEnvs;
+  for (int64_t grp = blockIdx.x * (int64_t)kPoolWarps + warp; grp < n_groups; grp += (int64_t)gridDim.x * kPoolWarps) {
+    const int64_t e0 = grp * kPoolGroupEnvs;
+    const int ne = (int)(n_env - e0 < kPoolGroupEnvs ? n_env - e0 : kPoolGroupEnvs);
     __syncwarp();
-    for (int i = lane; i < K; i += 32) {
-      const int row = i / NL;
-      sG[warp][row * NLP + (i - row * NL)] = dA[env * K + i];
-    }
+    for (int b = 0; b < ne; ++b)
+      for (int i = lane; i < K; i += 32) {
+        const int row = i / NL;
+        sGw[b * env_floats + row * NLP + (i - row * NL)] = dA[(e0 + b) * K + i];
+      }
     __syncwarp();
-    const int64_t j0 = offsets[env], j1 = offsets[env + 1];
-    for (int64_t j = j0 + lane; j < j1; j += 32) {
+    // neighbour offsets of the group (environments past the end repeat the last one)
+    int64_t ob[kPoolGroupEnvs + 1];
+#pragma unroll
+    for (int b = 0; b <= kPoolGroupEnvs; ++b) ob[b] = offsets[e0 + (b < ne ? b : ne)];
+    for (int64_t j = ob[0] + lane; j < ob[kPoolGroupEnvs]; j += 32) {
+      int slot = 0;
+#pragma unroll
+      for (int b = 1; b < kPoolGroupEnvs; ++b) slot += j >= ob[b] ? 1 : 0;
+      const float* const sG = sGw + slot * env_floats;
       const float x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
       const geo::Geo gm = geo::geometry(x, y, z, cut);
       if (!gm.ok) {
@@ -234,7 +251,7 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
       for (int n = 0; n <= nmax; ++n) {
         if (n >= nmin) {
           const float rn = T * env2, drn = dT * two_over_rc * env2 + T * denv;
-          const float4* row = reinterpret_cast<const float4*>(&sG[warp][(n - nmin) * kf * NLP]);
+          const float4* row = reinterpret_cast<const float4*>(sG + (n - nmin) * kf * NLP);
 #pragma unroll
           for (int q = 0; q < NL4; ++q) {
             float4 v = row[q];
@@ -347,11 +364,12 @@ cudaError_t ensure_pool_constants() {
   return cudaSuccess;
 }
 
-int pool_grid(int64_t n_env) {
+// CTAs for n_groups warp work items (environments, or groups of them), at most 8 per SM.
+int pool_grid(int64_t n_groups) {
   int dev_id = 0, sms = 148;
   cudaGetDevice(&dev_id);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
-  int64_t need = (n_env + dev::kPoolWarps - 1) / dev::kPoolWarps;
+  int64_t need = (n_groups + dev::kPoolWarps - 1) / dev::kPoolWarps;
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
 }
 
@@ -381,15 +399,48 @@ cudaError_t launch_pool(const float* pos, const float* mu, const int64_t* offset
   return cudaGetLastError();
 }
 
+namespace {
+
+// The adjoint kernel for one lmax: its shared memory (G of kPoolGroupEnvs environments
+// per warp) can pass the 48 KB default (16 radial x feature rows at lmax 8 take 86 KB).
+template <int LMAX>
+cudaError_t launch_pool_grad_l(int grid, size_t smem, cudaStream_t st, const float* pos, const float* mu,
+                               const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax, int kf,
+                               const float* dA, float alpha, float* dpos) {
+  if (smem > 48 * 1024) {  // a per-device attribute: set on every such launch
+    const cudaError_t e =
+        cudaFuncSetAttribute(dev::pool_grad_kernel<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dev::pool_grad_kernel<LMAX><<<grid, dev::kPoolWarps * 32, smem, st>>>(pos, mu, offsets, n_env, rc, nmin, nmax, kf,
+                                                                         dA, alpha, dpos);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_pool_grad(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, float rc,
                              int nmin, int nmax, int lmax, int kmax, const float* dA, float alpha, float* dpos,
                              cudaStream_t st) {
   cudaError_t e = ensure_pool_constants();
   if (e != cudaSuccess) return e;
-  const int grid = pool_grid(n_env);
   const int kf = kmax + 1;
-  ACE_POOL_DISPATCH(pool_grad_kernel, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos)
-  return cudaGetLastError();
+  const int64_t n_groups = (n_env + dev::kPoolGroupEnvs - 1) / dev::kPoolGroupEnvs;
+  const int grid = pool_grid(n_groups);
+  const int NLP = 4 * (((lmax + 1) * (lmax + 1) + 3) / 4);
+  const size_t smem = (size_t)dev::kPoolWarps * dev::kPoolGroupEnvs * (nmax - nmin + 1) * kf * NLP * sizeof(float);
+  switch (lmax) {
+    case 0: return launch_pool_grad_l<0>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 1: return launch_pool_grad_l<1>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 2: return launch_pool_grad_l<2>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 3: return launch_pool_grad_l<3>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 4: return launch_pool_grad_l<4>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 5: return launch_pool_grad_l<5>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 6: return launch_pool_grad_l<6>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 7: return launch_pool_grad_l<7>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 8: return launch_pool_grad_l<8>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace ace
