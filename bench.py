@@ -419,13 +419,11 @@ def main():
         n_e2e = max(3, min(args.steps, 50))
 
         def e2e_step():
-            x = A_host.to(dev, non_blocking=True)
+            # ace_eval(_grad)_host: chunked, copies in and out overlapped with the evaluation
             if w.grad:
-                phi, dA = dag.evaluate_grad(x, step.c, None, args.readout)
-                dA_host.copy_(dA, non_blocking=True)
+                dag.evaluate_grad_host(A_host, step.c, None, args.readout, phi=phi_host, dA=dA_host, sync=False)
             else:
-                phi = dag.evaluate(x, step.c, args.readout)
-            phi_host.copy_(phi, non_blocking=True)
+                dag.evaluate_host(A_host, step.c, args.readout, phi=phi_host, sync=False)
 
         run_e2e = capture_or_direct(torch, e2e_step, not args.no_graph)
         barrier()
@@ -436,7 +434,8 @@ def main():
         barrier()
         e_ms = ev0.elapsed_time(ev1)
         e2e = {"value": w.n_env * n_e2e / (e_ms / 1e3), "unit": "env/s", "h2d_bytes_per_step": step.in_bytes,
-               "d2h_bytes_per_step": step.out_bytes, "steps": n_e2e}
+               "d2h_bytes_per_step": step.out_bytes, "steps": n_e2e,
+               "api": "ace_eval_grad_host" if w.grad else "ace_eval_host"}
     else:
         from paper_2202_04140_gb300.torch_api import energy_and_forces
         P_host = step.A0.cpu().pin_memory()

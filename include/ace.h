@@ -209,6 +209,33 @@ ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void*
                          int64_t n_env, int32_t n_out, int32_t dtype, int32_t readout, void* phi,
                          void* dA, void* stream);
 
+/* ace_eval / ace_eval_grad with HOST buffers: the copies to and from the device
+ * overlap the evaluation.  The batch is cut into chunks of chunk_env
+ * environments.  Chunk i's rows of A
+ * (and phi_bar) are copied to a device staging slot on one library stream, the
+ * chunk is evaluated on a second, and its phi (and dA) copied back on a third:
+ * while chunk i is evaluated, chunk i+1 is copied in and chunk i-1 out (two
+ * staging slots).  Evaluations run one after another, as ace_eval_grad would.
+ * chunk_env = 0 takes a third of the batch but at least 8 MiB of A per chunk
+ * (a batch smaller than that is one chunk).
+ *  A       : host [n_env][K] in dtype, read.
+ *  c       : dev [n_basis][n_out] in dtype, or NULL (bound coefficients), as ace_eval.
+ *  phi_bar : host [n_env][n_out] in dtype, or NULL (ones); ace_eval_grad_host only.
+ *  phi     : host [n_env][n_out] in dtype, written (may be NULL for the adjoint form).
+ *  dA      : host [n_env][K] in dtype, written; ace_eval_grad_host only.
+ * Host buffers should be page-locked (pinned): with pageable memory the copies
+ * are correct but do not overlap.  Asynchronous with respect to `stream`: the
+ * library streams first wait for the work queued on `stream`, and `stream` then
+ * waits for every chunk, so the host outputs are complete once `stream` is
+ * synchronised; the call can be captured in a CUDA graph (after a first call
+ * of the same chunk size, which allocates the staging slots kept in the
+ * handle).  Errors: as ace_eval / ace_eval_grad; INVALID_ARG for chunk_env < 0. */
+ace_status ace_eval_host(ace_dag* dag, const void* A, const void* c, int64_t n_env, int32_t n_out,
+                         int32_t dtype, int32_t readout, void* phi, int64_t chunk_env, void* stream);
+ace_status ace_eval_grad_host(ace_dag* dag, const void* A, const void* c, const void* phi_bar,
+                              int64_t n_env, int32_t n_out, int32_t dtype, int32_t readout, void* phi,
+                              void* dA, int64_t chunk_env, void* stream);
+
 /* Autotuner (not in the paper): time every compiled kernel configuration for
  * this request — the one-environment-per-lane kernel with its stored values in
  * shared memory and in a global workspace, and the tile-per-lane kernel with

@@ -32,7 +32,8 @@ ACE_READOUT_PLAIN, ACE_READOUT_COMPENSATED, ACE_READOUT_FP64_FINAL = 0, 1, 2
 EXPORTED = [
     "ace_last_error", "ace_abi_version", "ace_build_spec", "ace_spec_info", "ace_spec_tuples",
     "ace_spec_free", "ace_build_dag", "ace_dag_info", "ace_dag_export", "ace_dag_plan_info",
-    "ace_dag_plan_array", "ace_dag_free", "ace_dag_upload", "ace_dag_autotune", "ace_eval", "ace_eval_grad", "ace_eval_plain_workspace_bytes",
+    "ace_dag_plan_array", "ace_dag_free", "ace_dag_upload", "ace_dag_autotune", "ace_eval", "ace_eval_grad",
+    "ace_eval_host", "ace_eval_grad_host", "ace_eval_plain_workspace_bytes",
     "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_pool_A_feat", "ace_pool_A_feat_grad", "ace_stream_status", "ace_device_info",
     "ace_fma_peak",
 ]
@@ -73,6 +74,8 @@ _SIG = {
     "ace_dag_autotune": (C.c_int, [_p, _i64, _i32, _i32, _i32, _i32, _p, _P(_i32), _P(_i32), _P(C.c_float)]),
     "ace_eval": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, _i32, _p, _p]),
     "ace_eval_grad": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _i32, _i32, _p, _p, _p]),
+    "ace_eval_host": (C.c_int, [_p, _p, _p, _i64, _i32, _i32, _i32, _p, _i64, _p]),
+    "ace_eval_grad_host": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _i32, _i32, _p, _p, _i64, _p]),
     "ace_eval_plain_workspace_bytes": (C.c_int, [_p, _i64, _i32, _P(_sz)]),
     "ace_eval_plain_f64": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _p, _p, _p, _sz, _p]),
     "ace_eval_plain_f64_static": (C.c_int, [_p, _p, _p, _p, _i64, _i32, _p, _p, _p]),
@@ -199,6 +202,17 @@ def ace_eval(dag, A, c, n_env, n_out, dtype, readout, phi, stream=0):
 def ace_eval_grad(dag, A, c, phi_bar, n_env, n_out, dtype, readout, phi, dA, stream=0):
     _check(_lib.ace_eval_grad(dag, A, c, phi_bar, n_env, n_out, dtype, readout, phi, dA, stream),
            "ace_eval_grad")
+
+
+def ace_eval_host(dag, A, c, n_env, n_out, dtype, readout, phi, chunk_env=0, stream=0):
+    """A and phi are host pointers (page-locked memory lets the copies overlap the evaluation)."""
+    _check(_lib.ace_eval_host(dag, A, c, n_env, n_out, dtype, readout, phi, chunk_env, stream), "ace_eval_host")
+
+
+def ace_eval_grad_host(dag, A, c, phi_bar, n_env, n_out, dtype, readout, phi, dA, chunk_env=0, stream=0):
+    """A, phi_bar, phi and dA are host pointers (page-locked memory lets the copies overlap the evaluation)."""
+    _check(_lib.ace_eval_grad_host(dag, A, c, phi_bar, n_env, n_out, dtype, readout, phi, dA, chunk_env, stream),
+           "ace_eval_grad_host")
 
 
 def ace_eval_plain_workspace_bytes(dag, n_env, with_grad) -> int:

@@ -132,6 +132,54 @@ class Dag:
                         _stream())
         return phi, dA
 
+    def evaluate_host(self, A: torch.Tensor, c: torch.Tensor, readout: str = "plain", phi: torch.Tensor | None = None,
+                      chunk_env: int = 0, sync: bool = True) -> torch.Tensor:
+        """phi for host (CPU) A: copies in, evaluation and copies out overlapped in chunks
+        (ace_eval_host).  Pin A (and phi) for the overlap.  With sync=False the result is complete
+        once the current CUDA stream has been synchronised (the call can be captured in a graph)."""
+        return self._host_call(False, A, c, None, readout, phi, None, chunk_env, sync)[0]
+
+    def evaluate_grad_host(self, A: torch.Tensor, c: torch.Tensor, phi_bar: torch.Tensor | None = None,
+                           readout: str = "plain", phi: torch.Tensor | None = None, dA: torch.Tensor | None = None,
+                           chunk_env: int = 0, sync: bool = True):
+        """(phi, dA) for host (CPU) A, as evaluate_grad, through ace_eval_grad_host."""
+        return self._host_call(True, A, c, phi_bar, readout, phi, dA, chunk_env, sync)
+
+    def _host_call(self, grad, A, c, phi_bar, readout, phi, dA, chunk_env, sync):
+        if A.device.type != "cpu" or not A.is_contiguous():
+            raise ValueError("A must be a contiguous CPU tensor")
+        c = _dev(c, "c", A.dtype)
+        n_env = A.shape[0]
+        c2 = c.reshape(self.n_basis, -1)
+        n_out = c2.shape[1]
+        pin = A.is_pinned()
+
+        def host_out(t, shape, name):
+            if t is None:
+                return torch.empty(shape, dtype=A.dtype, pin_memory=pin)
+            if t.device.type != "cpu" or not t.is_contiguous() or t.dtype != A.dtype or tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be a contiguous CPU tensor of shape {shape} and A's dtype")
+            return t
+
+        phi = host_out(phi, (n_env, n_out), "phi")
+        if grad:
+            dA = host_out(dA, tuple(A.shape), "dA")
+            pb = 0
+            if phi_bar is not None:
+                phi_bar = phi_bar.reshape(n_env, n_out)
+                if phi_bar.device.type != "cpu" or not phi_bar.is_contiguous() or phi_bar.dtype != A.dtype:
+                    raise ValueError("phi_bar must be a contiguous CPU tensor of A's dtype")
+                pb = phi_bar.data_ptr()
+            L.ace_eval_grad_host(self.handle, A.data_ptr(), self._c_arg("sym", c, c2, n_out), pb, n_env, n_out,
+                                 _DTYPE[A.dtype], _READOUT[readout], phi.data_ptr(), dA.data_ptr(), chunk_env,
+                                 _stream())
+        else:
+            L.ace_eval_host(self.handle, A.data_ptr(), self._c_arg("one", c, c2, n_out), n_env, n_out,
+                            _DTYPE[A.dtype], _READOUT[readout], phi.data_ptr(), chunk_env, _stream())
+        if sync:
+            torch.cuda.current_stream().synchronize()
+        return phi, dA
+
     def evaluate_plain_f64(self, A: torch.Tensor, c: torch.Tensor, phi_bar: torch.Tensor | None = None,
                            grad: bool = False, workspace: torch.Tensor | None = None):
         """The plain FP64 graph walk (one thread per environment, node values in global memory)."""

@@ -1,0 +1,114 @@
+"""Host-buffer entry points (ace_eval_host, ace_eval_grad_host): chunked copies
+overlapped with the evaluation must give what the device entry points give on
+the same inputs, for every kernel form, chunk size (automatic, ragged last chunk,
+larger than the batch), pinned and pageable memory, and inside a CUDA graph;
+phi is summed in a fixed order (equal bit for bit), dA with atomics (compared to
+1e-5 of the condition-aware scale)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.basis import workload_index_set
+from oracle.evaluate import grad_error_scale
+from tests.metrics import normalized_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_2202_04140_gb300.torch_api import Spec
+    w = W.WORKLOADS["fwd_grad_k392"]
+    o = workload_index_set(w)
+    s = Spec.from_workload(w)
+    n_env = 1000
+    A = W.draw_A(n_env, s.K)
+    c = W.draw_c(o.deg, 1)
+    pb = np.random.default_rng(7).standard_normal((n_env, 1))
+    return w, o, s, A, c, pb
+
+
+@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg"])
+@pytest.mark.parametrize("chunk", [0, 300, 4096])
+def test_grad_host_matches_device(dev, case, kernel, chunk, monkeypatch):
+    from paper_2202_04140_gb300.torch_api import Dag
+    monkeypatch.setenv("ACE_KERNEL", kernel)
+    w, o, s, A, c, pb = case
+    d = Dag(s)
+    A32 = torch.tensor(A, dtype=torch.float32)
+    pb32 = torch.tensor(pb, dtype=torch.float32)
+    cd = torch.tensor(c, dtype=torch.float32, device=dev)
+    phi_d, dA_d = d.evaluate_grad(A32.to(dev), cd, pb32.to(dev), readout="compensated")
+    phi_h, dA_h = d.evaluate_grad_host(A32.pin_memory(), cd, pb32.pin_memory(), readout="compensated",
+                                       chunk_env=chunk)
+    assert phi_h.device.type == "cpu" and dA_h.device.type == "cpu"
+    assert torch.equal(phi_h, phi_d.cpu())
+    scale = grad_error_scale(A32.double().numpy(), o, c, pb32.double().numpy())
+    assert normalized_error(dA_h.double().numpy(), dA_d.double().cpu().numpy(), scale) < TOL32
+
+
+def test_forward_host_matches_device_pageable(dev, case):
+    from paper_2202_04140_gb300.torch_api import Dag
+    w, o, s, A, c, pb = case
+    d = Dag(s)
+    A32 = torch.tensor(A, dtype=torch.float32)          # pageable: correct, not overlapped
+    c16 = torch.tensor(np.random.default_rng(8).standard_normal((s.n_basis, 4)) * 1e-2, dtype=torch.float32,
+                       device=dev)
+    phi_d = d.evaluate(A32.to(dev), c16, readout="plain")
+    phi_h = d.evaluate_host(A32, c16, readout="plain", chunk_env=257)
+    assert torch.equal(phi_h, phi_d.cpu())
+
+
+def test_grad_host_in_cuda_graph(dev, case):
+    from paper_2202_04140_gb300.torch_api import Dag
+    w, o, s, A, c, pb = case
+    d = Dag(s)
+    A_host = torch.tensor(A, dtype=torch.float32).pin_memory()
+    phi_h = torch.empty((A.shape[0], 1), dtype=torch.float32).pin_memory()
+    dA_h = torch.empty_like(A_host).pin_memory()
+    cd = torch.tensor(c, dtype=torch.float32, device=dev)
+    phi_d, dA_d = d.evaluate_grad(A_host.to(dev), cd, readout="plain")
+
+    def step():
+        d.evaluate_grad_host(A_host, cd, None, "plain", phi=phi_h, dA=dA_h, chunk_env=256, sync=False)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()                                          # allocates the staging slots outside the capture
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    phi_h.zero_()
+    dA_h.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(phi_h, phi_d.cpu())
+    scale = grad_error_scale(A.astype(np.float32).astype(np.float64), o, c, np.ones((A.shape[0], 1)))
+    assert normalized_error(dA_h.double().numpy(), dA_d.double().cpu().numpy(), scale) < TOL32
+
+
+def test_host_entry_points_reject_bad_arguments(dev, case):
+    from paper_2202_04140_gb300 import ace as L
+    from paper_2202_04140_gb300.torch_api import Dag
+    w, o, s, A, c, pb = case
+    d = Dag(s)
+    A32 = torch.tensor(A[:4], dtype=torch.float32)
+    cd = torch.tensor(c, dtype=torch.float32, device=dev)
+    phi = torch.empty((4, 1))
+    with pytest.raises(L.AceError):
+        L.ace_eval_host(d.handle, A32.data_ptr(), cd.data_ptr(), 4, 1, L.ACE_F32, 0, phi.data_ptr(), -1, 0)
+    with pytest.raises(L.AceError):
+        L.ace_eval_grad_host(d.handle, A32.data_ptr(), cd.data_ptr(), 0, 4, 1, L.ACE_F32, 0, phi.data_ptr(), 0, 0, 0)
+    # n_env = 0 binds the coefficients and copies nothing
+    L.ace_eval_host(d.handle, 0, cd.data_ptr(), 0, 1, L.ACE_F32, 0, 0, 0, 0)
