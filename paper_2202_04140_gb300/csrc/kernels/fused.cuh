@@ -623,7 +623,13 @@ __device__ __forceinline__ void run_cold_tasks(const FusedArgs<T>& a, const T* _
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
-  for (int sl = warp; sl < a.n_cold_slices; sl += NW) {
+  // entry steps whose factor slots and coefficients are loaded together (fewer when the
+  // tile's accumulators already fill the registers: measured on 16 channels, E = 4)
+  constexpr int CB = E * NOUT >= 64 ? 1 : (E >= 4 ? 2 : 4);
+  // Hot slices go round-robin in order of decreasing length, so the last warps
+  // carry the least hot work: cold slice i goes to warp NW - 1 - i (a fixed
+  // assignment, so phi keeps its summation order).
+  for (int sl = NW - 1 - warp; sl < a.n_cold_slices; sl += NW) {
     const int4 task = __ldg(a.cold_tasks + (size_t)sl * 32 + lane);
     const int hdr = __ldg(a.cold_slice_steps + sl);
     const int steps = hdr & 0xffff, rounds = hdr >> 16;
@@ -633,25 +639,38 @@ __device__ __forceinline__ void run_cold_tasks(const FusedArgs<T>& a, const T* _
     for (int e = 0; e < E; ++e)
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) acc[e][c] = T(0);
-    for (int k = 0; k < steps; ++k) {
-      const size_t idx = (size_t)off + (size_t)k * 32 + lane;
-      const uint32_t q = __ldg(a.cold_cab + idx);
-      int ca = (int)(q & 0xffffu), cb = (int)(q >> 16);
-      if constexpr (CHECK) {
-        if ((unsigned)ca >= (unsigned)a.n_slots || (unsigned)cb >= (unsigned)a.n_slots) {
-          atomicOr(a.status, kStatusBounds);
-          ca = cb = 0;
+    for (int k0 = 0; k0 < steps; k0 += CB) {
+      uint32_t q[CB];
+      T v[CB][NOUT];
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        const size_t idx = (size_t)off + (size_t)(k0 + u) * 32 + lane;
+        q[u] = k0 + u < steps ? __ldg(a.cold_cab + idx) : 0u;
+        if (k0 + u < steps) {
+          load_vals<T, NOUT>(a.cold_vals + idx * NS + c0, v[u]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) v[u][c] = T(0);
         }
       }
-      T v[NOUT], xa[E], xb[E];
-      load_vals<T, NOUT>(a.cold_vals + idx * NS + c0, v);
-      load_slot<T, E>(AA + (size_t)ca * E, xa);
-      load_slot<T, E>(AA + (size_t)cb * E, xb);
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const T x = xa[e] * xb[e];
+      for (int u = 0; u < CB; ++u) {
+        int ca = (int)(q[u] & 0xffffu), cb = (int)(q[u] >> 16);
+        if constexpr (CHECK) {
+          if ((unsigned)ca >= (unsigned)a.n_slots || (unsigned)cb >= (unsigned)a.n_slots) {
+            atomicOr(a.status, kStatusBounds);
+            ca = cb = 0;
+          }
+        }
+        T xa[E], xb[E];
+        load_slot<T, E>(AA + (size_t)ca * E, xa);
+        load_slot<T, E>(AA + (size_t)cb * E, xb);
 #pragma unroll
-        for (int c = 0; c < NOUT; ++c) acc[e][c] = fma_t(v[c], x, acc[e][c]);
+        for (int e = 0; e < E; ++e) {
+          const T x = xa[e] * xb[e];
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) acc[e][c] = fma_t(v[u][c], x, acc[e][c]);
+        }
       }
     }
     T lin[NOUT];
