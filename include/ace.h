@@ -331,6 +331,32 @@ ace_status ace_pool_A_feat_grad(const float* pos, const float* mu, const int64_t
                                 int64_t n_pairs, float rc, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax,
                                 const float* dA, float alpha, float* dpos, void* stream);
 
+/* Energy and forces of a batch of environments with HOST buffers: pooling
+ * (ace_pool_A_feat), forward + adjoint with phi_bar = 1 (ace_eval_grad, FP32, one
+ * channel) and the pooling adjoint with alpha = -1 (ace_pool_A_feat_grad), the
+ * batch cut into chunks of chunk_env environments (0: a third of the batch, at
+ * least 8 MiB of A per chunk).  Positions (and mu) of chunk i are copied in on one
+ * library stream, the three kernels run on a second, its forces and phi are
+ * copied out on a third: the copies overlap the kernels of neighbouring chunks.
+ *  pos     : host [n_pairs][3] float, neighbour positions relative to their centre.
+ *  mu      : host [n_pairs] float (invariant feature per neighbour) or NULL (kmax = 0).
+ *  offsets : host [n_env + 1] int64, CSR: environment e owns pairs offsets[e] ..
+ *            offsets[e+1]; checked here (offsets[0] = 0, non-decreasing,
+ *            offsets[n_env] = n_pairs).
+ *  c       : dev [n_basis] float, or NULL (the bound coefficients of the adjoint form).
+ *  phi     : host [n_env] float, written.  forces: host [n_pairs][3] float, written
+ *            (F_j = -dphi/dr_j).
+ * The graph must be built over the pooling's one-particle set:
+ * K = (nmax - nmin + 1)(kmax + 1)(lmax + 1)^2.  Device buffers (positions, offsets,
+ * forces and phi of the whole batch, A and dA of two chunks) belong to the
+ * handle and grow on demand.  Asynchronous and capturable as ace_eval_grad_host.
+ * Errors: as ace_pool_A_feat and ace_eval_grad; INVALID_ARG for inconsistent offsets
+ * or a graph whose K does not match. */
+ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* mu, const int64_t* offsets,
+                                  int64_t n_env, int64_t n_pairs, const void* c, int32_t readout, float rc,
+                                  int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax, float* phi,
+                                  float* forces, int64_t chunk_env, void* stream);
+
 /* ---- status / utilities --------------------------------------------------------- */
 
 /* Synchronise `stream` and read the device status word of `dag` (written by

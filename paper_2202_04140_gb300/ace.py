@@ -34,7 +34,7 @@ EXPORTED = [
     "ace_spec_free", "ace_build_dag", "ace_dag_info", "ace_dag_export", "ace_dag_plan_info",
     "ace_dag_plan_array", "ace_dag_free", "ace_dag_upload", "ace_dag_autotune", "ace_eval", "ace_eval_grad",
     "ace_eval_host", "ace_eval_grad_host", "ace_eval_plain_workspace_bytes",
-    "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_pool_A_feat", "ace_pool_A_feat_grad", "ace_stream_status", "ace_device_info",
+    "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_pool_A_feat", "ace_pool_A_feat_grad", "ace_energy_forces_host", "ace_stream_status", "ace_device_info",
     "ace_fma_peak",
 ]
 
@@ -83,6 +83,8 @@ _SIG = {
     "ace_pool_A_grad": (C.c_int, [_p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _p, _f32, _p, _p]),
     "ace_pool_A_feat": (C.c_int, [_p, _p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _i32, _p, _p]),
     "ace_pool_A_feat_grad": (C.c_int, [_p, _p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _i32, _p, _f32, _p, _p]),
+    "ace_energy_forces_host": (C.c_int, [_p, _p, _p, _p, _i64, _i64, _p, _i32, _f32, _i32, _i32, _i32, _i32, _p, _p,
+                                         _i64, _p]),
     "ace_stream_status": (C.c_int, [_p, _p]),
     "ace_device_info": (C.c_int, [_P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
     "ace_fma_peak": (C.c_int, [_i64, _P(C.c_double), _P(C.c_double), _p]),
@@ -250,6 +252,13 @@ def ace_pool_A_feat(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax
 def ace_pool_A_feat_grad(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax, dA, alpha, dpos, stream=0):
     _check(_lib.ace_pool_A_feat_grad(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax, dA, alpha, dpos,
                                      stream), "ace_pool_A_feat_grad")
+
+
+def ace_energy_forces_host(dag, pos, mu, offsets, n_env, n_pairs, c, readout, rc, nmin, nmax, lmax, kmax, phi, forces,
+                           chunk_env=0, stream=0):
+    """pos, mu, offsets, phi and forces are host pointers; c a device pointer or 0."""
+    _check(_lib.ace_energy_forces_host(dag, pos, mu, offsets, n_env, n_pairs, c, readout, rc, nmin, nmax, lmax, kmax,
+                                       phi, forces, chunk_env, stream), "ace_energy_forces_host")
 
 
 def ace_stream_status(dag, stream=0) -> int:

@@ -118,6 +118,8 @@ struct ace_dag {
               hev_out[2] = {nullptr, nullptr}, hev_join[3] = {nullptr, nullptr, nullptr};
   void* hslot[2] = {nullptr, nullptr};
   size_t hslot_bytes = 0;
+  void* fbuf = nullptr;  // host-buffer forces pipeline: whole-batch positions, offsets, forces, phi; two A/dA chunks
+  size_t fbuf_bytes = 0;
   uint32_t* status = nullptr;
   std::vector<void*> allocations;
   std::vector<std::vector<uint16_t>> staging16;  // host copies kept alive until the upload completes
@@ -1027,6 +1029,7 @@ void ace_dag_free(ace_dag* dag) {
     if (dag->loe_ws) cudaFree(dag->loe_ws);
     for (void* p : dag->hslot)
       if (p) cudaFree(p);
+    if (dag->fbuf) cudaFree(dag->fbuf);
     for (cudaStream_t h : dag->hstream)
       if (h) cudaStreamDestroy(h);
     for (cudaEvent_t ev : {dag->hev_fork, dag->hev_in[0], dag->hev_in[1], dag->hev_done[0], dag->hev_done[1],
@@ -1294,6 +1297,91 @@ ace_status ace_pool_A_grad(const float* pos, const int64_t* offsets, int64_t n_e
                            void* stream) {
   return ace_pool_A_feat_grad(pos, nullptr, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, 0, dA, alpha, dpos,
                               stream);
+}
+
+ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* mu, const int64_t* offsets,
+                                  int64_t n_env, int64_t n_pairs, const void* c, int32_t readout, float rc,
+                                  int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax, float* phi, float* forces,
+                                  int64_t chunk_env, void* stream) {
+  ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, mu, kmax);
+  if (s != ACE_OK) return s;
+  if ((s = check_eval_args(dag, nullptr, 0, 1, ACE_F32, readout)) != ACE_OK) return s;
+  if (chunk_env < 0) return fail(ACE_ERR_INVALID_ARG, "chunk_env must be >= 0");
+  if (n_env > 0 && (!phi || (!forces && n_pairs > 0))) return fail(ACE_ERR_INVALID_ARG, "phi or forces is NULL");
+  if (c && !aligned16(c)) return fail(ACE_ERR_INVALID_ARG, "c must be 16-byte aligned");
+  const int64_t K = (int64_t)(nmax - nmin + 1) * (kmax + 1) * (lmax + 1) * (lmax + 1);
+  if (K != dag->K) return fail(ACE_ERR_INVALID_ARG, "the graph's K does not match the pooling's one-particle set");
+  if (n_env > 0) {  // the host holds the offsets: check them before any copy
+    if (offsets[0] != 0 || offsets[n_env] != n_pairs)
+      return fail(ACE_ERR_INVALID_ARG, "offsets must start at 0 and end at n_pairs");
+    for (int64_t e = 0; e < n_env; ++e)
+      if (offsets[e + 1] < offsets[e]) return fail(ACE_ERR_INVALID_ARG, "offsets must not decrease");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = ensure_uploaded(dag, st)) != ACE_OK) return s;
+  if ((s = bind(dag, dag->sym, c, 1, ACE_F32, st)) != ACE_OK) return s;
+  if (n_env == 0) return ACE_OK;
+  int64_t chunk = chunk_env;
+  if (chunk == 0) chunk = std::max<int64_t>((n_env + 2) / 3, (int64_t)((8u << 20) / ((size_t)K * 4)) + 1);
+  chunk = std::min(chunk, n_env);
+  // one allocation: positions, mu, offsets, forces, phi of the batch, then A and dA of two chunks
+  const size_t b_pos = dev::align16((size_t)n_pairs * 12), b_mu = kmax > 0 ? dev::align16((size_t)n_pairs * 4) : 0;
+  const size_t b_off = dev::align16((size_t)(n_env + 1) * 8), b_phi = dev::align16((size_t)n_env * 4);
+  const size_t b_a = dev::align16((size_t)chunk * K * 4);
+  const size_t need = 2 * b_pos + b_mu + b_off + b_phi + 4 * b_a;
+  if ((s = ensure_host_pipeline(dag, 0)) != ACE_OK) return s;
+  cudaError_t e;
+  if (need > dag->fbuf_bytes) {
+    if (dag->fbuf) cudaFree(dag->fbuf);
+    dag->fbuf = nullptr;
+    dag->fbuf_bytes = 0;
+    if ((e = cudaMalloc(&dag->fbuf, need)) != cudaSuccess) return cuda_fail(e, "cudaMalloc (forces pipeline)");
+    dag->fbuf_bytes = need;
+  }
+  unsigned char* base = static_cast<unsigned char*>(dag->fbuf);
+  float* pos_d = reinterpret_cast<float*>(base);
+  float* F_d = reinterpret_cast<float*>(base + b_pos);
+  float* mu_d = kmax > 0 ? reinterpret_cast<float*>(base + 2 * b_pos) : nullptr;
+  int64_t* off_d = reinterpret_cast<int64_t*>(base + 2 * b_pos + b_mu);
+  float* phi_d = reinterpret_cast<float*>(base + 2 * b_pos + b_mu + b_off);
+  unsigned char* slots = base + 2 * b_pos + b_mu + b_off + b_phi;
+  cudaStream_t hin = dag->hstream[0], hk = dag->hstream[1], hout = dag->hstream[2];
+  e = cudaEventRecord(dag->hev_fork, st);
+  for (cudaStream_t h : dag->hstream)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h, dag->hev_fork, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(off_d, offsets, (size_t)(n_env + 1) * 8, cudaMemcpyHostToDevice, hin);
+  s = ACE_OK;
+  for (int64_t k = 0, e0 = 0; e0 < n_env && e == cudaSuccess && s == ACE_OK; ++k, e0 += chunk) {
+    const int64_t n = std::min(chunk, n_env - e0);
+    const int64_t p0 = offsets[e0], p1 = offsets[e0 + n];
+    const int b = (int)(k & 1);
+    float* A_d = reinterpret_cast<float*>(slots + (size_t)b * 2 * b_a);
+    float* dA_d = reinterpret_cast<float*>(slots + (size_t)b * 2 * b_a + b_a);
+    // copy in this chunk's neighbours (the slots of A and dA are only used on the kernel stream)
+    if (p1 > p0) e = cudaMemcpyAsync(pos_d + 3 * p0, pos + 3 * p0, (size_t)(p1 - p0) * 12, cudaMemcpyHostToDevice, hin);
+    if (e == cudaSuccess && kmax > 0 && p1 > p0)
+      e = cudaMemcpyAsync(mu_d + p0, mu + p0, (size_t)(p1 - p0) * 4, cudaMemcpyHostToDevice, hin);
+    if (e == cudaSuccess) e = cudaEventRecord(dag->hev_in[b], hin);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hk, dag->hev_in[b], 0);
+    // pooling -> forward + adjoint -> pooling adjoint (offsets index the whole batch's positions)
+    if (e == cudaSuccess) e = launch_pool(pos_d, mu_d, off_d + e0, n, rc, nmin, nmax, lmax, kmax, A_d, hk);
+    if (e != cudaSuccess) break;
+    s = run_fused(dag, A_d, nullptr, nullptr, n, 1, ACE_F32, readout, phi_d + e0, dA_d, true, hk);
+    if (s != ACE_OK) break;
+    e = launch_pool_grad(pos_d, mu_d, off_d + e0, n, rc, nmin, nmax, lmax, kmax, dA_d, -1.f, F_d, hk);
+    if (e == cudaSuccess) e = cudaEventRecord(dag->hev_done[b], hk);
+    // copy out
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hout, dag->hev_done[b], 0);
+    if (e == cudaSuccess && p1 > p0)
+      e = cudaMemcpyAsync(forces + 3 * p0, F_d + 3 * p0, (size_t)(p1 - p0) * 12, cudaMemcpyDeviceToHost, hout);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(phi + e0, phi_d + e0, (size_t)n * 4, cudaMemcpyDeviceToHost, hout);
+  }
+  for (int i = 0; i < 3; ++i) {
+    if (cudaEventRecord(dag->hev_join[i], dag->hstream[i]) == cudaSuccess) cudaStreamWaitEvent(st, dag->hev_join[i], 0);
+  }
+  if (s != ACE_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "host-buffer forces pipeline");
+  return ACE_OK;
 }
 
 ace_status ace_stream_status(ace_dag* dag, void* stream) {

@@ -265,3 +265,37 @@ def energy_and_forces(dag: Dag, pos: torch.Tensor, offsets: torch.Tensor, c: tor
     phi, dA = dag.evaluate_grad(A, c, None, readout)
     F = pool_A_grad(pos, offsets, dA, nmin, nmax, lmax, rc, alpha=-1.0, mu=mu, kmax=kmax)
     return phi, F
+
+
+def energy_and_forces_host(dag: Dag, pos: torch.Tensor, offsets: torch.Tensor, c: torch.Tensor, nmin: int, nmax: int,
+                           lmax: int, rc: float, readout: str = "plain", mu: torch.Tensor | None = None,
+                           kmax: int = 0, phi: torch.Tensor | None = None, forces: torch.Tensor | None = None,
+                           chunk_env: int = 0, sync: bool = True):
+    """energy_and_forces for host (CPU) positions, offsets (and mu) through ace_energy_forces_host:
+    the batch in chunks, copies overlapped with the kernels.  Returns CPU (phi [n_env], F [n_pairs, 3]);
+    pin pos and the outputs for the overlap.  With sync=False the results are complete once the
+    current CUDA stream has been synchronised."""
+    for t, name in ((pos, "pos"), (offsets, "offsets")):
+        if t.device.type != "cpu" or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU tensor")
+    if pos.dtype != torch.float32 or offsets.dtype != torch.int64:
+        raise ValueError("pos must be float32 and offsets int64")
+    n_env = offsets.numel() - 1
+    n_pairs = pos.shape[0]
+    pin = pos.is_pinned()
+    if phi is None:
+        phi = torch.empty((n_env,), dtype=torch.float32, pin_memory=pin)
+    if forces is None:
+        forces = torch.empty((n_pairs, 3), dtype=torch.float32, pin_memory=pin)
+    if mu is not None and (mu.device.type != "cpu" or not mu.is_contiguous() or mu.dtype != torch.float32):
+        raise ValueError("mu must be a contiguous float32 CPU tensor")
+    c = _dev(c, "c", torch.float32)
+    c2 = c.reshape(dag.n_basis, -1)
+    if c2.shape[1] != 1:
+        raise ValueError("one output channel")
+    L.ace_energy_forces_host(dag.handle, pos.data_ptr(), mu.data_ptr() if mu is not None else 0, offsets.data_ptr(),
+                             n_env, n_pairs, dag._c_arg("sym", c, c2, 1), _READOUT[readout], float(rc), nmin, nmax,
+                             lmax, kmax, phi.data_ptr(), forces.data_ptr(), chunk_env, _stream())
+    if sync:
+        torch.cuda.current_stream().synchronize()
+    return phi, forces
