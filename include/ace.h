@@ -216,8 +216,8 @@ ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void*
  * chunk is evaluated on a second, and its phi (and dA) copied back on a third:
  * while chunk i is evaluated, chunk i+1 is copied in and chunk i-1 out (two
  * staging slots).  Evaluations run one after another, as ace_eval_grad would.
- * chunk_env = 0 takes a third of the batch but at least 8 MiB of A per chunk
- * (a batch smaller than that is one chunk).
+ * chunk_env = 0 takes a third of the batch but at least 8 MiB of A and 4 x SMs
+ * tiles of the kernel form per chunk (a smaller batch is one chunk).
  *  A       : host [n_env][K] in dtype, read.
  *  c       : dev [n_basis][n_out] in dtype, or NULL (bound coefficients), as ace_eval.
  *  phi_bar : host [n_env][n_out] in dtype, or NULL (ones); ace_eval_grad_host only.
@@ -334,8 +334,7 @@ ace_status ace_pool_A_feat_grad(const float* pos, const float* mu, const int64_t
 /* Energy and forces of a batch of environments with HOST buffers: pooling
  * (ace_pool_A_feat), forward + adjoint with phi_bar = 1 (ace_eval_grad, FP32, one
  * channel) and the pooling adjoint with alpha = -1 (ace_pool_A_feat_grad), the
- * batch cut into chunks of chunk_env environments (0: a third of the batch, at
- * least 8 MiB of A per chunk).  Positions (and mu) of chunk i are copied in on one
+ * batch cut into chunks of chunk_env environments (0: as ace_eval_grad_host).  Positions (and mu) of chunk i are copied in on one
  * library stream, the three kernels run on a second, its forces and phi are
  * copied out on a third: the copies overlap the kernels of neighbouring chunks.
  *  pos     : host [n_pairs][3] float, neighbour positions relative to their centre.

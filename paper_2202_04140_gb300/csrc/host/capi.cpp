@@ -714,6 +714,49 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
   return ACE_OK;
 }
 
+// Environments per tile of the kernel form that an evaluation of this request takes
+// (the same choice as run_fused: forced, tuned, else one environment per lane when it
+// fits, else tile per lane, else the global workspace): 32 for the one-environment-per-lane
+// forms, E for tile per lane.
+int64_t tile_envs_of(const ace_dag* d, const DevTaskSet& dt, int dtype, int n_out, int readout, bool grad,
+                     int64_t n_env) {
+  const int npad = nout_pad_of(n_out);
+  int choice = kernel_choice(), E_force = 0;
+  if (const char* v = std::getenv("ACE_TILE_E")) E_force = std::atoi(v);
+  if (choice == 0 && E_force == 0) {
+    auto it = d->tuned.find(std::make_tuple(dtype, npad, grad ? 1 : 0));
+    if (it != d->tuned.end()) {
+      choice = it->second.first;
+      E_force = it->second.second;
+    }
+  }
+  const bool loeg_ok = dtype == ACE_F32 && n_out == 1 && dt.rm_bound;
+  const bool loe_ok = loeg_ok && loe_smem(d->plan.n_slots, d->plan.n_g, grad, 1024) <= (size_t)d->smem_optin;
+  if (choice == 2 || choice == 3 || (loe_ok && choice != 1)) return 32;
+  int E = 0, nt = 0;
+  size_t smem = 0;
+  const void* k = nullptr;
+  bool stage = false;
+  const int ro = dtype == ACE_F32 ? readout : 0;
+  if (dt.col16 && choose_tile(d, dtype, npad, grad, ro, n_env, E_force, &E, &nt, &smem, &k, &stage) == ACE_OK)
+    return std::max(E, 1);
+  return 32;
+}
+
+// Automatic chunk size of the host-buffer entry points: a third of the batch, but at least
+// 8 MiB of A (smaller evaluations are launch-bound) and 4 x SMs tiles of the kernel form
+// (fewer tiles leave the last wave of a chunk's evaluation mostly idle).  Measured on the
+// stress graph (16,384 environments, tiles of 4): thirds 2.98 ms, quarters 3.03, eighths
+// 3.38, one piece 3.30; on the paper-degree graph (tiles of 32 environments, 44 ms of
+// evaluation) thirds lost a quarter of the throughput to the tail.
+int64_t auto_chunk(const ace_dag* d, const DevTaskSet& dt, int dtype, int n_out, int readout, bool grad,
+                   int64_t n_env, size_t row_bytes) {
+  const int64_t by_bytes = (int64_t)((8u << 20) / row_bytes) + 1;
+  const int64_t by_tiles = 4 * (int64_t)std::max(d->sm_count, 1) * tile_envs_of(d, dt, dtype, n_out, readout, grad,
+                                                                                 n_env);
+  return std::max<int64_t>({(n_env + 2) / 3, by_bytes, by_tiles});
+}
+
 // Streams, events and two staging slots of `bytes` each for the host-buffer entry points.
 ace_status ensure_host_pipeline(ace_dag* d, size_t bytes) {
   cudaError_t e;
@@ -748,12 +791,7 @@ ace_status eval_host(ace_dag* d, const void* A, const void* c, const void* phiba
   if ((s = bind(d, dt, c, n_out, dtype, st)) != ACE_OK) return s;
   if (n_env == 0) return ACE_OK;
   const size_t tsz = dtype == ACE_F32 ? 4 : 8;
-  // automatic: a third of the batch, but at least 8 MiB of A per chunk (smaller
-  // evaluations are launch-bound, so a small batch stays in one piece).  Measured on
-  // the stress graph (16,384 environments): thirds 2.98 ms, quarters 3.03, eighths 3.38,
-  // one piece 3.30.
-  if (chunk == 0)
-    chunk = std::max<int64_t>((n_env + 2) / 3, (int64_t)((8u << 20) / ((size_t)d->K * tsz)) + 1);
+  if (chunk == 0) chunk = auto_chunk(d, dt, dtype, n_out, readout, grad, n_env, (size_t)d->K * tsz);
   chunk = std::min(chunk, n_env);
   const size_t a_bytes = dev::align16((size_t)chunk * d->K * tsz);
   const size_t o_bytes = dev::align16((size_t)chunk * n_out * tsz);
@@ -1322,7 +1360,7 @@ ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* m
   if ((s = bind(dag, dag->sym, c, 1, ACE_F32, st)) != ACE_OK) return s;
   if (n_env == 0) return ACE_OK;
   int64_t chunk = chunk_env;
-  if (chunk == 0) chunk = std::max<int64_t>((n_env + 2) / 3, (int64_t)((8u << 20) / ((size_t)K * 4)) + 1);
+  if (chunk == 0) chunk = auto_chunk(dag, dag->sym, ACE_F32, 1, readout, true, n_env, (size_t)K * 4);
   chunk = std::min(chunk, n_env);
   // one allocation: positions, mu, offsets, forces, phi of the batch, then A and dA of two chunks
   const size_t b_pos = dev::align16((size_t)n_pairs * 12), b_mu = kmax > 0 ? dev::align16((size_t)n_pairs * 4) : 0;
