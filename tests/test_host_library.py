@@ -455,3 +455,38 @@ def test_invalid_arguments_fail_cleanly():
         L.ace_pool_A(0, 0, 1, 0, 5.0, 1, 8, 9, 0)                  # lmax > 8 unsupported
     with pytest.raises(L.AceError):
         L.ace_pool_A_grad(0, 0, 1, 0, 5.0, 1, 20, 2, 0, -1.0, 0)   # more than 16 radial functions
+
+
+def test_host_buffer_entry_points_check_arguments_before_the_device():
+    """The host-buffer entry points reject bad requests before any CUDA call (no GPU needed):
+    the CSR offsets (which the host holds), a graph over another one-particle set, the chunk size."""
+    w = W.WORKLOADS["forces_k392"]
+    d = Dag(Spec.from_workload(w))
+    n_env = 3
+    pos = np.zeros((6, 3), np.float32)
+    phi = np.zeros(n_env, np.float32)
+    F = np.zeros((6, 3), np.float32)
+    ptr = lambda a: a.ctypes.data
+
+    def call(off, lmax=w.lmax, chunk=0, n_pairs=6):
+        L.ace_energy_forces_host(d.handle, ptr(pos), 0, ptr(off), n_env, n_pairs, 0, 0, w.rc, w.nmin, w.nmax,
+                                 lmax, 0, ptr(phi), ptr(F), chunk, 0)
+
+    for bad in ([0, 4, 2, 6], [1, 2, 4, 6], [0, 2, 4, 5]):      # decreasing, not from 0, not to n_pairs
+        with pytest.raises(L.AceError) as e:
+            call(np.array(bad, np.int64))
+        assert e.value.status == -1 and "offsets" in str(e.value)
+    good = np.array([0, 2, 4, 6], np.int64)
+    with pytest.raises(L.AceError) as e:
+        call(good, lmax=w.lmax - 1)                               # K of the graph != pooling basis
+    assert e.value.status == -1 and "K" in str(e.value)
+    with pytest.raises(L.AceError) as e:
+        call(good, chunk=-1)
+    assert e.value.status == -1
+    A = np.zeros((2, d.K), np.float32)
+    with pytest.raises(L.AceError) as e:
+        L.ace_eval_grad_host(d.handle, ptr(A), 0, 0, 2, 1, L.ACE_F32, 0, 0, 0, 0, 0)   # dA NULL
+    assert e.value.status == -1
+    with pytest.raises(L.AceError) as e:
+        L.ace_eval_host(d.handle, ptr(A), 0, 2, 1, L.ACE_F32, 0, ptr(phi), -5, 0)      # chunk_env < 0
+    assert e.value.status == -1
