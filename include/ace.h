@@ -229,7 +229,10 @@ ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void*
  * waits for every chunk, so the host outputs are complete once `stream` is
  * synchronised; the call can be captured in a CUDA graph (after a first call
  * of the same chunk size, which allocates the staging slots kept in the
- * handle).  Errors: as ace_eval / ace_eval_grad; INVALID_ARG for chunk_env < 0. */
+ * handle).  The staging slots and streams belong to the handle: calls on one
+ * handle must not overlap in time (issue them on one stream, or synchronise
+ * between them).  Errors: as ace_eval / ace_eval_grad; INVALID_ARG for
+ * chunk_env < 0. */
 ace_status ace_eval_host(ace_dag* dag, const void* A, const void* c, int64_t n_env, int32_t n_out,
                          int32_t dtype, int32_t readout, void* phi, int64_t chunk_env, void* stream);
 ace_status ace_eval_grad_host(ace_dag* dag, const void* A, const void* c, const void* phi_bar,
