@@ -2,8 +2,11 @@
 Theorem 3.1 (ii) and Theorem 3.3 (host library only, no GPU)."""
 from math import comb
 
+import numpy as np
 import pytest
 
+from oracle.basis import index_set, o3_basis, torus_basis
+from oracle.dag import build_dag
 from paper_2202_04140_gb300.graph_stats import aux_ratio
 
 
@@ -59,3 +62,17 @@ def test_ratio_is_aux_over_aux_plus_basis():
     # #V = #A + |K(1..nu, D)| (section 3.1); leaves outside K are not counted.
     r = aux_ratio("torus", 4, 12, 1)
     assert r["V"] == r["aux"] + r["basis"] and r["ratio"] == pytest.approx(r["aux"] / r["V"])
+
+
+@pytest.mark.parametrize("group,p,nu,D,ob", [
+    ("torus", 1, 4, 16, lambda: torus_basis(16)),
+    ("o3", 0, 3, 4, lambda: o3_basis(1, 4, 3, 1, 1)),
+    ("o3", 1, 3, 10, lambda: o3_basis(1, 10, 9, 1, 1)),
+])
+@pytest.mark.parametrize("algo", [1, 2])
+def test_statistics_graphs_match_the_oracle_builder(group, p, nu, D, ob, algo):
+    # the sets the tables use, built by the oracle's own Algorithm 1 / 2 (section 3.2, 3.3)
+    o = index_set(ob(), nu, D, p={1: 1, 2: 2, 0: np.inf}[p])
+    od = build_dag(o, algo=algo, rule="balanced", n_split=2)
+    r = aux_ratio(group, nu, D, algo, 2, p)
+    assert r["basis"] == len(o.deg) and r["aux"] == od.n_aux

@@ -68,11 +68,11 @@ def test_spec_matches_oracle(kind, kw, ob):
     assert np.array_equal(d, o.deg.astype(np.int32))
 
 
-@pytest.mark.parametrize("kind,kw,ob", [c for c in CASES if c[1].get("p", 1) == 1])
+@pytest.mark.parametrize("kind,kw,ob", CASES)
 @pytest.mark.parametrize("algo,rule", [(1, "balanced"), (1, "peel"), (2, "balanced")])
 def test_dag_matches_oracle(kind, kw, ob, algo, rule):
     s = spec_of(kind, **kw)
-    o = index_set(ob(), kw["nu"], kw["D"])
+    o = index_set(ob(), kw["nu"], kw["D"], p={1: 1, 2: 2, 0: np.inf}[kw.get("p", 1)])
     od = build_dag(o, algo=algo, rule=rule, n_split=2)
     d = Dag(s, algo=algo, rule=rule, n_split=2)
     ex = d.export()
