@@ -283,12 +283,18 @@ def energy_and_forces_host(dag: Dag, pos: torch.Tensor, offsets: torch.Tensor, c
     n_env = offsets.numel() - 1
     n_pairs = pos.shape[0]
     pin = pos.is_pinned()
-    if phi is None:
-        phi = torch.empty((n_env,), dtype=torch.float32, pin_memory=pin)
-    if forces is None:
-        forces = torch.empty((n_pairs, 3), dtype=torch.float32, pin_memory=pin)
-    if mu is not None and (mu.device.type != "cpu" or not mu.is_contiguous() or mu.dtype != torch.float32):
-        raise ValueError("mu must be a contiguous float32 CPU tensor")
+    def host_out(t, shape, name):
+        if t is None:
+            return torch.empty(shape, dtype=torch.float32, pin_memory=pin)
+        if t.device.type != "cpu" or not t.is_contiguous() or t.dtype != torch.float32 or tuple(t.shape) != shape:
+            raise ValueError(f"{name} must be a contiguous float32 CPU tensor of shape {shape}")
+        return t
+
+    phi = host_out(phi, (n_env,), "phi")
+    forces = host_out(forces, (n_pairs, 3), "forces")
+    if mu is not None and (mu.device.type != "cpu" or not mu.is_contiguous() or mu.dtype != torch.float32
+                           or mu.numel() != n_pairs):
+        raise ValueError("mu must be a contiguous float32 CPU tensor with one value per neighbour")
     c = _dev(c, "c", torch.float32)
     c2 = c.reshape(dag.n_basis, -1)
     if c2.shape[1] != 1:
