@@ -276,13 +276,18 @@ ace_status ace_eval_plain_f64(ace_dag* dag, const double* A, const double* c, co
  * synchronise the device, is not acceptable, and hosts that only hand out
  * input and output buffers.  Its scratch is one array of 32 MiB that lives in
  * the library image on every GPU that loads libace, until the process exits.
- * Inside it go the graph (three int32 arrays of n_nodes, copied from host
- * memory on each call) and the node values (n_nodes x n_env doubles, twice that
- * when dA != NULL).  A request larger than the array fails with
- * ACE_ERR_INVALID_ARG and a message giving the bytes needed; nothing is
- * truncated or split.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture.  Every call on a device shares the array and the kernel
+ * Inside it go the graph (three int32 arrays of n_nodes, copied on each call
+ * with cudaMemcpyAsync from pageable host memory held by the handle, so the
+ * call returns once those bytes are staged) and the node values (n_nodes x
+ * n_env doubles, twice that when dA != NULL).  A request larger than the array
+ * fails with ACE_ERR_INVALID_ARG before any CUDA call, with a message giving
+ * the bytes needed and the largest n_env that fits; nothing is truncated or
+ * split.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it for the life of the process; make that
+ * first call before any stream capture.  The cached address does not survive
+ * cudaDeviceReset (or any other teardown of the device's primary context):
+ * after one, do not call this entry point again in the same process.  Every
+ * call on a device shares the array and the kernel
  * writes each scratch value before reading it, so nothing is cleared between
  * calls; calls whose work overlaps on the GPU (other streams, other threads)
  * race on the array and must be serialised by the caller.  The graph handle is

@@ -1,4 +1,5 @@
 // extern "C" entry points of libace (include/ace.h).
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -1220,7 +1221,11 @@ ace_status ace_dag_autotune(ace_dag* dag, int64_t n_env, int32_t n_out, int32_t 
 ace_status ace_eval_plain_workspace_bytes(const ace_dag* dag, int64_t n_env, int32_t with_grad, size_t* bytes) {
   if (!dag || !bytes) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
   if (n_env < 0) return fail(ACE_ERR_INVALID_ARG, "n_env must be >= 0");
-  *bytes = (size_t)dag->g.n_nodes() * (size_t)n_env * sizeof(double) * (with_grad ? 2 : 1);
+  // n_nodes x n_env x 8 (x 2) bytes, refused where size_t would wrap
+  const size_t per_env = (size_t)dag->g.n_nodes() * sizeof(double) * (with_grad ? 2 : 1);
+  if (per_env > 0 && (size_t)n_env > SIZE_MAX / per_env)
+    return fail(ACE_ERR_INVALID_ARG, "workspace size overflows size_t for n_env = " + std::to_string(n_env));
+  *bytes = per_env * (size_t)n_env;
   return ACE_OK;
 }
 
@@ -1233,7 +1238,7 @@ ace_status ace_eval_plain_f64(ace_dag* dag, const double* A, const double* c, co
   if (!c) return fail(ACE_ERR_INVALID_ARG, "c is NULL");
   if (!phi && !dA) return fail(ACE_ERR_INVALID_ARG, "nothing to compute: phi and dA are NULL");
   size_t need = 0;
-  ace_eval_plain_workspace_bytes(dag, n_env, dA != nullptr, &need);
+  if ((s = ace_eval_plain_workspace_bytes(dag, n_env, dA != nullptr, &need)) != ACE_OK) return s;
   if (!workspace || workspace_bytes < need) return fail(ACE_ERR_INVALID_ARG, "workspace missing or too small");
   cudaStream_t st = (cudaStream_t)stream;
   if ((s = ensure_uploaded(dag, st)) != ACE_OK) return s;
@@ -1254,15 +1259,16 @@ ace_status ace_eval_plain_f64_static(ace_dag* dag, const double* A, const double
   if (!phi && !dA) return fail(ACE_ERR_INVALID_ARG, "nothing to compute: phi and dA are NULL");
   const int64_t N = dag->g.n_nodes();
   const size_t graph_bytes = (size_t(3) * (size_t)N * sizeof(int32_t) + 255) & ~size_t(255);
-  const size_t value_bytes = (size_t)N * (size_t)n_env * sizeof(double) * (dA ? 2 : 1);
+  const size_t per_env = (size_t)N * sizeof(double) * (dA ? 2 : 1);
   const size_t cap = static_scratch_bytes();
-  if (graph_bytes + value_bytes > cap)
-    return fail(ACE_ERR_INVALID_ARG, "ace_eval_plain_f64_static needs " + std::to_string(graph_bytes + value_bytes) +
-                                         " bytes of scratch; the static scratch holds " + std::to_string(cap) +
-                                         " bytes (at most " +
-                                         std::to_string((cap - std::min(cap, graph_bytes)) /
-                                                        ((size_t)N * sizeof(double) * (dA ? 2 : 1))) +
-                                         " environments for this graph)");
+  // compared by division, so that no product of n_env can wrap around
+  const size_t max_env = graph_bytes >= cap ? 0 : (cap - graph_bytes) / per_env;
+  if ((uint64_t)n_env > (uint64_t)max_env)
+    return fail(ACE_ERR_INVALID_ARG,
+                "ace_eval_plain_f64_static: " + std::to_string(n_env) + " environments need " +
+                    std::to_string(graph_bytes) + " bytes of graph plus " + std::to_string(per_env) +
+                    " bytes per environment; the static scratch holds " + std::to_string(cap) + " bytes (at most " +
+                    std::to_string(max_env) + " environments for this graph)");
   void* base = nullptr;
   cudaError_t e = static_scratch_ptr(&base);
   if (e != cudaSuccess) return cuda_fail(e, "static scratch lookup");

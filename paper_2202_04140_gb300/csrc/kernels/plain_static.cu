@@ -5,7 +5,10 @@
 // holds these bytes until the process exits.  In host code the array's name
 // only denotes a host-side stand-in, never a device address, so the device
 // address is looked up with cudaGetSymbolAddress once per device (with that
-// device current) and cached; kernels receive that address as an argument.
+// device current) and cached for the life of the process; kernels receive that
+// address as an argument.  The cache assumes the device's primary context is
+// never torn down (cudaDeviceReset would leave a stale address), which the
+// entry point's documentation states.
 #include <cstdint>
 #include <mutex>
 

@@ -490,3 +490,22 @@ def test_host_buffer_entry_points_check_arguments_before_the_device():
     with pytest.raises(L.AceError) as e:
         L.ace_eval_host(d.handle, ptr(A), 0, 2, 1, L.ACE_F32, 0, ptr(phi), -5, 0)      # chunk_env < 0
     assert e.value.status == -1
+
+
+def test_plain_f64_sizes_refused_without_wrapping():
+    """Huge n_env: the workspace query and the allocation-free entry point refuse it before any CUDA
+    call, also where n_env x bytes per environment wraps around size_t to a small number."""
+    d = Dag(Spec.from_workload(W.WORKLOADS["fwd_grad_k392"]))
+    per_env = d.n_nodes * 8 * 2                                   # FP64 values and adjoints
+    wrap = (2 ** 64 + per_env - 1) // per_env                     # n_env * per_env = 2^64 + small
+    assert (wrap * per_env) % 2 ** 64 < 2 ** 25
+    buf = np.zeros(64, np.float64)
+    p = buf.ctypes.data
+    for n_env in (wrap, 2 ** 62, 2 ** 63 - 1):
+        with pytest.raises(L.AceError) as e:
+            L.ace_eval_plain_workspace_bytes(d.handle, n_env, 1)
+        assert e.value.status == -1
+        with pytest.raises(L.AceError) as e:
+            L.ace_eval_plain_f64_static(d.handle, p, p, 0, n_env, 1, p, p, 0)
+        assert e.value.status == -1 and "static scratch" in str(e.value)
+    assert L.ace_eval_plain_workspace_bytes(d.handle, 10, 1) == 10 * per_env
