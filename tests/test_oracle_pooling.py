@@ -117,3 +117,96 @@ def test_gradient_bound_dominates_gradient():
     _, g = one_particle(P, 1, 8, LMAX, 5.0, with_grad=True)
     b = one_particle_grad_bound(P, 1, 8, LMAX, 5.0)
     assert np.all(b >= np.abs(g) * (1 - 1e-12) - 1e-300)
+
+
+# ---- the force-error scale, pinned from above: equal to |grad phi_k| where one product term is left ----
+
+def _k(n, l, m, nmin=1, lmax=LMAX):
+    return (n - nmin) * (lmax + 1) ** 2 + lm_index(l, m)
+
+
+def test_gradient_bound_equals_gradient_where_one_term_is_left():
+    """grad(R_n Y_lm) is a sum of product terms; where all but one vanish, the bound must equal |grad|.
+
+    (a) l = 0 (Y constant) at a zero of T_n: only dT_n/dr (1 - r/rc)^2 Y rhat is left;
+    (b) l = 0 at an interior extremum of T_n: only T_n d(1 - r/rc)^2/dr Y rhat;
+    (c) z-component in the plane z = 0 (rhat_z = 0, and the r^-m factor has no z-derivative there);
+    (d) sine parts (m < 0) on the x-axis, y-component; (e) cosine parts (m > 0) on the y-axis, x-component.
+    """
+    from oracle.pooling import one_particle_grad_bound
+    rc, nmax = 5.0, 8
+    d = unit(3, 11)
+    for n in range(1, nmax + 1):
+        xs = [np.cos((2 * k - 1) * pi / (2 * n)) for k in range(1, n + 1)]          # T_n = 0
+        xs += [np.cos(k * pi / n) for k in range(1, n)]                            # T_n' = 0
+        for x in xs:
+            P = d * (rc * (x + 1) / 2)
+            _, g = one_particle(P, 1, nmax, LMAX, rc, with_grad=True)
+            b = one_particle_grad_bound(P, 1, nmax, LMAX, rc)
+            k = _k(n, 0, 0)
+            assert np.allclose(b[:, k], np.abs(g[:, k]), rtol=1e-12, atol=1e-15), (n, x)
+    rng = np.random.default_rng(12)
+    r = rng.uniform(0.3, 4.7, 6)
+    phi = rng.uniform(0, 2 * pi, 6)
+    planes = {"z": (np.stack([np.cos(phi), np.sin(phi), 0 * phi], 1) * r[:, None], 2, None),
+              "x-axis": (np.stack([r, 0 * r, 0 * r], 1), 1, -1),
+              "y-axis": (np.stack([0 * r, r, 0 * r], 1), 0, +1)}
+    for name, (P, comp, sign) in planes.items():
+        _, g = one_particle(P, 1, nmax, LMAX, rc, with_grad=True)
+        b = one_particle_grad_bound(P, 1, nmax, LMAX, rc)
+        ks = [_k(n, l, m) for n in range(1, nmax + 1) for l in range(LMAX + 1) for m in range(-l, l + 1)
+              if sign is None or (m != 0 and np.sign(m) == sign)]
+        gk, bk = np.abs(g[:, ks, comp]), b[:, ks, comp]
+        assert np.allclose(bk, gk, rtol=1e-12, atol=1e-13), name
+        assert np.mean(gk > 1e-6) > 0.2, name    # a fair share of the compared values is not zero
+
+
+def test_harmonic_gradient_bound_r_power_term():
+    """l = m: d^m P_m/du^m is constant, so the z-derivative of Y_mm has the r^-m term only."""
+    P = unit(20, 13) * 1.7
+    _, dY = real_sph_harm(P, LMAX, with_grad=True)
+    _, dYb = real_sph_harm(P, LMAX, with_grad=True, bound=True)
+    for m in range(1, LMAX + 1):
+        for mm in (m, -m):
+            i = lm_index(m, mm)
+            assert np.allclose(dYb[:, i, 2], np.abs(dY[:, i, 2]), rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("(np.abs(dT * (2.0 / rc) * env) + np.abs(T * denv))", "(np.abs(dT * (4.0 / rc) * env) + np.abs(T * denv))"),
+    ("(np.abs(dT * (2.0 / rc) * env) + np.abs(T * denv))", "(np.abs(dT * (2.0 / rc) * env) + 2 * np.abs(T * denv))"),
+    ("+ np.abs(Q[:, None] * dg * h[:, None])", "+ 2 * np.abs(Q[:, None] * dg * h[:, None])"),
+    ("+ np.abs((Q * g)[:, None] * grad_h))", "+ 2 * np.abs((Q * g)[:, None] * grad_h))"),
+    ("fac * (np.abs(dQ[:, None]", "2 * fac * (np.abs(dQ[:, None]"),
+    ("+ np.abs(R)[:, :, None, None] * dYb", "+ 2 * np.abs(R)[:, :, None, None] * dYb"),
+])
+def test_gradient_bound_pins_catch_planted_factors(old, new):
+    """A stray factor in any term of the bound (plausible slips) fails one of the equalities above."""
+    import inspect
+    import sys
+    import oracle.pooling as Pm
+    src = inspect.getsource(Pm)
+    assert src.count(old) == 1, old
+    mod = type(Pm)("mutant_pooling")
+    sys.modules["mutant_pooling"] = mod
+    try:
+        exec(compile(src.replace(old, new), "mutant_pooling", "exec"), mod.__dict__)
+    finally:
+        del sys.modules["mutant_pooling"]
+    saved = {k: globals()[k] for k in ("one_particle", "real_sph_harm")}
+    import oracle.pooling
+    orig_bound = oracle.pooling.one_particle_grad_bound
+    globals()["real_sph_harm"] = mod.real_sph_harm
+    oracle.pooling.one_particle_grad_bound = mod.one_particle_grad_bound
+    try:
+        failed = 0
+        for t in (test_gradient_bound_equals_gradient_where_one_term_is_left,
+                  test_harmonic_gradient_bound_r_power_term):
+            try:
+                t()
+            except AssertionError:
+                failed += 1
+        assert failed > 0, new
+    finally:
+        oracle.pooling.one_particle_grad_bound = orig_bound
+        globals().update(saved)
