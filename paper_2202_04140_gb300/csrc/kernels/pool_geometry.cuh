@@ -40,7 +40,12 @@ ACE_HD float div(float a, float b) { return __fdiv_rn(a, b); }
 ACE_HD float add(float a, float b) { return a + b; }
 ACE_HD float mul(float a, float b) { return a * b; }
 ACE_HD float fma(float a, float b, float c) { return __builtin_fmaf(a, b, c); }
+#ifdef ACE_GEO_HOST_RSQRT
+// an accuracy check may stand in an approximate seed, as the device's rsqrtf is one
+ACE_HD float rsqrt(float a) { return ACE_GEO_HOST_RSQRT(a); }
+#else
 ACE_HD float rsqrt(float a) { return 1.0f / __builtin_sqrtf(a); }
+#endif
 ACE_HD float div(float a, float b) { return a / b; }
 #endif
 

@@ -141,3 +141,39 @@ def test_forces_full_size_sampled(dev):
         Gabs = grad_naive(Aabs, o, np.abs(c))
         Fref = forces(Pe, oe, G, w.nmin, w.nmax, w.lmax, w.rc)
         assert normalized_error(F[a:b], Fref, force_scale(Pe, oe, Gabs, w)) < TOL32
+
+
+def test_pool_and_adjoint_next_to_centre_and_cutoff(dev):
+    """Neighbours at r ~ 1e-6 and at r ~ rc (1 - 1e-6), also on the coordinate axes: the FP32
+    geometry (error-free r^2, Newton-refined 1/r, 1 - r/rc from rc^2 - r^2) keeps A and the
+    adjoint within the gate even where R_n(r) ~ (1 - r/rc)^2 ~ 1e-12."""
+    from paper_2202_04140_gb300.torch_api import pool_A as gpu_pool, pool_A_grad
+    w = W.WORKLOADS["forces_k392"]
+    rc = w.rc
+    rng = np.random.default_rng(31)
+
+    def cloud(n, radii, axes=False):
+        d = rng.standard_normal((n, 3))
+        if axes:                                    # +-x, +-y or +-z, per point
+            d = np.zeros((n, 3))
+            d[np.arange(n), rng.integers(0, 3, n)] = rng.choice([-1.0, 1.0], n)
+        d /= np.linalg.norm(d, axis=1)[:, None]
+        return d * radii[:, None]
+
+    clouds = [cloud(20, 1e-6 * rng.uniform(1, 10, 20)),                       # next to the centre
+              cloud(20, rc * (1 - 1e-6 * rng.uniform(1, 10, 20))),            # next to the cutoff
+              cloud(12, np.concatenate([1e-6 * rng.uniform(1, 10, 6), rc * (1 - 1e-6 * rng.uniform(1, 10, 6))]),
+                    axes=True),
+              np.concatenate([cloud(10, rc * (1 - 1e-6 * rng.uniform(1, 10, 10))),
+                              cloud(10, rc * rng.uniform(0, 1, 10) ** (1 / 3))])]
+    P = W.round_to(np.concatenate(clouds), "f32")
+    assert np.all(np.linalg.norm(P, axis=1) < rc) and np.all(np.linalg.norm(P, axis=1) > 0)
+    offsets = np.concatenate([[0], np.cumsum([len(c) for c in clouds])]).astype(np.int64)
+    Pt, ot = torch.tensor(P, dtype=torch.float32, device=dev), torch.tensor(offsets, device=dev)
+    A = gpu_pool(Pt, ot, w.nmin, w.nmax, w.lmax, rc).cpu().numpy()
+    ref = pool_A(P, offsets, w.nmin, w.nmax, w.lmax, rc)
+    assert normalized_error(A, ref, abs_pool(P, offsets, w)) < TOL32
+    G = rng.standard_normal(ref.shape)
+    dpos = pool_A_grad(Pt, ot, torch.tensor(G, dtype=torch.float32, device=dev), w.nmin, w.nmax, w.lmax, rc)
+    Fref = -forces(P, offsets, G, w.nmin, w.nmax, w.lmax, rc)
+    assert normalized_error(dpos.cpu().numpy(), Fref, force_scale(P, offsets, G, w)) < TOL32
