@@ -176,3 +176,67 @@ def workload_index_set(w) -> IndexSet:
     """Index set of a ``workloads.Workload`` (O(3), p = 1, degree wn*n + wl*l [+ wk*k])."""
     b = o3_basis(w.nmin, w.nmax, w.lmax, w.wn, w.wl, w.kmax, w.wk)
     return index_set(b, w.nu_max, w.deg_max)
+
+
+def index_set_by_first(basis: OneParticleBasis, nu_max: int, deg_max: int,
+                       require_l_even: bool | None = None) -> IndexSet:
+    """The same set as ``index_set`` with p = 1, enumerated one block at a time (section 2.5, Eq. 3).
+
+    For large sets (millions of tuples) ``index_set`` holds every degree-bounded
+    tuple of an order at once.  Here, for each order nu and each first element
+    k_1 in increasing id order, the non-decreasing tuples starting with k_1 are
+    grown one element at a time: a row with last element a and degree sum d
+    extends by every id j >= a with d + deg(j) <= deg_max (rows that share (a, d)
+    share that candidate list).  The completed rows are filtered by the same
+    invariance rule as ``index_set`` and sorted lexicographically; since every
+    tuple of the block starts with k_1, the blocks in k_1 order give the
+    canonical (nu, lexicographic) order.
+    """
+    if require_l_even is None:
+        require_l_even = basis.group == "O3"
+    deg = basis.deg.astype(np.int64)
+    K = deg.shape[0]
+    blocks, nus = [], []
+    for nu in range(1, nu_max + 1):
+        for k1 in range(K):
+            if deg[k1] > deg_max:
+                continue
+            T = np.array([[k1]], dtype=np.int64)
+            acc = deg[[k1]]
+            for _ in range(1, nu):
+                key = T[:, -1] * (deg_max + 1) + acc
+                order = np.argsort(key, kind="stable")
+                T, acc, key = T[order], acc[order], key[order]
+                starts = np.flatnonzero(np.r_[True, key[1:] != key[:-1]])
+                ends = np.r_[starts[1:], key.shape[0]]
+                new_T, new_acc = [], []
+                for s, e in zip(starts, ends):
+                    a, d = int(T[s, -1]), int(acc[s])
+                    cand = np.arange(a, K, dtype=np.int64)
+                    cand = cand[deg[cand] + d <= deg_max]
+                    if cand.size == 0:
+                        continue
+                    rows = np.repeat(T[s:e], cand.size, axis=0)
+                    new_T.append(np.concatenate([rows, np.tile(cand, e - s)[:, None]], axis=1))
+                    new_acc.append(np.repeat(acc[s:e], cand.size) + np.tile(deg[cand], e - s))
+                if not new_T:
+                    T = np.zeros((0, T.shape[1] + 1), np.int64)
+                    break
+                T, acc = np.concatenate(new_T), np.concatenate(new_acc)
+            if T.shape[0] == 0:
+                continue
+            ok = basis.m[T].sum(axis=1) == 0
+            if require_l_even:
+                ok &= (basis.l[T].sum(axis=1) % 2) == 0
+            T = T[ok]
+            if T.shape[0] == 0:
+                continue
+            T = T[np.lexsort(T.T[::-1])]
+            pad = np.full((T.shape[0], nu_max), -1, dtype=np.int64)
+            pad[:, :nu] = T
+            blocks.append(pad)
+            nus.append(np.full(T.shape[0], nu, dtype=np.int64))
+    tuples = np.concatenate(blocks, axis=0) if blocks else np.zeros((0, nu_max), np.int64)
+    nu_arr = np.concatenate(nus) if nus else np.zeros(0, np.int64)
+    d = np.where(tuples >= 0, basis.deg[np.maximum(tuples, 0)], 0).sum(axis=1)
+    return IndexSet(basis, nu_max, deg_max, tuples, nu_arr, d.astype(np.int64))

@@ -89,3 +89,19 @@ def test_one_particle_ids():
     for k, (n, l, m) in enumerate(b.labels):
         assert k == (n - 1) * 16 + l * l + l + m
         assert b.deg[k] == n + 2 * l
+
+
+@pytest.mark.parametrize("make,nu,D", [
+    (lambda: o3_basis(1, 4, 3, 1, 2), 3, 10),
+    (lambda: o3_basis(1, 8, 6, 1, 2), 4, 16),
+    (lambda: o3_basis(1, 3, 2, 1, 1, 2, 1), 4, 7),
+    (lambda: o3_basis(1, 6, 5, 1, 1), 5, 12),
+    (lambda: so2_basis(1, 3, 4), 4, 8),
+    (lambda: torus_basis(10), 5, 10),
+])
+def test_blockwise_enumeration_equals_index_set(make, nu, D):
+    """index_set_by_first (one block per first element, for the multi-million sets) is index_set, p = 1."""
+    from oracle.basis import index_set_by_first
+    b = make()
+    a, c = index_set(b, nu, D), index_set_by_first(b, nu, D)
+    assert np.array_equal(a.tuples, c.tuples) and np.array_equal(a.nu, c.nu) and np.array_equal(a.deg, c.deg)
