@@ -7,7 +7,7 @@ the Algorithm 1 graph counts, and SHA-256 digests of the canonical arrays:
                int32 basis_node (n_basis)
 The C++ builder is compared with these digests bit for bit.
 
-Run:  python tests/golden/make_golden.py
+Run:  python tests/golden/make_golden.py   (about 10 minutes; the largest set needs ~15 GB)
 """
 import hashlib
 import json
@@ -44,13 +44,14 @@ def dag_digest(d) -> str:
 def main():
     out = {}
     for name in ["plain_fp64_k64", "fwd_grad_k392", "uneven_16ch_k392", "stress_k810", "species_forces_k375",
-                 "paper_degree_d20_k810"]:
+                 "paper_degree_d20_k810", "paper_degree_k810"]:
         w = W.WORKLOADS[name]
         t0 = time.time()
         s = workload_index_set(w)
         rec = {"K": s.basis.K, "n_basis": s.n_basis, "counts_per_nu": s.counts_per_nu(),
                "spec_sha256": spec_digest(s), "rules": {}}
-        # the 1.5-million-function set: the balanced rule only (the oracle's graph build is slow)
+        # the 1.5- and 17.3-million-function sets: the balanced rule only (the oracle's graph build is
+        # slow: about 5 minutes and 15 GB for the 17.3 million set)
         for rule in (["balanced"] if name.startswith("paper_degree") else ["balanced", "peel"]):
             d = build_dag(s, rule=rule)
             rec["rules"][rule] = {

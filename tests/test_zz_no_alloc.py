@@ -32,10 +32,12 @@ def test_static_scratch_matches_allocating_entry_point_and_oracle():
     stream = torch.cuda.current_stream().cuda_stream
     # two different graphs: the K = 392 graph by Algorithm 1, then the K = 64 graph by Algorithm 2
     cases = [("fwd_grad_k392", 1, 96, 2, 21), ("plain_fp64_k64", 2, 40, 3, 22)]
+    dags = []
     for call, (name, algo, n_env, n_out, seed) in enumerate(cases):
         w = W.WORKLOADS[name]
         o = workload_index_set(w)
         dag = Dag(Spec.from_workload(w), algo=algo)
+        dags.append(dag)
         A = W.draw_A(n_env, dag.K, seed=seed)
         c = W.draw_c(o.deg, n_out, seed=seed + 100)
         pb = np.random.default_rng(seed + 200).standard_normal((n_env, n_out))
@@ -54,10 +56,13 @@ def test_static_scratch_matches_allocating_entry_point_and_oracle():
         assert normalized_error(dA_h, ref_dA.cpu().numpy(), s_dA) < TOL64, call
         assert normalized_error(phi_h, phi_naive(A, o, c), s_phi) < TOL64, call
         assert normalized_error(dA_h, grad_naive(A, o, c, pb), s_dA) < TOL64, call
-    # a request beyond the fixed scratch is refused with a clear error, nothing is computed
+    # a request beyond the fixed scratch is refused with a clear error, nothing is computed:
+    # 4096 environments of the K = 392 graph need 3,729 nodes x 4096 x 16 bytes > 32 MiB
+    dag = dags[0]
     big = torch.zeros((4096, dag.K), dtype=torch.float64, device=dev)
     out = torch.zeros((4096, 1), dtype=torch.float64, device=dev)
+    c1 = torch.zeros((dag.n_basis, 1), dtype=torch.float64, device=dev)
     with pytest.raises(L.AceError) as err:
-        L.ace_eval_plain_f64_static(dag.handle, big.data_ptr(), ct[:, :1].contiguous().data_ptr(), 0, 4096, 1,
+        L.ace_eval_plain_f64_static(dag.handle, big.data_ptr(), c1.data_ptr(), 0, 4096, 1,
                                     out.data_ptr(), big.data_ptr(), stream)
     assert err.value.status == -1 and "static scratch" in str(err.value)
