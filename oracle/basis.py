@@ -173,9 +173,11 @@ def index_set(basis: OneParticleBasis, nu_max: int, deg_max: int, p: float = 1,
 
 
 def workload_index_set(w) -> IndexSet:
-    """Index set of a ``workloads.Workload`` (O(3), p = 1, degree wn*n + wl*l [+ wk*k])."""
+    """Index set of a ``workloads.Workload`` (O(3), p = 1, degree wn*n + wl*l [+ wk*k]).
+
+    Enumerated block by block (``index_set_by_first``, the same set as ``index_set``)."""
     b = o3_basis(w.nmin, w.nmax, w.lmax, w.wn, w.wl, w.kmax, w.wk)
-    return index_set(b, w.nu_max, w.deg_max)
+    return index_set_by_first(b, w.nu_max, w.deg_max)
 
 
 def index_set_by_first(basis: OneParticleBasis, nu_max: int, deg_max: int,

@@ -112,7 +112,8 @@ struct LoeArgs {
 // AA [n_slots][E] (slot-major: the E values of one slot are one vector load),
 // G [E][gs] (adjoint only, environment-major: the bank of an accumulator is
 // its slot mod 32, gs = n_g rounded up to 32), phibar [E][NOUT], phi partials
-// [warps][E][NOUT] in FP64, and, when staging is on, the bulk-copy buffer of
+// [warps][E][NOUT] (8 bytes each: the readout's accumulator, an FP32 (s, c) pair for the
+// compensated readout, FP64 for the FP64 one), and, when staging is on, the bulk-copy buffer of
 // the next tile's rows of A (E K values + 16 bytes) and its mbarrier.
 struct SmemLayout {
   size_t g, pb, red, stage, mbar, total;
@@ -282,7 +283,7 @@ struct Acc<float, kReadPlain> {
   float s = 0.f;
   __device__ __forceinline__ void add(float x) { s += x; }
   __device__ __forceinline__ void add_acc(const Acc& o) { s += o.s; }
-  __device__ __forceinline__ double value() const { return (double)s; }
+  __device__ __forceinline__ float value() const { return s; }
   __device__ __forceinline__ void shfl_down_add(int d) { s += __shfl_down_sync(0xffffffffu, s, d); }
 };
 
@@ -304,7 +305,7 @@ struct Acc<float, kReadComp> {
     add(o.s);
     add(-o.c);
   }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  __device__ __forceinline__ float value() const { return s - c; }  // one rounding of s + (-c)
   __device__ __forceinline__ void shfl_down_add(int d) {
     Acc o;
     o.s = __shfl_down_sync(0xffffffffu, s, d);
@@ -688,7 +689,9 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
   T* AA = reinterpret_cast<T*>(smem_raw);
   T* G = reinterpret_cast<T*>(smem_raw + L.g);
   T* pb = reinterpret_cast<T*>(smem_raw + L.pb);
-  double* red = reinterpret_cast<double*>(smem_raw + L.red);
+  // per-warp phi partials: the readout's own accumulator (FP32 sums stay FP32 across warps)
+  static_assert(sizeof(Acc<T, RO>) <= sizeof(double), "phi partial slot");
+  Acc<T, RO>* red = reinterpret_cast<Acc<T, RO>*>(smem_raw + L.red);
   T* sbuf = reinterpret_cast<T*>(smem_raw + L.stage);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L.mbar);
   const int tid = threadIdx.x;
@@ -810,7 +813,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
         for (int c = 0; c < NB; ++c) {
 #pragma unroll
           for (int d = 16; d >= 1; d >>= 1) phiacc[e][c].shfl_down_add(d);
-          if (lane == 0) red[(warp * E + e) * NOUT + c0 + c] = phiacc[e][c].value();
+          if (lane == 0) red[(warp * E + e) * NOUT + c0 + c] = phiacc[e][c];
         }
     }
     __syncthreads();
@@ -863,14 +866,15 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
         if (env < a.n_env) a.dA[env * K + k] = G[(size_t)e * a.gs + k];
       }
     }
-    // 5. phi: the per-warp partials (already in shared memory) summed in fixed warp order
+    // 5. phi: the per-warp partials (already in shared memory) combined in fixed warp order by the
+    //    readout's own accumulator (plain FP32, Kahan FP32, or FP64), rounded once to T
     if (a.phi) {
       for (int i = tid; i < E * NOUT; i += NT) {
         const int e = i / NOUT, c = i - e * NOUT;
-        double s = 0.0;
-        for (int w = 0; w < NW; ++w) s += red[(w * E + e) * NOUT + c];
+        Acc<T, RO> s;
+        for (int w = 0; w < NW; ++w) s.add_acc(red[(w * E + e) * NOUT + c]);
         const int64_t env = env0 + e;
-        if (env < a.n_env && c < a.n_out) a.phi[env * a.n_out + c] = (T)s;
+        if (env < a.n_env && c < a.n_out) a.phi[env * a.n_out + c] = (T)s.value();
       }
     }
     __syncthreads();

@@ -155,7 +155,9 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
     G = reinterpret_cast<float*>(smem_raw + align16((size_t)a.n_slots * S * 4));
     pb = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(G) + (GRAD ? align16((size_t)a.n_g * S * 4) : 0));
   }
-  double* red = reinterpret_cast<double*>(pb + 32);
+  // per-lane phi partials of every warp: the readout's own accumulator (8 bytes reserved per slot)
+  static_assert(sizeof(Acc<float, RO>) <= sizeof(double), "phi partial slot");
+  Acc<float, RO>* red = reinterpret_cast<Acc<float, RO>*>(pb + 32);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int K = a.K;
   for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
@@ -236,13 +238,14 @@ __global__ void __launch_bounds__(NT) loe_kernel(const LoeArgs a) {
         for (int k = lane; k < K; k += 32) row[k] = G[k * S + e];
       }
     }
-    // 5. phi: per-lane partials of every warp, summed in FP64 in warp order
-    red[warp * 32 + lane] = phiacc.value();
+    // 5. phi: per-lane partials of every warp, combined in warp order by the readout's accumulator
+    //    (plain FP32, Kahan FP32, or FP64 for the FP64 readout) and rounded once
+    red[warp * 32 + lane] = phiacc;
     __syncthreads();
     if (tid < 32 && tid < n_here && a.phi) {
-      double s = 0.0;
-      for (int w = 0; w < NW; ++w) s += red[w * 32 + tid];
-      a.phi[env0 + tid] = (float)s;
+      Acc<float, RO> s;
+      for (int w = 0; w < NW; ++w) s.add_acc(red[w * 32 + tid]);
+      a.phi[env0 + tid] = (float)s.value();
     }
     __syncthreads();
   }
