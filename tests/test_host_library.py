@@ -84,7 +84,9 @@ def test_dag_matches_oracle(kind, kw, ob, algo, rule):
     assert np.array_equal(ex["level"], od.order.astype(np.int32))
 
 
-@pytest.mark.parametrize("name", sorted(GOLDEN))
+# the 17.3-million-function set takes about two minutes to build; its digests are checked by
+# tests/test_gpu_paper_degree.py before the evaluation there
+@pytest.mark.parametrize("name", sorted(n for n in GOLDEN if n != "paper_degree_k810"))
 def test_workload_digests(name):
     """Bit-exact against the oracle's digests (written by tests/golden/make_golden.py)."""
     g = GOLDEN[name]

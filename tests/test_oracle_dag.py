@@ -26,8 +26,9 @@ def check_structure(dag, index):
         assert 0 <= l < i and 0 <= r < i
         assert tuple(sorted(dag.tuples[l] + dag.tuples[r])) == t        # mset union, Eq. 4
         assert dag.is_aux[i] == (t not in basis)
+    basis_tuples = index.as_tuples()
     for b, node in enumerate(dag.basis_node):
-        assert dag.tuples[node] == index.as_tuples()[b]
+        assert dag.tuples[node] == basis_tuples[b]
 
 
 def test_worked_examples_section_2_6():
