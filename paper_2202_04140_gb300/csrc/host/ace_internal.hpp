@@ -68,6 +68,16 @@ struct Task {
 
 // Warps per CTA of the one-environment-per-lane kernel (1024 threads).
 constexpr int kLoeWarps = 32;
+// Blocks of that kernel's streams: rows with equal column sets of at most kLoeBlockCols
+// columns, kLoeBlockMinRows or more of them, in units of at most kLoeBlockRows rows.
+constexpr int kLoeBlockCols = 8;
+constexpr int kLoeBlockMinRows = 2;
+constexpr int kLoeBlockRows = 16;
+// Flag bits beyond those of Task::flags: a row-major task that is a block row (its
+// coefficients follow its header four per item, in the block's column order), and a
+// stream item that is a block header.
+constexpr int kTaskBlockRow = 8;
+constexpr int kLoeBlockUnit = 16;
 
 struct TaskSet {
   // Tasks grouped in slices of 32 (one per lane); entries of a slice are
@@ -97,11 +107,15 @@ struct TaskSet {
   std::vector<int32_t> rm_col, rm_ebasis;
   std::vector<uint8_t> rm_ew2;
   // Their layout as one stream per warp of that kernel (kLoeWarps warps per CTA;
-  // warp w takes tasks w, w + kLoeWarps, ...): each task is a 16-byte header
-  // followed by its entry pairs (16 bytes each), contiguous.  Positions count
-  // 16-byte items.
+  // units spread over the warps longest first): a unit is either a task (a 16-byte
+  // header followed by its entry pairs, 16 bytes each) or a block (a header
+  // {m, rows << 8 | kLoeBlockUnit, 0, 0}, kLoeBlockCols / 4 items of columns, then
+  // per row its header and kLoeBlockCols / 4 items of coefficients).  The rm tasks
+  // are in stream order.  Positions count 16-byte items.
   std::vector<int32_t> loe_wbeg;      // [kLoeWarps + 1] first item of each warp's stream
-  std::vector<int32_t> loe_hpos;      // [n_rm] item of each task's header (its pairs follow)
+  std::vector<int32_t> loe_hpos;      // [n_rm] item of each task's (or block row's) header
+  std::vector<int32_t> loe_spos;      // items written once, not by the binding: block headers, columns
+  std::vector<int32_t> loe_sval;      // [4 per loe_spos] their values
   int32_t n_slices() const { return (int32_t)slice_steps.size(); }
 };
 

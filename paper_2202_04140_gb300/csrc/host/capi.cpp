@@ -18,6 +18,9 @@ namespace ace {
 namespace {
 thread_local std::string g_last_error;
 }
+static_assert(dev::kLoeBlockCols == kLoeBlockCols && dev::kLoeBlockFlag == kLoeBlockUnit &&
+                  dev::kLoeStreamWarps == kLoeWarps,
+              "stream layout of the plan and of the one-environment-per-lane kernel");
 
 ace_status fail(ace_status st, const std::string& msg) {
   g_last_error = msg;
@@ -79,6 +82,9 @@ struct DevTaskSet {
   int32_t n_rm = 0;
   int64_t n_rm_ent = 0;
   int32_t* loe_hpos = nullptr;  // item of each task's header in the per-warp streams
+  int32_t* loe_spos = nullptr;  // items written once (block headers and columns) and their values
+  int4* loe_sval = nullptr;
+  int32_t n_loe_static = 0;
   int32_t loe_wbeg[kLoeWarps + 1] = {};
   int64_t n_loe_items = 0;
   int4* loe_stream = nullptr;   // bound streams: headers and {column, coefficient} pairs (FP32, one channel)
@@ -169,10 +175,31 @@ int reduction_rounds(const std::vector<Task>& tasks, size_t sl) {
   return rounds;
 }
 
+// Per-lane structure of the segmented warp sum over equal "A" targets, as flag bits of the
+// device task: bit 8 + r is set when lane + 2^r (r < 5) holds the same target (the sum at
+// distance 2^r stays inside the run), bit 13 marks the first lane of a run (it does the update).
+int32_t segment_bits(const std::vector<Task>& tasks, size_t sl, int j) {
+  auto key = [&](int l) {
+    const Task& t = tasks[sl * 32 + l];
+    return t.row < 0 ? -1 - l : ((t.flags & 2) ? t.pl : t.row);
+  };
+  int32_t bits = 0;
+  for (int r = 0; r < 5; ++r)
+    if (j + (1 << r) < 32 && key(j + (1 << r)) == key(j)) bits |= 1 << (8 + r);
+  if (j == 0 || key(j - 1) != key(j)) bits |= 1 << 13;
+  return bits;
+}
+
+std::vector<int4> device_tasks(const std::vector<Task>& tasks) {
+  std::vector<int4> t4(tasks.size());
+  for (size_t i = 0; i < tasks.size(); ++i)
+    t4[i] = make_int4(tasks[i].row, tasks[i].flags | segment_bits(tasks, i / 32, (int)(i % 32)), tasks[i].pl,
+                      tasks[i].pr);
+  return t4;
+}
+
 ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStream_t st) {
-  std::vector<int4> t4(ts.tasks.size());
-  for (size_t i = 0; i < ts.tasks.size(); ++i)
-    t4[i] = make_int4(ts.tasks[i].row, ts.tasks[i].flags, ts.tasks[i].pl, ts.tasks[i].pr);
+  std::vector<int4> t4 = device_tasks(ts.tasks);
   d->staging_int4.push_back(std::move(t4));
   ace_status s;
   if ((s = upload_vec(d, d->staging_int4.back(), &dt.tasks, st)) != ACE_OK) return s;
@@ -232,9 +259,7 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   dt.n_cold_slices = ts.n_cold_slices();
   dt.n_cold_pad = (int64_t)ts.cold_ca.size();
   if (dt.n_cold_slices > 0) {
-    std::vector<int4> c4(ts.cold_tasks.size());
-    for (size_t i = 0; i < ts.cold_tasks.size(); ++i)
-      c4[i] = make_int4(ts.cold_tasks[i].row, ts.cold_tasks[i].flags, ts.cold_tasks[i].pl, ts.cold_tasks[i].pr);
+    std::vector<int4> c4 = device_tasks(ts.cold_tasks);
     std::vector<int32_t> hdr(ts.cold_slice_steps.size());
     for (size_t sl = 0; sl < hdr.size(); ++sl)
       hdr[sl] = ts.cold_slice_steps[sl] | (reduction_rounds(ts.cold_tasks, sl) << 16);
@@ -267,6 +292,15 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   dt.n_rm = (int32_t)ts.rm_tasks.size();
   dt.n_rm_ent = (int64_t)ts.rm_col.size();
   if ((s = upload_vec(d, ts.loe_hpos, &dt.loe_hpos, st)) != ACE_OK) return s;
+  if ((s = upload_vec(d, ts.loe_spos, &dt.loe_spos, st)) != ACE_OK) return s;
+  {
+    std::vector<int4> sv(ts.loe_spos.size());
+    for (size_t i = 0; i < sv.size(); ++i)
+      sv[i] = make_int4(ts.loe_sval[4 * i], ts.loe_sval[4 * i + 1], ts.loe_sval[4 * i + 2], ts.loe_sval[4 * i + 3]);
+    d->staging_int4.push_back(std::move(sv));
+    if ((s = upload_vec(d, d->staging_int4.back(), &dt.loe_sval, st)) != ACE_OK) return s;
+    dt.n_loe_static = (int32_t)ts.loe_spos.size();
+  }
   for (int w = 0; w <= kLoeWarps; ++w) dt.loe_wbeg[w] = ts.loe_wbeg[w];
   dt.n_loe_items = ts.loe_wbeg[kLoeWarps];
   return ACE_OK;
@@ -335,18 +369,45 @@ ace_status validate_plan(const Plan& p) {
       if (ts == &p.sym && !(t.flags & 2) && !in(t.row, p.n_g))
         return fail(ACE_ERR_BOUNDS, "plan: row-major adjoint row out of range");
     }
-    // per-warp streams: every task's header and pairs inside its warp's stream, no overlap
+    // per-warp streams, decoded as the kernel walks them: every unit (a task, or a block header,
+    // its columns and rows) inside its warp's stream, every rm task exactly once, in order
     if (ts->loe_wbeg.size() != (size_t)kLoeWarps + 1 || ts->loe_hpos.size() != ts->rm_tasks.size() ||
-        ts->loe_wbeg[0] != 0)
+        ts->loe_wbeg[0] != 0 || ts->loe_sval.size() != 4 * ts->loe_spos.size())
       return fail(ACE_ERR_BOUNDS, "plan: per-warp stream sizes");
+    size_t t = 0, si = 0;
     for (int w = 0; w < kLoeWarps; ++w) {
       int32_t pos = ts->loe_wbeg[w];
-      for (size_t t = (size_t)w; t < ts->rm_tasks.size(); t += kLoeWarps) {
-        if (ts->loe_hpos[t] != pos) return fail(ACE_ERR_BOUNDS, "plan: per-warp stream header position");
-        pos += 1 + (ts->rm_off[t + 1] - ts->rm_off[t]) / 2;
+      while (pos < ts->loe_wbeg[w + 1]) {
+        if (si < ts->loe_spos.size() && ts->loe_spos[si] == pos) {  // a block
+          const int32_t* h = &ts->loe_sval[4 * si];
+          const int32_t m = h[0], nrows = h[1] >> 8;
+          if ((h[1] & 0xff) != kLoeBlockUnit || m < 1 || m > kLoeBlockCols || nrows < 1)
+            return fail(ACE_ERR_BOUNDS, "plan: block header");
+          ++si;
+          ++pos;
+          for (int k = 0; k < kLoeBlockCols / 4; ++k, ++si, ++pos) {
+            if (si >= ts->loe_spos.size() || ts->loe_spos[si] != pos)
+              return fail(ACE_ERR_BOUNDS, "plan: block columns");
+            for (int c = 0; c < 4; ++c)
+              if (!in(ts->loe_sval[4 * si + c], p.n_slots)) return fail(ACE_ERR_BOUNDS, "plan: block column");
+          }
+          for (int32_t r = 0; r < nrows; ++r, ++t) {
+            if (t >= ts->rm_tasks.size() || ts->loe_hpos[t] != pos || !(ts->rm_tasks[t].flags & kTaskBlockRow) ||
+                ts->rm_off[t + 1] - ts->rm_off[t] != kLoeBlockCols)
+              return fail(ACE_ERR_BOUNDS, "plan: block row");
+            pos += 1 + kLoeBlockCols / 4;
+          }
+        } else {                                                    // a task
+          if (t >= ts->rm_tasks.size() || ts->loe_hpos[t] != pos || (ts->rm_tasks[t].flags & kTaskBlockRow))
+            return fail(ACE_ERR_BOUNDS, "plan: per-warp stream header position");
+          pos += 1 + (ts->rm_off[t + 1] - ts->rm_off[t]) / 2;
+          ++t;
+        }
       }
       if (pos != ts->loe_wbeg[w + 1]) return fail(ACE_ERR_BOUNDS, "plan: per-warp stream extent");
     }
+    if (t != ts->rm_tasks.size() || si != ts->loe_spos.size())
+      return fail(ACE_ERR_BOUNDS, "plan: per-warp streams do not cover the tasks");
   }
   return ACE_OK;
 }
@@ -471,6 +532,9 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
       if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
       dt.loe_stream = static_cast<int4*>(p);
       if ((e = cudaMemsetAsync(p, 0, bytes, st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+      // block headers and columns: part of the plan, written once
+      if ((e = launch_loe_static(dt.loe_spos, dt.loe_sval, dt.n_loe_static, dt.loe_stream, st)) != cudaSuccess)
+        return cuda_fail(e, "stream layout launch");
     }
     e = launch_bind_loe(static_cast<const float*>(c), dt.rm_tasks, dt.rm_off, dt.rm_col, dt.rm_ebasis, dt.rm_ew2,
                         d->slot_basis, dt.loe_hpos, dt.n_rm, dt.loe_stream, st);
@@ -1016,6 +1080,8 @@ ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out
     else if (field == "rm_col") v = &ts.rm_col;
     else if (field == "loe_wbeg") v = &ts.loe_wbeg;
     else if (field == "loe_hpos") v = &ts.loe_hpos;
+    else if (field == "loe_spos") v = &ts.loe_spos;
+    else if (field == "loe_sval") v = &ts.loe_sval;
     else if (field == "rm_ebasis") v = &ts.rm_ebasis;
     else if (field == "rm_ew2") {
       tmp.assign(ts.rm_ew2.begin(), ts.rm_ew2.end());

@@ -18,6 +18,7 @@
 // length and grouped 32 at a time (one per lane), their entries interleaved so
 // that a warp reads one contiguous 128-byte line of indices per step.
 #include <algorithm>
+#include <map>
 #include <numeric>
 
 #include "ace_internal.hpp"
@@ -352,41 +353,120 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
     }
   }
 
-  // ---- row-major copy of all entries (kernels that keep every slot), longest tasks first
+  // ---- row-major copy of all entries (kernels that keep every slot), laid out as one stream per
+  //      warp of the one-environment-per-lane kernel
   {
     std::vector<Task> tasks;
     std::vector<Proto> protos;
     make_tasks(rows, slot_basis, n_g, true, slot_l, slot_r, task_len, tasks, protos);
-    std::vector<int32_t> order(tasks.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t a, int32_t b) { return protos[a].len > protos[b].len; });
-    ts.rm_off.push_back(0);
-    for (int32_t ti : order) {
-      ts.rm_tasks.push_back(tasks[ti]);
+    // Blocks: whole rows of at most kLoeBlockCols entries whose column sets are equal.  Such a
+    // row needs no gathers of its own: the block's columns are read once per warp, and each
+    // row is a header, its coefficients and the epilogue.
+    std::map<std::vector<int32_t>, std::vector<int32_t>> by_cols;
+    std::vector<uint8_t> in_block(tasks.size(), 0);
+    for (size_t ti = 0; ti < tasks.size(); ++ti) {
       const auto& r = rows[tasks[ti].row];
-      for (int32_t q = protos[ti].begin; q < protos[ti].begin + protos[ti].len; ++q) {
-        ts.rm_col.push_back(r[q].col);
-        ts.rm_ebasis.push_back(r[q].basis);
-        ts.rm_ew2.push_back(r[q].w2);
-      }
-      if (protos[ti].len % 2) {
-        ts.rm_col.push_back(0);
-        ts.rm_ebasis.push_back(-1);
-        ts.rm_ew2.push_back(0);
-      }
-      ts.rm_off.push_back((int32_t)ts.rm_col.size());
+      const int32_t len = protos[ti].len;
+      if (len < 1 || len > kLoeBlockCols || len != (int32_t)r.size()) continue;
+      std::vector<int32_t> cols;
+      for (const Entry& e : r) cols.push_back(e.col);
+      std::sort(cols.begin(), cols.end());
+      by_cols[cols].push_back((int32_t)ti);
     }
-    // per-warp streams: warp w's tasks in rm order, each header then its pairs
-    const int32_t n_rm = (int32_t)ts.rm_tasks.size();
-    ts.loe_hpos.assign(n_rm, 0);
+    struct Unit {
+      std::vector<int32_t> tis;  // one task, or the rows of a block
+      std::vector<int32_t> cols; // block columns (empty: a task)
+      int64_t cost;
+    };
+    std::vector<Unit> units;
+    for (auto& kv : by_cols) {
+      if ((int32_t)kv.second.size() < kLoeBlockMinRows) continue;
+      for (size_t i0 = 0; i0 < kv.second.size(); i0 += kLoeBlockRows) {
+        Unit u;
+        u.cols = kv.first;
+        for (size_t i = i0; i < std::min(kv.second.size(), i0 + kLoeBlockRows); ++i) {
+          u.tis.push_back(kv.second[i]);
+          in_block[kv.second[i]] = 1;
+        }
+        u.cost = 40 + 40 * (int64_t)u.tis.size();
+        units.push_back(std::move(u));
+      }
+    }
+    for (size_t ti = 0; ti < tasks.size(); ++ti)
+      if (!in_block[ti]) units.push_back(Unit{{(int32_t)ti}, {}, 100 + 4 * (int64_t)protos[ti].len});
+    // longest processing time first onto the least loaded warp (ties: lowest warp); units of
+    // equal cost keep their order, so the layout is deterministic
+    std::vector<int32_t> uorder(units.size());
+    std::iota(uorder.begin(), uorder.end(), 0);
+    std::stable_sort(uorder.begin(), uorder.end(),
+                     [&](int32_t x, int32_t y) { return units[x].cost > units[y].cost; });
+    std::vector<int64_t> load(kLoeWarps, 0);
+    std::vector<std::vector<int32_t>> wunits(kLoeWarps);
+    for (int32_t ui : uorder) {
+      const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      load[w] += units[ui].cost;
+      wunits[w].push_back(ui);
+    }
+    // rm order: warp by warp, unit by unit; every task's entries padded to an even count (pairs),
+    // every block row's to 2 * 4 coefficients (two items)
+    ts.rm_off.push_back(0);
     ts.loe_wbeg.assign(kLoeWarps + 1, 0);
     int32_t pos = 0;
+    auto push_entries = [&](int32_t ti, const std::vector<int32_t>* cols) {
+      const Task& t = tasks[ti];
+      const auto& r = rows[t.row];
+      Task rt = t;
+      if (cols) rt.flags |= kTaskBlockRow;
+      ts.rm_tasks.push_back(rt);
+      ts.loe_hpos.push_back(pos);
+      if (cols) {
+        for (int32_t c : *cols) {  // the block's column order
+          const Entry* e = nullptr;
+          for (const Entry& x : r)
+            if (x.col == c) e = &x;
+          ts.rm_col.push_back(c);
+          ts.rm_ebasis.push_back(e->basis);
+          ts.rm_ew2.push_back(e->w2);
+        }
+        for (size_t k = cols->size(); k < (size_t)kLoeBlockCols; ++k) {
+          ts.rm_col.push_back(0);
+          ts.rm_ebasis.push_back(-1);
+          ts.rm_ew2.push_back(0);
+        }
+        pos += 1 + kLoeBlockCols / 4;
+      } else {
+        for (int32_t q = protos[ti].begin; q < protos[ti].begin + protos[ti].len; ++q) {
+          ts.rm_col.push_back(r[q].col);
+          ts.rm_ebasis.push_back(r[q].basis);
+          ts.rm_ew2.push_back(r[q].w2);
+        }
+        if (protos[ti].len % 2) {
+          ts.rm_col.push_back(0);
+          ts.rm_ebasis.push_back(-1);
+          ts.rm_ew2.push_back(0);
+        }
+        pos += 1 + (protos[ti].len + 1) / 2;
+      }
+      ts.rm_off.push_back((int32_t)ts.rm_col.size());
+    };
     for (int w = 0; w < kLoeWarps; ++w) {
       ts.loe_wbeg[w] = pos;
-      for (int32_t t = w; t < n_rm; t += kLoeWarps) {
-        ts.loe_hpos[t] = pos;
-        pos += 1 + (ts.rm_off[t + 1] - ts.rm_off[t]) / 2;
+      for (int32_t ui : wunits[w]) {
+        const Unit& u = units[ui];
+        if (u.cols.empty()) {
+          push_entries(u.tis[0], nullptr);
+          continue;
+        }
+        // block header {m, rows << 8 | kLoeBlockUnit, 0, 0}, then the columns, kLoeBlockCols / 4 items
+        ts.loe_spos.push_back(pos);
+        ts.loe_sval.insert(ts.loe_sval.end(),
+                           {(int32_t)u.cols.size(), ((int32_t)u.tis.size() << 8) | kLoeBlockUnit, 0, 0});
+        ++pos;
+        for (int k = 0; k < kLoeBlockCols; k += 4) {
+          ts.loe_spos.push_back(pos++);
+          for (int c = k; c < k + 4; ++c) ts.loe_sval.push_back(c < (int)u.cols.size() ? u.cols[c] : 0);
+        }
+        for (int32_t ti : u.tis) push_entries(ti, &u.cols);
       }
     }
     ts.loe_wbeg[kLoeWarps] = pos;

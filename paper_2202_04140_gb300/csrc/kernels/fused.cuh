@@ -35,6 +35,11 @@ constexpr int kMaxLevels = 8;
 constexpr int kLoeStreamWarps = 32;
 // Zero items allocated after the last stream (the kernel reads up to this many items ahead).
 constexpr int kLoeStreamPad = 8;
+// Block units of the streams: header {m, rows << 8 | kLoeBlockFlag, 0, 0}, kLoeBlockCols / 4
+// items of columns, then per row a header {x, flags, z, row coefficient} and kLoeBlockCols / 4
+// items of coefficients.
+constexpr int kLoeBlockCols = 8;
+constexpr int kLoeBlockFlag = 16;
 
 enum : int { kReadPlain = 0, kReadComp = 1, kReadF64 = 2 };
 enum : uint32_t { kStatusBounds = 1u, kStatusTimeout = 2u };
@@ -98,9 +103,10 @@ struct LoeArgs {
   int32_t fwd_off[kMaxLevels + 1];
   int32_t rev_off[kMaxLevels + 1];
   int32_t n_fwd_levels, n_rev_levels;
-  // One stream per warp: each task is a header {target slot, (entry pairs << 8) |
+  // One stream per warp of units: a task is a header {target slot, (entry pairs << 8) |
   // flags, second factor slot (top operands), row coefficient bits} followed by
-  // its entry pairs {col0, coef0 bits, col1, coef1 bits}.
+  // its entry pairs {col0, coef0 bits, col1, coef1 bits}; a block of rows with the
+  // same kLoeBlockCols columns is laid out as described at kLoeBlockCols.
   const int4* stream;                 // followed by kLoeStreamPad zero items
   int32_t wbeg[kLoeStreamWarps + 1];  // first item of each warp's stream
   float* ws;          // global-workspace variant: [gridDim.x][n_slots (+ n_g)][32] floats
@@ -327,6 +333,7 @@ struct Acc<float, kReadF64> : AccD<float> {};
 template <>
 struct Acc<double, kReadPlain> : AccD<double> {};
 
+
 // ---- the kernel ------------------------------------------------------------------------
 
 // Entries of one lane's task, software-pipelined: the (column, coefficient)
@@ -467,9 +474,29 @@ __device__ __forceinline__ void task_entries_packed(const FusedArgs<float>& a, c
 // half u), and in the adjoint form g = phibar . (lin + u) goes to the row's
 // accumulator or, for a top operand, to its factors (segmented warp sums over
 // equal "A" targets, one shared-memory update per run).  Called by all lanes.
+// phibar of the tile: in registers when it is small, else read from shared memory.
+template <typename T, int E, int NOUT, int NS>
+struct PhiBar {
+  static constexpr bool kRegs = E * NOUT <= 8;  // measured: -2% on the stress step (E = 4, one channel)
+  T r[kRegs ? E : 1][kRegs ? NOUT : 1];
+  const T* p;
+  __device__ __forceinline__ PhiBar(const T* pb, int c0) : p(pb) {
+    if constexpr (kRegs) {
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) r[e][c] = pb[e * NS + c0 + c];
+    }
+  }
+  __device__ __forceinline__ T get(int e, int c, int c0) const {
+    if constexpr (kRegs) return r[e][c];
+    else return p[e * NS + c0 + c];
+  }
+};
+
 template <typename T, int E, int NOUT, int NS, bool GRAD, int RO, bool CHECK>
 __device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
-                                              const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT],
+                                              const PhiBar<T, E, NOUT, NS>& pb, Acc<T, RO> (&phiacc)[E][NOUT],
                                               const int4 task, const T (&acc)[E][NOUT], const T (&lin)[NOUT],
                                               const int rounds, const int lane, const int c0) {
   // channels c0 .. c0 + NOUT of NS; the adjoint seed g sums over them (the blocks of a
@@ -514,27 +541,27 @@ __device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __
     for (int e = 0; e < E; ++e) {
       T s = T(0);
 #pragma unroll
-      for (int c = 0; c < NOUT; ++c) s = fma_t(pb[e * NS + c0 + c], acc[e][c] + lin[c], s);
+      for (int c = 0; c < NOUT; ++c) s = fma_t(pb.get(e, c, c0), acc[e][c] + lin[c], s);
       g[e] = valid ? s : T(0);
     }
     // "A" target: the row itself, or the first factor of a top operand.  Lanes
     // are ordered by A target, so equal targets form runs; a segmented suffix
-    // sum leaves each run's total in its first lane, which does one atomic.
-    int key = valid ? (top ? pl : row) : -1 - lane;
+    // sum leaves each run's total in its first lane, which does one atomic.  The
+    // plan stores the runs with the task (bit 8 + r: lane + 2^r is in the same
+    // run; bit 13: first lane of its run), so no target is shuffled here.
+    const int key = valid ? (top ? pl : row) : 0;
     T va[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) va[e] = top ? g[e] * xr[e] : g[e];
     for (int r = 0, d = 1; r < rounds; ++r, d <<= 1) {  // rounds: warp-uniform, from the plan
-      const int k2 = __shfl_down_sync(0xffffffffu, key, d);
-      const bool same = (lane + d < 32) && (k2 == key);
+      const bool same = (task.y >> (8 + r)) & 1;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const T y = __shfl_down_sync(0xffffffffu, va[e], d);
         if (same) va[e] += y;
       }
     }
-    const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-    const bool head = lane == 0 || kprev != key;
+    const bool head = (task.y >> 13) & 1;
     if (valid && head) {
 #pragma unroll
       for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * gs + key, va[e]);
@@ -549,7 +576,8 @@ __device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __
 
 template <typename T, int E, int NOUT, int NS, bool GRAD, int RO, int NT, bool CHECK>
 __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
-                                          const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT], const int c0) {
+                                          const PhiBar<T, E, NOUT, NS>& pb, Acc<T, RO> (&phiacc)[E][NOUT],
+                                          const int c0) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   constexpr int NW = NT / 32;
@@ -619,7 +647,7 @@ __device__ __forceinline__ void run_tasks(const FusedArgs<T>& a, const T* __rest
 // epilogue as the other tasks (no row coefficient).
 template <typename T, int E, int NOUT, int NS, bool GRAD, int RO, int NT, bool CHECK>
 __device__ __forceinline__ void run_cold_tasks(const FusedArgs<T>& a, const T* __restrict__ AA, T* __restrict__ G,
-                                               const T* __restrict__ pb, Acc<T, RO> (&phiacc)[E][NOUT],
+                                               const PhiBar<T, E, NOUT, NS>& pb, Acc<T, RO> (&phiacc)[E][NOUT],
                                                const int c0) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -800,12 +828,13 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
     constexpr int NB = (NOUT > 8 && RO != kReadComp) ? 8 : NOUT;
     for (int c0 = 0; c0 < NOUT; c0 += NB) {
       Acc<T, RO> phiacc[E][NB];
+      const PhiBar<T, E, NB, NOUT> pbv(pb, c0);
       if (a.check) {
-        run_tasks<T, E, NB, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc, c0);
-        run_cold_tasks<T, E, NB, NOUT, GRAD, RO, NT, true>(a, AA, G, pb, phiacc, c0);
+        run_tasks<T, E, NB, NOUT, GRAD, RO, NT, true>(a, AA, G, pbv, phiacc, c0);
+        run_cold_tasks<T, E, NB, NOUT, GRAD, RO, NT, true>(a, AA, G, pbv, phiacc, c0);
       } else {
-        run_tasks<T, E, NB, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc, c0);
-        run_cold_tasks<T, E, NB, NOUT, GRAD, RO, NT, false>(a, AA, G, pb, phiacc, c0);
+        run_tasks<T, E, NB, NOUT, GRAD, RO, NT, false>(a, AA, G, pbv, phiacc, c0);
+        run_cold_tasks<T, E, NB, NOUT, GRAD, RO, NT, false>(a, AA, G, pbv, phiacc, c0);
       }
 #pragma unroll
       for (int e = 0; e < E; ++e)

@@ -25,6 +25,10 @@ cudaError_t launch_bind_loe(const float* c, const int4* tasks, const int32_t* to
                             const int32_t* ebasis, const uint8_t* ew2, const int32_t* slot_basis,
                             const int32_t* hpos, int32_t n_tasks, int4* stream, cudaStream_t st);
 
+// Write the items of the per-warp streams that the binding does not touch (block headers and
+// their columns): stream[pos[i]] = val[i].
+cudaError_t launch_loe_static(const int32_t* pos, const int4* val, int32_t n, int4* stream, cudaStream_t st);
+
 cudaError_t launch_bind(int dtype, const void* c, int n_out, int nout_pad, const int32_t* ebasis, const uint8_t* ew2,
                         int64_t n_entries, void* vals, const int32_t* lin_basis, int64_t n_lin, void* lin,
                         cudaStream_t st);

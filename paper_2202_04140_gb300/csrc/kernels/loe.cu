@@ -65,6 +65,87 @@ __device__ __forceinline__ void loe_pair(const LoeArgs& a, const float* AA, cons
 // Epilogue: phi += AA_s (lin + half u); adjoint g = phibar (lin + u) to G_s, or
 // G_x += g AA_z, G_z += g AA_x.  While a task runs, the next header and the
 // items after it (the next task's first pairs, when it has that many) are loaded.
+// Epilogue of a task or block row with header {x, flags, z, row coefficient} and row sum acc:
+// phi += AA_s (lin + half acc); adjoint g = phibar (lin + acc) to G_s, or G_x += g AA_z,
+// G_z += g AA_x for a top operand s = [x, z].
+template <bool GRAD, int RO, int S, bool CHECK>
+__device__ __forceinline__ void loe_epilogue(const LoeArgs& a, const float* AA, float* G, const float pbl,
+                                             Acc<float, RO>& phiacc, const int4 h, const float acc, const int lane) {
+  const float half = GRAD ? 0.5f : 1.f;
+  const bool top = (h.y & 2) != 0;
+  const int x = h.x, z = h.z;
+  if (CHECK) {
+    const unsigned lim = GRAD ? (unsigned)a.n_g : (unsigned)a.n_slots;
+    if ((unsigned)x >= lim || (top && (unsigned)z >= lim)) {
+      if (lane == 0) atomicOr(a.status, kStatusBounds);
+      return;
+    }
+  }
+  float ap, xl = 0.f, xr = 0.f;
+  if (top) {
+    xl = AA[x * S + lane];
+    xr = AA[z * S + lane];
+    ap = xl * xr;
+  } else {
+    ap = AA[x * S + lane];
+  }
+  const float lin = __int_as_float(h.w);
+  phiacc.add(ap * __fmaf_rn(half, acc, lin));
+  if constexpr (GRAD) {
+    const float g = pbl * (acc + lin);
+    if (top) {
+      atomicAdd(G + x * S + lane, g * xr);
+      atomicAdd(G + z * S + lane, g * xl);
+    } else {
+      atomicAdd(G + x * S + lane, g);
+    }
+  }
+}
+
+// A block unit at p (header h): the block's kLoeBlockCols column values of this lane's
+// environment are read once into registers; every row is then its header, two items of
+// coefficients and the epilogue (no gathers of its own).  Returns the item after the unit.
+template <bool GRAD, int RO, int S, bool CHECK>
+__device__ __forceinline__ const int4* loe_block(const LoeArgs& a, const float* AA, float* G, const float pbl,
+                                                 Acc<float, RO>& phiacc, const int4* p, const int4 h,
+                                                 const int4 c0, const int4 c1, const int lane) {
+  static_assert(kLoeBlockCols == 8, "two items of columns and of coefficients per row");
+  const int nrows = h.y >> 8;
+  int col[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  float q[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (CHECK && (unsigned)col[j] >= (unsigned)a.n_slots) {
+      if (lane == 0) atomicOr(a.status, kStatusBounds);
+      col[j] = 0;
+    }
+    q[j] = AA[col[j] * S + lane];
+  }
+  const int4* r = p + 3;
+  int4 rh = __ldg(r);
+  float4 f0 = __ldg(reinterpret_cast<const float4*>(r + 1));
+  float4 f1 = __ldg(reinterpret_cast<const float4*>(r + 2));
+  for (int i = 0; i < nrows; ++i) {
+    // the next row's items (or the items after the unit: inside the stream and its padding)
+    const int4 rhn = __ldg(r + 3);
+    const float4 f0n = __ldg(reinterpret_cast<const float4*>(r + 4));
+    const float4 f1n = __ldg(reinterpret_cast<const float4*>(r + 5));
+    float s0 = f0.x * q[0], s1 = f0.y * q[1];
+    s0 = __fmaf_rn(f0.z, q[2], s0);
+    s1 = __fmaf_rn(f0.w, q[3], s1);
+    s0 = __fmaf_rn(f1.x, q[4], s0);
+    s1 = __fmaf_rn(f1.y, q[5], s1);
+    s0 = __fmaf_rn(f1.z, q[6], s0);
+    s1 = __fmaf_rn(f1.w, q[7], s1);
+    loe_epilogue<GRAD, RO, S, CHECK>(a, AA, G, pbl, phiacc, rh, s0 + s1, lane);
+    r += 3;
+    rh = rhn;
+    f0 = f0n;
+    f1 = f1n;
+  }
+  return r;
+}
+
 template <bool GRAD, int RO, int S, bool CHECK>
 __device__ __forceinline__ void loe_tasks(const LoeArgs& a, float* AA, float* G, const float pbl,
                                           Acc<float, RO>& phiacc, const int warp, const int lane) {
@@ -74,12 +155,20 @@ __device__ __forceinline__ void loe_tasks(const LoeArgs& a, float* AA, float* G,
   const int4* p = a.stream + a.wbeg[warp];
   const int4* const pend = a.stream + a.wbeg[warp + 1];
   if (p >= pend) return;
-  const float half = GRAD ? 0.5f : 1.f;
   int4 h = __ldg(p);
   int4 cur[kPairBatch];
 #pragma unroll
   for (int u = 0; u < kPairBatch; ++u) cur[u] = __ldg(p + 1 + u);
   while (true) {
+    if (h.y & kLoeBlockFlag) {
+      const int4* const pn = loe_block<GRAD, RO, S, CHECK>(a, AA, G, pbl, phiacc, p, h, cur[0], cur[1], lane);
+      if (pn >= pend) break;
+      p = pn;
+      h = __ldg(p);
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u) cur[u] = __ldg(p + 1 + u);
+      continue;
+    }
     const int np = h.y >> 8;
     const int4* const pn = p + 1 + np;  // the next header
     const bool more = pn < pend;
@@ -100,38 +189,7 @@ __device__ __forceinline__ void loe_tasks(const LoeArgs& a, float* AA, float* G,
       for (int u = 0; u < kPairBatch; ++u)
         if (b + u < np) loe_pair<S, CHECK>(a, AA, bt[u], lane, acc0, acc1);
     }
-    const float acc = acc0 + acc1;
-    const bool top = (h.y & 2) != 0;
-    int x = h.x, z = h.z;
-    bool ok = true;
-    if (CHECK) {
-      const unsigned lim = GRAD ? (unsigned)a.n_g : (unsigned)a.n_slots;
-      if ((unsigned)x >= lim || (top && (unsigned)z >= lim)) {
-        if (lane == 0) atomicOr(a.status, kStatusBounds);
-        ok = false;
-      }
-    }
-    if (ok) {
-      float ap, xl = 0.f, xr = 0.f;
-      if (top) {
-        xl = AA[x * S + lane];
-        xr = AA[z * S + lane];
-        ap = xl * xr;
-      } else {
-        ap = AA[x * S + lane];
-      }
-      const float lin = __int_as_float(h.w);
-      phiacc.add(ap * __fmaf_rn(half, acc, lin));
-      if constexpr (GRAD) {
-        const float g = pbl * (acc + lin);
-        if (top) {
-          atomicAdd(G + x * S + lane, g * xr);
-          atomicAdd(G + z * S + lane, g * xl);
-        } else {
-          atomicAdd(G + x * S + lane, g);
-        }
-      }
-    }
+    loe_epilogue<GRAD, RO, S, CHECK>(a, AA, G, pbl, phiacc, h, acc0 + acc1, lane);
     if (!more) break;
     p = pn;
     h = hn;
@@ -285,7 +343,9 @@ size_t loe_global_bytes_per_cta(int n_slots, int n_g, bool grad) {
 
 // One thread per task: its header {target, (pairs << 8) | flags, second factor,
 // row coefficient} and its entry pairs {column, c of the entry's basis function
-// (doubled on the diagonal of the symmetric form; 0 for padding)}.  The target of
+// (doubled on the diagonal of the symmetric form; 0 for padding)}; for a block
+// row (flag bit 3) the header without a pair count and its coefficients alone,
+// four per item, in the block's column order.  The target of
 // a top operand is its first factor (the kernel forms its value from both
 // factors and pushes adjoints to them), otherwise the row itself; the row
 // coefficient is c of the row when the task is the row's first and the row is a
@@ -302,14 +362,30 @@ __global__ void bind_loe_kernel(const float* __restrict__ c, const int4* __restr
     const float lin = ((t.y & 5) == 5 && b >= 0) ? c[b] : 0.f;
     const bool top = (t.y & 2) != 0;
     int4* h = stream + hpos[i];
-    *h = make_int4(top ? t.z : t.x, (((q1 - q0) >> 1) << 8) | (t.y & 0xff), top ? t.w : 0, __float_as_int(lin));
+    const bool block_row = (t.y & 8) != 0;  // coefficients only, four per item (block column order)
+    *h = make_int4(top ? t.z : t.x, block_row ? (t.y & 0xff) : ((((q1 - q0) >> 1) << 8) | (t.y & 0xff)),
+                   top ? t.w : 0, __float_as_int(lin));
     int2* e = reinterpret_cast<int2*>(h + 1);
+    float* f = reinterpret_cast<float*>(h + 1);
     for (int32_t q = q0; q < q1; ++q) {
       const int32_t eb = ebasis[q];
       const float v = eb >= 0 ? c[eb] * (ew2[q] ? 2.f : 1.f) : 0.f;
-      e[q - q0] = make_int2(col[q], __float_as_int(v));
+      if (block_row) f[q - q0] = v;
+      else e[q - q0] = make_int2(col[q], __float_as_int(v));
     }
   }
+}
+
+__global__ void loe_static_kernel(const int32_t* __restrict__ pos, const int4* __restrict__ val, int32_t n,
+                                  int4* __restrict__ stream) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) stream[pos[i]] = val[i];
+}
+
+cudaError_t launch_loe_static(const int32_t* pos, const int4* val, int32_t n, int4* stream, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>(((int64_t)n + 255) / 256, 4096);
+  loe_static_kernel<<<blocks, 256, 0, st>>>(pos, val, n, stream);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_bind_loe(const float* c, const int4* tasks, const int32_t* toff, const int32_t* col,

@@ -303,27 +303,43 @@ def test_row_major_plan_emulation_matches_oracle(name):
 
 
 def loe_streams(dag, mode, c):
-    """The per-warp task streams as the binding writes them: a header (x, pairs << 8 | flags, z, lin)
-    then the task's pairs, task t of the row-major copy in warp t mod 32 at item loe_hpos[t]."""
+    """The per-warp streams as the plan lays them out and the binding fills them.  A task is a
+    header (x, pairs << 8 | flags, z, lin) then its pairs; a block is a header (m, rows << 8 | 16)
+    and two items of 4 columns (written once from the plan), then per row (flag 8) a header and
+    two items of 4 coefficients in the block's column order.  Task t of the row-major copy has its
+    header at loe_hpos[t]."""
     P = plan_arrays(dag, mode)
     R = {k: L.ace_dag_plan_array(dag.handle, f"{mode}_rm_{k}") for k in ["tasks", "off", "col", "ebasis", "ew2"]}
     wbeg = L.ace_dag_plan_array(dag.handle, f"{mode}_loe_wbeg")
     hpos = L.ace_dag_plan_array(dag.handle, f"{mode}_loe_hpos")
+    spos = L.ace_dag_plan_array(dag.handle, f"{mode}_loe_spos")
+    sval = L.ace_dag_plan_array(dag.handle, f"{mode}_loe_sval").reshape(-1, 4)
     T = R["tasks"].reshape(-1, 4)
     c = c.reshape(-1)
     items = [None] * int(wbeg[-1])
+    for i in range(0, len(spos), 3):
+        items[spos[i]] = ("b",) + tuple(int(v) for v in sval[i])
+        for k in (1, 2):
+            items[spos[i + k]] = ("cols",) + tuple(int(v) for v in sval[i + k])
     for t, (row, flags, pl, pr) in enumerate(T):
         q0, q1 = R["off"][t], R["off"][t + 1]
         b = P["slot_basis"][row]
         lin = c[b] if ((flags & 5) == 5 and b >= 0) else 0.0
         top = (flags & 2) > 0
+        v = [c[R["ebasis"][q]] * (2.0 if R["ew2"][q] else 1.0) if R["ebasis"][q] >= 0 else 0.0 for q in range(q0, q1)]
         assert items[hpos[t]] is None
+        if flags & 8:
+            assert q1 - q0 == 8
+            items[hpos[t]] = ("r", pl if top else row, flags, pr if top else 0, lin)
+            for k in (0, 1):
+                assert items[hpos[t] + 1 + k] is None
+                items[hpos[t] + 1 + k] = ("c",) + tuple(v[4 * k:4 * k + 4])
+            continue
         items[hpos[t]] = ("h", pl if top else row, ((q1 - q0) // 2) << 8 | flags, pr if top else 0, lin)
         for k in range(q0, q1, 2):
-            v = [c[R["ebasis"][q]] * (2.0 if R["ew2"][q] else 1.0) if R["ebasis"][q] >= 0 else 0.0 for q in (k, k + 1)]
             j = hpos[t] + 1 + (k - q0) // 2
             assert items[j] is None
-            items[j] = ("p", R["col"][k], v[0], R["col"][k + 1], v[1])
+            items[j] = ("p", R["col"][k], v[k - q0], R["col"][k + 1], v[k + 1 - q0])
     assert all(it is not None for it in items)
     return wbeg, items, T
 
@@ -345,26 +361,45 @@ def emulate_loe_streams(dag, mode, A, c, phibar=None):
     pb = np.ones(n_env) if phibar is None else phibar.reshape(-1)
     half = 0.5 if mode == "sym" else 1.0
     seen = 0
+
+    def epilogue(x, y, z, lin, u):
+        top = (y & 2) > 0
+        ap = AA[:, x] * AA[:, z] if top else AA[:, x]
+        phi[:] += ap * (lin + half * u)
+        if mode == "sym":
+            g = pb * (u + lin)
+            if top:
+                G[:, x] += g * AA[:, z]
+                G[:, z] += g * AA[:, x]
+            else:
+                G[:, x] += g
+
     for w in range(len(wbeg) - 1):
         p = wbeg[w]
         while p < wbeg[w + 1]:
+            if items[p][0] == "b":                   # a block: columns once, then its rows
+                _, m, y, _, _ = items[p]
+                assert y & 0xff == 16 and 1 <= m <= 8
+                cols = list(items[p + 1][1:]) + list(items[p + 2][1:])
+                p += 3
+                for _ in range(y >> 8):
+                    kind, x, yr, z, lin = items[p]
+                    assert kind == "r" and yr & 8
+                    cf = list(items[p + 1][1:]) + list(items[p + 2][1:])
+                    u = sum(cf[j] * AA[:, cols[j]] for j in range(8))
+                    epilogue(x, yr, z, lin, u)
+                    p += 3
+                    seen += 1
+                continue
             kind, x, y, z, lin = items[p]
             assert kind == "h"
-            npair, top = y >> 8, (y & 2) > 0
+            npair = y >> 8
             u = np.zeros(n_env)
             for q in range(p + 1, p + 1 + npair):
                 kind2, j0, c0, j1, c1 = items[q]
                 assert kind2 == "p"
                 u += c0 * AA[:, j0] + c1 * AA[:, j1]
-            ap = AA[:, x] * AA[:, z] if top else AA[:, x]
-            phi += ap * (lin + half * u)
-            if mode == "sym":
-                g = pb * (u + lin)
-                if top:
-                    G[:, x] += g * AA[:, z]
-                    G[:, z] += g * AA[:, x]
-                else:
-                    G[:, x] += g
+            epilogue(x, y, z, lin, u)
             p += 1 + npair
             seen += 1
     assert seen == len(T)
@@ -395,15 +430,13 @@ def test_per_warp_stream_emulation_matches_oracle(name):
         assert normalized_error(phi[:, None], ref, error_scale(A, o, c)) < 1e-12
     _, dA = emulate_loe_streams(dag, "sym", A, c, pb)
     assert normalized_error(dA, grad_naive(A, o, c, pb), grad_error_scale(A, o, c, pb)) < 1e-12
-    # warp w holds tasks w, w + 32, ... in order
+    # the row-major tasks are in stream order; most rows of this graph are block rows
     hpos = L.ace_dag_plan_array(dag.handle, "sym_loe_hpos")
     wbeg = L.ace_dag_plan_array(dag.handle, "sym_loe_wbeg")
-    assert len(wbeg) == 33
-    for t in range(len(hpos)):
-        wv = t % 32
-        assert wbeg[wv] <= hpos[t] < wbeg[wv + 1]
-        if t + 32 < len(hpos):
-            assert hpos[t + 32] > hpos[t]
+    assert len(wbeg) == 33 and np.all(np.diff(hpos) > 0) and hpos[-1] < wbeg[-1]
+    if name == "fwd_grad_k392":
+        flags = L.ace_dag_plan_array(dag.handle, "sym_rm_tasks").reshape(-1, 4)[:, 1]
+        assert np.mean((flags & 8) > 0) > 0.5
 
 
 def test_plan_emulation_stress_sample():
