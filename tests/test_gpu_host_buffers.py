@@ -175,3 +175,27 @@ def test_forces_host_with_features_and_bad_offsets(dev):
         energy_and_forces_host(d, P32, bad, cd, w.nmin, w.nmax, w.lmax, w.rc, mu=mu32, kmax=w.kmax)
     with pytest.raises(L.AceError):                       # a graph over another one-particle set
         energy_and_forces_host(d, P32, off, cd, w.nmin, w.nmax, w.lmax - 1, w.rc, mu=mu32, kmax=w.kmax)
+
+
+def test_grad_host_full_size_stress_against_oracle(dev):
+    """The end-to-end path the benchmark times: the stress workload's whole batch (16,384
+    environments, K = 810, nu <= 6) through ace_eval_grad_host with pinned host buffers and the
+    automatic chunks, compared with the FP64 oracle on sampled environments, including the first
+    and last of every chunk boundary region."""
+    from paper_2202_04140_gb300.torch_api import Dag, Spec
+    from oracle.evaluate import error_scale, grad_naive, phi_naive
+    w = W.WORKLOADS["stress_k810"]
+    o = workload_index_set(w)
+    d = Dag(Spec.from_workload(w))
+    A = W.round_to(W.draw_A(w.n_env, d.K), "f32")
+    c = W.round_to(W.draw_c(o.deg, 1), "f32")
+    A32 = torch.tensor(A, dtype=torch.float32).pin_memory()
+    cd = torch.tensor(c, dtype=torch.float32, device=dev)
+    phi_h, dA_h = d.evaluate_grad_host(A32, cd, None, readout="compensated")
+    assert d.status() == 0
+    n = w.n_env
+    idx = np.array([0, 1, n // 3 - 1, n // 3, n // 2, 2 * n // 3 - 1, 2 * n // 3, n - 2, n - 1])
+    sub = A[idx]
+    phi_ref = phi_naive(sub, o, c)
+    assert normalized_error(phi_h.numpy()[idx], phi_ref, error_scale(sub, o, c)) < TOL32
+    assert normalized_error(dA_h.numpy()[idx], grad_naive(sub, o, c), grad_error_scale(sub, o, c)) < TOL32
