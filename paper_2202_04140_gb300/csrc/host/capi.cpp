@@ -88,6 +88,9 @@ struct DevTaskSet {
   int32_t loe_wbeg[kLoeWarps + 1] = {};
   int64_t n_loe_items = 0;
   int4* loe_stream = nullptr;   // bound streams: headers and {column, coefficient} pairs (FP32, one channel)
+  int4* loe_istream = nullptr;  // the same layout bound with basis indices (FP32, several channels)
+  float* cvals16 = nullptr;     // bound coefficients [n_basis][16] (channels past n_out zero)
+  bool multi_bound = false;
   bool rm_bound = false;
   // coefficients bound into this task set
   void* vals = nullptr;
@@ -525,6 +528,35 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
     if (e != cudaSuccess) return cuda_fail(e, "coefficient binding launch");
   }
   dt.rm_bound = false;
+  dt.multi_bound = false;
+  if (dtype == ACE_F32 && n_out > 1) {
+    // several channels, one environment per lane: streams of basis indices and the coefficient table
+    const size_t sbytes = ((size_t)dt.n_loe_items + dev::kLoeStreamPad) * sizeof(int4);
+    if (!dt.loe_istream) {
+      void* p = nullptr;
+      if ((e = cudaMalloc(&p, sbytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      dt.loe_istream = static_cast<int4*>(p);
+      if ((e = cudaMemsetAsync(p, 0, sbytes, st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+      if ((e = launch_loe_static(dt.loe_spos, dt.loe_sval, dt.n_loe_static, dt.loe_istream, st)) != cudaSuccess)
+        return cuda_fail(e, "stream layout launch");
+      if ((e = launch_bind_loe_idx(dt.rm_tasks, dt.rm_off, dt.rm_col, dt.rm_ebasis, dt.rm_ew2, d->slot_basis,
+                                   dt.loe_hpos, dt.n_rm, dt.loe_istream, st)) != cudaSuccess)
+        return cuda_fail(e, "index binding launch");
+    }
+    if (!dt.cvals16) {
+      void* p = nullptr;
+      if ((e = cudaMalloc(&p, std::max<size_t>((size_t)d->n_basis * 16 * sizeof(float), 16))) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc");
+      dt.cvals16 = static_cast<float*>(p);
+    }
+    if ((e = cudaMemsetAsync(dt.cvals16, 0, (size_t)d->n_basis * 16 * sizeof(float), st)) != cudaSuccess ||
+        (d->n_basis > 0 &&
+         (e = cudaMemcpy2DAsync(dt.cvals16, 16 * sizeof(float), c, (size_t)n_out * sizeof(float),
+                                (size_t)n_out * sizeof(float), (size_t)d->n_basis, cudaMemcpyDeviceToDevice, st)) !=
+             cudaSuccess))
+      return cuda_fail(e, "coefficient table copy");
+    dt.multi_bound = true;
+  }
   if (dtype == ACE_F32 && n_out == 1) {
     if (!dt.loe_stream) {
       void* p = nullptr;
@@ -609,7 +641,74 @@ int kernel_choice() {
   if (v && std::strcmp(v, "lon") == 0) return 1;
   if (v && std::strcmp(v, "loe") == 0) return 2;
   if (v && std::strcmp(v, "loeg") == 0) return 3;
+  if (v && std::strcmp(v, "loem") == 0) return 4;
   return 0;
+}
+
+ace_status grow_loe_workspace(ace_dag* d, size_t need) {
+  if (need <= d->loe_ws_bytes) return ACE_OK;
+  if (d->loe_ws) cudaFree(d->loe_ws);
+  d->loe_ws = nullptr;
+  d->loe_ws_bytes = 0;
+  cudaError_t e = cudaMalloc(&d->loe_ws, need);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (stored-value workspace)");
+  d->loe_ws_bytes = need;
+  return ACE_OK;
+}
+
+void fill_loe_args(const ace_dag* d, const DevTaskSet& dt, const void* A, const void* phibar, int64_t n_env,
+                   void* phi, void* dA, dev::LoeArgs& a) {
+  const Plan& p = d->plan;
+  a.ws = static_cast<float*>(d->loe_ws);
+  a.A = static_cast<const float*>(A);
+  a.phibar = static_cast<const float*>(phibar);
+  a.phi = static_cast<float*>(phi);
+  a.dA = static_cast<float*>(dA);
+  a.n_env = n_env;
+  a.n_tiles = (n_env + 31) / 32;
+  a.K = p.K;
+  a.n_slots = p.n_slots;
+  a.n_g = p.n_g;
+  a.fwd_slot = d->fwd_slot;
+  a.fwd_l = d->fwd_l;
+  a.fwd_r = d->fwd_r;
+  a.rev_slot = d->rev_slot;
+  a.rev_l = d->rev_l;
+  a.rev_r = d->rev_r;
+  a.n_fwd_levels = (int32_t)p.fwd.off.size() - 1;
+  a.n_rev_levels = (int32_t)p.rev.off.size() - 1;
+  for (int i = 0; i <= dev::kMaxLevels; ++i) {
+    a.fwd_off[i] = i < (int)p.fwd.off.size() ? p.fwd.off[i] : 0;
+    a.rev_off[i] = i < (int)p.rev.off.size() ? p.rev.off[i] : 0;
+  }
+  a.stream = dt.loe_stream;
+  for (int w = 0; w <= kLoeWarps; ++w) a.wbeg[w] = dt.loe_wbeg[w];
+  a.check = checked_mode() ? 1 : 0;
+  a.status = d->status;
+}
+
+// Several channels, forward only, one environment per lane (stored values in the global workspace).
+ace_status run_loe_multi(ace_dag* d, DevTaskSet& dt, const void* A, int64_t n_env, int n_out, int readout, void* phi,
+                         cudaStream_t st) {
+  int nt = 0;
+  const void* k = loe_multi_kernel_ptr(readout, &nt);
+  if (!k) return fail(ACE_ERR_UNSUPPORTED, "no kernel for this readout mode");
+  const size_t smem = loe_multi_smem(nt);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  int bps = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, nt, smem)) != cudaSuccess)
+    return cuda_fail(e, "occupancy query");
+  if (bps < 1) return fail(ACE_ERR_UNSUPPORTED, "several-channel kernel cannot be resident");
+  const int64_t n_tiles = (n_env + 31) / 32;
+  const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)d->sm_count * bps);
+  ace_status s = grow_loe_workspace(d, (size_t)grid * d->plan.n_slots * 32 * sizeof(float));
+  if (s != ACE_OK) return s;
+  dev::LoeArgs a{};
+  fill_loe_args(d, dt, A, nullptr, n_env, phi, nullptr, a);
+  e = launch_loe_multi(k, (int)grid, nt, smem, a, dt.loe_istream, dt.cvals16, n_out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "several-channel kernel launch");
+  return ACE_OK;
 }
 
 ace_status run_loe(ace_dag* d, DevTaskSet& dt, const void* A, const void* phibar, int64_t n_env, int readout,
@@ -689,6 +788,10 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
       E_force = it->second.second;
     }
   }
+  const bool multi_ok = dtype == ACE_F32 && n_out > 1 && !grad && dt.multi_bound;
+  if (choice == 4 && !multi_ok)
+    return fail(ACE_ERR_UNSUPPORTED, "ACE_KERNEL=loem: FP32 forward requests with several channels only");
+  if (choice == 4) return run_loe_multi(d, dt, A, n_env, n_out, readout, phi, st);
   const bool loeg_ok = dtype == ACE_F32 && n_out == 1 && dt.rm_bound;
   const bool loe_ok = loeg_ok && loe_smem(d->plan.n_slots, d->plan.n_g, grad, 1024) <= (size_t)d->smem_optin;
   if (choice == 2 && !loe_ok) return fail(ACE_ERR_UNSUPPORTED, "ACE_KERNEL=loe: graph or request does not fit");
@@ -797,7 +900,7 @@ int64_t tile_envs_of(const ace_dag* d, const DevTaskSet& dt, int dtype, int n_ou
   }
   const bool loeg_ok = dtype == ACE_F32 && n_out == 1 && dt.rm_bound;
   const bool loe_ok = loeg_ok && loe_smem(d->plan.n_slots, d->plan.n_g, grad, 1024) <= (size_t)d->smem_optin;
-  if (choice == 2 || choice == 3 || (loe_ok && choice != 1)) return 32;
+  if (choice == 2 || choice == 3 || choice == 4 || (loe_ok && choice != 1)) return 32;
   int E = 0, nt = 0;
   size_t smem = 0;
   const void* k = nullptr;
@@ -1146,6 +1249,8 @@ void ace_dag_free(ace_dag* dag) {
       if (t->vals4) cudaFree(t->vals4);
       if (t->cold_vals) cudaFree(t->cold_vals);
       if (t->loe_stream) cudaFree(t->loe_stream);
+      if (t->loe_istream) cudaFree(t->loe_istream);
+      if (t->cvals16) cudaFree(t->cvals16);
     }
     cudaSetDevice(cur);
   }
@@ -1233,7 +1338,7 @@ ace_status ace_dag_autotune(ace_dag* dag, int64_t n_env, int32_t n_out, int32_t 
   const int npad = nout_pad_of(n_out);
   const auto key = std::make_tuple((int)dtype, npad, grad ? 1 : 0);
   dag->tuned.erase(key);
-  std::vector<std::pair<int, int>> cands = {{2, 0}, {3, 0}};
+  std::vector<std::pair<int, int>> cands = {{2, 0}, {3, 0}, {4, 0}};
   for (int E : {1, 2, 4, 8, 16}) cands.push_back({1, E});
   cudaEvent_t a, b;
   cudaEventCreate(&a);

@@ -9,6 +9,10 @@
 
 namespace ace {
 
+namespace dev {
+struct LoeArgs;
+}
+
 // Returns the fused kernel instantiation for (dtype, E, NOUT, grad, readout) or
 // nullptr when that combination is not compiled; *nt receives its block size.
 const void* fused_kernel_ptr(int dtype, int E, int nout, bool grad, int readout, int* nt);
@@ -24,6 +28,17 @@ size_t loe_global_bytes_per_cta(int n_slots, int n_g, bool grad);
 cudaError_t launch_bind_loe(const float* c, const int4* tasks, const int32_t* toff, const int32_t* col,
                             const int32_t* ebasis, const uint8_t* ew2, const int32_t* slot_basis,
                             const int32_t* hpos, int32_t n_tasks, int4* stream, cudaStream_t st);
+
+// Several channels, one environment per lane (loe_multi.cu, forward only): kernel, shared
+// memory, launch with the index-bound streams and the coefficient table c[n_basis][16].
+const void* loe_multi_kernel_ptr(int readout, int* nt);
+size_t loe_multi_smem(int nt);
+cudaError_t launch_loe_multi(const void* kernel, int grid, int nt, size_t smem, const dev::LoeArgs& base,
+                             const int4* istream, const float* cvals, int n_out, cudaStream_t st);
+// The per-warp streams bound with basis indices (bit 30: doubled) in place of coefficients.
+cudaError_t launch_bind_loe_idx(const int4* tasks, const int32_t* toff, const int32_t* col, const int32_t* ebasis,
+                                const uint8_t* ew2, const int32_t* slot_basis, const int32_t* hpos, int32_t n_tasks,
+                                int4* stream, cudaStream_t st);
 
 // Write the items of the per-warp streams that the binding does not touch (block headers and
 // their columns): stream[pos[i]] = val[i].

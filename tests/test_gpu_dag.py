@@ -187,6 +187,40 @@ def test_uneven_16ch_full_size_sampled(dev):
     assert np.all(np.isfinite(phi))
 
 
+@pytest.mark.parametrize("readout", ["plain", "compensated", "fp64"])
+@pytest.mark.parametrize("n_out", [2, 3, 16])
+def test_several_channels_env_per_lane(dev, readout, n_out, monkeypatch):
+    """The several-channel forward kernel (one environment per lane, coefficient rows read once per
+    warp, stored values in the global workspace): 301 environments (a ragged last tile of 13)."""
+    monkeypatch.setenv("ACE_KERNEL", "loem")
+    w, o, d, A, c = setup("uneven_16ch_k392", n_env=301, n_out=n_out)
+    A32, c32 = to_f32(A), to_f32(c)
+    phi = d.evaluate(t(A32, torch.float32, dev), t(c32, torch.float32, dev), readout=readout).cpu().numpy()
+    assert phi.shape == (301, n_out)
+    assert normalized_error(phi, phi_naive(A32, o, c32), error_scale(A32, o, c32)) < TOL32
+    assert d.status() == 0
+
+
+def test_several_channels_env_per_lane_full_size_and_refusals(dev, monkeypatch):
+    """All 100,000 environments of the 16-channel workload in one launch (every CTA's workspace
+    slice in use), sampled against the oracle; the form refuses adjoint and one-channel requests."""
+    monkeypatch.setenv("ACE_KERNEL", "loem")
+    w, o, d, A, c = setup("uneven_16ch_k392")
+    A32, c32 = to_f32(A), to_f32(c)
+    At, ct = t(A32, torch.float32, dev), t(c32, torch.float32, dev)
+    phi = d.evaluate(At, ct, readout="compensated").cpu().numpy()
+    idx = np.sort(np.random.default_rng(6).choice(A.shape[0], 48, replace=False))
+    idx = np.concatenate([[0, 31, 32], idx, [A.shape[0] - 1]])
+    sub = A32[idx]
+    assert normalized_error(phi[idx], phi_naive(sub, o, c32), error_scale(sub, o, c32)) < TOL32
+    assert np.all(np.isfinite(phi)) and d.status() == 0
+    from paper_2202_04140_gb300.ace import AceError
+    with pytest.raises(AceError):
+        d.evaluate_grad(At[:64], ct)
+    with pytest.raises(AceError):
+        d.evaluate(At[:64], ct[:, :1].contiguous())
+
+
 # ---- FP32: the stress workload (K = 810, nu <= 6, D = 24, 16384 environments) ----------------------
 
 def test_stress_k810_full_size_sampled(dev):
@@ -253,11 +287,13 @@ def test_autotune_then_evaluate(dev, name, n_out, grad):
     w, o, _, A, c = setup(name, n_env=301)
     d = Dag(_CACHE[(name, "balanced")][2])          # own graph handle: the tuned choice stays local
     res = d.autotune(n_env=4096, n_out=n_out, dtype=torch.float32, grad=grad)
-    assert res["kernel"] in ("tile_per_lane", "env_per_lane") and res["ms"] > 0
+    assert res["kernel"] in ("tile_per_lane", "env_per_lane", "env_per_lane_multi") and res["ms"] > 0
     if res["kernel"] == "tile_per_lane":
         assert res["E"] in (1, 2, 4, 8, 16)
     if n_out > 1:
-        assert res["kernel"] == "tile_per_lane"
+        assert res["kernel"] in ("tile_per_lane", "env_per_lane_multi")
+    else:
+        assert res["kernel"] != "env_per_lane_multi"
     A32, c32 = to_f32(A), to_f32(c)
     At, ct = t(A32, torch.float32, dev), t(c32, torch.float32, dev)
     ref, scale = phi_naive(A32, o, c32), error_scale(A32, o, c32)
