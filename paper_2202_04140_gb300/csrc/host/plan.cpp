@@ -388,12 +388,12 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
           u.tis.push_back(kv.second[i]);
           in_block[kv.second[i]] = 1;
         }
-        u.cost = 40 + 40 * (int64_t)u.tis.size();
+        u.cost = 20 + 30 * (int64_t)u.tis.size();  // measured against 40 + 40 rows, 40 + 60 rows: best
         units.push_back(std::move(u));
       }
     }
     for (size_t ti = 0; ti < tasks.size(); ++ti)
-      if (!in_block[ti]) units.push_back(Unit{{(int32_t)ti}, {}, 100 + 4 * (int64_t)protos[ti].len});
+      if (!in_block[ti]) units.push_back(Unit{{(int32_t)ti}, {}, 60 + 6 * (int64_t)protos[ti].len});
     // longest processing time first onto the least loaded warp (ties: lowest warp); units of
     // equal cost keep their order, so the layout is deterministic
     std::vector<int32_t> uorder(units.size());
