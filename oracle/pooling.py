@@ -17,6 +17,9 @@ uses (readings, applied identically in the GPU path):
     Since (1 - u^2)^{m/2} cos(m phi) = Re((x + i y)^m) / r^m (and Im for sin),
     Y_lm = sqrt(2) N_lm Q_lm(z/r) Re/Im((x+iy)^m) r^{-m} with Q_lm = d^m P_l/du^m;
     the gradient below differentiates exactly this product.
+  * Cutoff: a neighbour at r >= rc (or at r = 0, where r/|r| is undefined) contributes
+    nothing, and its force is zero.  The envelope (1 - r/rc)^2 has a double root at rc, so
+    R_n and dR_n/dr both reach 0 there: the zero continuation is C^1 at the cutoff.
   * One-particle id = (n - nmin)(lmax+1)^2 + l^2 + (l + m).
   * Invariant features (section "Invariant features"): phi_nlmk(r, mu) =
     R_n(r) Y_l^m(r/|r|) T_k(mu), T_k the Chebyshev polynomial of the first kind
@@ -138,19 +141,29 @@ def one_particle(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float, with
                  mu: np.ndarray | None = None, kmax: int = 0):
     """phi_k(r_j) for all neighbours j and one-particle ids k, and grad phi_k (n, K, 3).
     With mu (one feature value per neighbour) the ids include the feature degree k <= kmax."""
-    P = np.asarray(P, dtype=np.float64)
+    P, inside = _inside(P, rc)
     r = np.linalg.norm(P, axis=1)
     Y, dY = real_sph_harm(P, lmax, with_grad)
     R, dR = radial(r, nmin, nmax, rc, with_grad)
     R, dR = _with_features(R, dR, mu, kmax)
     nR, nL = R.shape[1], Y.shape[1]
-    phi = (R[:, :, None] * Y[:, None, :]).reshape(P.shape[0], nR * nL)
+    phi = (R[:, :, None] * Y[:, None, :]).reshape(P.shape[0], nR * nL) * inside[:, None]
     if not with_grad:
         return phi, None
     rhat = P / r[:, None]
     g = (dR[:, :, None, None] * Y[:, None, :, None] * rhat[:, None, None, :]
          + R[:, :, None, None] * dY[:, None, :, :])
-    return phi, g.reshape(P.shape[0], nR * nL, 3)
+    return phi, g.reshape(P.shape[0], nR * nL, 3) * inside[:, None, None]
+
+
+def _inside(P: np.ndarray, rc: float):
+    """(P', inside): neighbours with 0 < r < rc; the others are replaced by a point inside the
+    ball (their contributions are multiplied by inside = 0 afterwards)."""
+    P = np.array(P, dtype=np.float64)
+    r = np.linalg.norm(P, axis=1)
+    inside = (r > 0.0) & (r < rc)
+    P[~inside] = (0.5 * rc, 0.0, 0.0)
+    return P, inside.astype(np.float64)
 
 
 def one_particle_grad_bound(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float,
@@ -160,7 +173,7 @@ def one_particle_grad_bound(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: 
     Used as the scale of the force error: |F_hat - F| / sum_k |G_k| bound_k is the
     force analogue of |phi_hat - phi| / sum_k |c_k| |AA_k|.
     """
-    P = np.asarray(P, dtype=np.float64)
+    P, inside = _inside(P, rc)
     r = np.linalg.norm(P, axis=1)
     Y, dYb = real_sph_harm(P, lmax, True, bound=True)
     R, dRb = radial(r, nmin, nmax, rc, True, bound=True)
@@ -171,7 +184,7 @@ def one_particle_grad_bound(P: np.ndarray, nmin: int, nmax: int, lmax: int, rc: 
     rhat = np.abs(P / r[:, None])
     g = (dRb[:, :, None, None] * np.abs(Y)[:, None, :, None] * rhat[:, None, None, :]
          + np.abs(R)[:, :, None, None] * dYb[:, None, :, :])
-    return g.reshape(P.shape[0], R.shape[1] * Y.shape[1], 3)
+    return g.reshape(P.shape[0], R.shape[1] * Y.shape[1], 3) * inside[:, None, None]
 
 
 def pool_A(P: np.ndarray, offsets: np.ndarray, nmin: int, nmax: int, lmax: int, rc: float,

@@ -210,3 +210,23 @@ def test_gradient_bound_pins_catch_planted_factors(old, new):
     finally:
         oracle.pooling.one_particle_grad_bound = orig_bound
         globals().update(saved)
+
+
+def test_cutoff_zero_continuation_is_c1_and_drops_the_neighbour():
+    """Neighbours at r >= rc or r = 0 contribute nothing.  The envelope's double root makes this the
+    C^1 continuation: R_n = O(eps^2) and dR_n/dr = O(eps) at r = rc(1 - eps), so phi_k and grad phi_k
+    of a neighbour just inside the cutoff are already within O(eps^2), O(eps) of the zero outside."""
+    rc = 5.0
+    for eps in (1e-2, 1e-3):
+        R, dR = radial(np.array([rc * (1 - eps)]), 1, 8, rc, with_grad=True)
+        assert np.all(np.abs(R) <= 1.01 * eps ** 2) and np.all(np.abs(dR) <= 2.01 * eps / rc * 8 ** 2)
+        u = unit(1, 7)
+        phi_in, g_in = one_particle(u * rc * (1 - eps), 1, 8, LMAX, rc, with_grad=True)
+        assert np.abs(phi_in).max() <= 2 * eps ** 2 and np.abs(g_in).max() <= 200 * eps
+    P = unit(5, 8) * np.array([1.0, 2.0, 4.0, 3.0, 2.5])[:, None]
+    extra = np.concatenate([P, unit(2, 9) * np.array([[rc], [1.5 * rc]]), np.zeros((1, 3))])
+    phi, g = one_particle(extra, 1, 8, LMAX, rc, with_grad=True)
+    assert np.all(phi[5:] == 0.0) and np.all(g[5:] == 0.0)
+    A = pool_A(P, np.array([0, 5]), 1, 8, LMAX, rc)
+    A2 = pool_A(extra, np.array([0, 8]), 1, 8, LMAX, rc)
+    assert np.array_equal(A, A2)
