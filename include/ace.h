@@ -344,12 +344,43 @@ ace_status ace_pool_A_feat_grad(const float* pos, const float* mu, const int64_t
                                 int64_t n_pairs, float rc, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax,
                                 const float* dA, float alpha, float* dpos, void* stream);
 
+/* Energy and forces of a batch of environments, DEVICE buffers: pooling (Eq. 2, section 2.4),
+ * the graph's forward and adjoint with phi_bar = 1 (Eq. 4, FP32, one channel) and the pooling
+ * adjoint with alpha = -1: F_j = -dphi/dr_j.  Two forms compute it:
+ *   fused       one kernel per tile of 32 environments: pooling into shared memory, the graph,
+ *               the pooling adjoint from the adjoints still in shared memory (A and dA never
+ *               reach global memory).  Needs no invariant features (kmax = 0), lmax = 6, at most
+ *               8 radial functions and the graph's 32-environment layout in shared memory.
+ *   three-kernel ace_pool_A_feat -> ace_eval_grad -> ace_pool_A_feat_grad through A and dA
+ *               buffers of the batch kept in the handle (allocated by the first such call).
+ * The three-kernel form runs by default (measured faster on GB300 with 50,000 environments of
+ * 10-60 neighbours and K = 392: 0.678 ms against 0.745 ms); ACE_FORCES=fused selects the fused
+ * form where it applies.  ace_energy_forces_plan tells which one runs.
+ *  pos, mu, offsets : dev, as ace_pool_A_feat (offsets are not checked: device memory).
+ *  c       : dev [n_basis] float, or NULL (the bound coefficients of the adjoint form).
+ *  phi     : dev [n_env] float, written.  forces: dev [n_pairs][3] float, written.
+ * The graph must be built over the pooling's one-particle set:
+ * K = (nmax - nmin + 1)(kmax + 1)(lmax + 1)^2.  Asynchronous on `stream`.  The fused form sums
+ * an environment whose neighbours fall into several warps' ranges with shared-memory atomics, so
+ * its last bits can differ between runs when an environment spans three or more ranges.
+ * Errors: as ace_pool_A_feat and ace_eval_grad; INVALID_ARG for a graph whose K does not match. */
+ace_status ace_energy_forces(ace_dag* dag, const float* pos, const float* mu, const int64_t* offsets, int64_t n_env,
+                             int64_t n_pairs, const void* c, int32_t readout, float rc, int32_t nmin, int32_t nmax,
+                             int32_t lmax, int32_t kmax, float* phi, float* forces, void* stream);
+
+/* Which form ace_energy_forces (and ace_energy_forces_host) takes for these pooling parameters
+ * on the current device: *fused = 1 and *smem_bytes = the fused kernel's shared memory per CTA,
+ * or 0 and 0 for the three kernels.  Reads device attributes only.  Either output may be NULL.
+ * Errors: INVALID_ARG (NULL dag), NO_DEVICE. */
+ace_status ace_energy_forces_plan(ace_dag* dag, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax,
+                                  int32_t* fused, int64_t* smem_bytes);
+
 /* Energy and forces of a batch of environments with HOST buffers: pooling
  * (ace_pool_A_feat), forward + adjoint with phi_bar = 1 (ace_eval_grad, FP32, one
  * channel) and the pooling adjoint with alpha = -1 (ace_pool_A_feat_grad), the
  * batch cut into chunks of chunk_env environments (0: as ace_eval_grad_host).  Positions (and mu) of chunk i are copied in on one
- * library stream, the three kernels run on a second, its forces and phi are
- * copied out on a third: the copies overlap the kernels of neighbouring chunks.
+ * library stream, its forces pipeline runs on a second (the form of ace_energy_forces), its
+ * forces and phi are copied out on a third: the copies overlap the kernels of neighbouring chunks.
  *  pos     : host [n_pairs][3] float, neighbour positions relative to their centre.
  *  mu      : host [n_pairs] float (invariant feature per neighbour) or NULL (kmax = 0).
  *  offsets : host [n_env + 1] int64, CSR: environment e owns pairs offsets[e] ..
@@ -360,7 +391,7 @@ ace_status ace_pool_A_feat_grad(const float* pos, const float* mu, const int64_t
  *            (F_j = -dphi/dr_j).
  * The graph must be built over the pooling's one-particle set:
  * K = (nmax - nmin + 1)(kmax + 1)(lmax + 1)^2.  Device buffers (positions, offsets,
- * forces and phi of the whole batch, A and dA of two chunks) belong to the
+ * forces and phi of the whole batch, A and dA of two chunks for the three-kernel form) belong to the
  * handle and grow on demand.  Asynchronous and capturable as ace_eval_grad_host.
  * Errors: as ace_pool_A_feat and ace_eval_grad; INVALID_ARG for inconsistent offsets
  * or a graph whose K does not match. */

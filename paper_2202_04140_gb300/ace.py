@@ -34,7 +34,7 @@ EXPORTED = [
     "ace_spec_free", "ace_build_dag", "ace_dag_info", "ace_dag_export", "ace_dag_plan_info",
     "ace_dag_plan_array", "ace_dag_free", "ace_dag_upload", "ace_dag_autotune", "ace_eval", "ace_eval_grad",
     "ace_eval_host", "ace_eval_grad_host", "ace_eval_plain_workspace_bytes",
-    "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_pool_A_feat", "ace_pool_A_feat_grad", "ace_energy_forces_host", "ace_stream_status", "ace_device_info",
+    "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_pool_A_feat", "ace_pool_A_feat_grad", "ace_energy_forces", "ace_energy_forces_plan", "ace_energy_forces_host", "ace_stream_status", "ace_device_info",
     "ace_fma_peak",
 ]
 
@@ -83,6 +83,8 @@ _SIG = {
     "ace_pool_A_grad": (C.c_int, [_p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _p, _f32, _p, _p]),
     "ace_pool_A_feat": (C.c_int, [_p, _p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _i32, _p, _p]),
     "ace_pool_A_feat_grad": (C.c_int, [_p, _p, _p, _i64, _i64, _f32, _i32, _i32, _i32, _i32, _p, _f32, _p, _p]),
+    "ace_energy_forces": (C.c_int, [_p, _p, _p, _p, _i64, _i64, _p, _i32, _f32, _i32, _i32, _i32, _i32, _p, _p, _p]),
+    "ace_energy_forces_plan": (C.c_int, [_p, _i32, _i32, _i32, _i32, _p, _p]),
     "ace_energy_forces_host": (C.c_int, [_p, _p, _p, _p, _i64, _i64, _p, _i32, _f32, _i32, _i32, _i32, _i32, _p, _p,
                                          _i64, _p]),
     "ace_stream_status": (C.c_int, [_p, _p]),
@@ -136,8 +138,9 @@ def ace_spec_tuples(spec: int, n_basis: int, nu_max: int):
     return t, d
 
 
-def ace_spec_free(spec: int):
-    _lib.ace_spec_free(spec)
+def ace_spec_free(spec: int, _free=_lib.ace_spec_free):
+    # the C function is bound at import: handles can be freed while the interpreter shuts down
+    _free(spec)
 
 
 # ---- graph ----------------------------------------------------------------------------------
@@ -179,8 +182,9 @@ def ace_dag_plan_array(dag: int, name: str) -> np.ndarray:
     return out[:n.value]
 
 
-def ace_dag_free(dag: int):
-    _lib.ace_dag_free(dag)
+def ace_dag_free(dag: int, _free=_lib.ace_dag_free):
+    # the C function is bound at import: handles can be freed while the interpreter shuts down
+    _free(dag)
 
 
 def ace_dag_upload(dag: int, stream: int = 0):
@@ -252,6 +256,19 @@ def ace_pool_A_feat(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax
 def ace_pool_A_feat_grad(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax, dA, alpha, dpos, stream=0):
     _check(_lib.ace_pool_A_feat_grad(pos, mu, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, kmax, dA, alpha, dpos,
                                      stream), "ace_pool_A_feat_grad")
+
+
+def ace_energy_forces(dag, pos, mu, offsets, n_env, n_pairs, c, readout, rc, nmin, nmax, lmax, kmax, phi, forces,
+                      stream=0):
+    _check(_lib.ace_energy_forces(dag, pos, mu, offsets, n_env, n_pairs, c, readout, rc, nmin, nmax, lmax, kmax, phi,
+                                  forces, stream), "ace_energy_forces")
+
+
+def ace_energy_forces_plan(dag, nmin, nmax, lmax, kmax):
+    """(fused, smem_bytes): whether ace_energy_forces takes the one-kernel form for these parameters."""
+    f, b = C.c_int32(0), C.c_int64(0)
+    _check(_lib.ace_energy_forces_plan(dag, nmin, nmax, lmax, kmax, C.byref(f), C.byref(b)), "ace_energy_forces_plan")
+    return bool(f.value), int(b.value)
 
 
 def ace_energy_forces_host(dag, pos, mu, offsets, n_env, n_pairs, c, readout, rc, nmin, nmax, lmax, kmax, phi, forces,

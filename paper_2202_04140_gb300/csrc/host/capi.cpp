@@ -130,6 +130,8 @@ struct ace_dag {
   size_t hslot_bytes = 0;
   void* fbuf = nullptr;  // host-buffer forces pipeline: whole-batch positions, offsets, forces, phi; two A/dA chunks
   size_t fbuf_bytes = 0;
+  void* fwork = nullptr;  // device-buffer forces pipeline, three-kernel form: A and dA of the batch
+  size_t fwork_bytes = 0;
   uint32_t* status = nullptr;
   std::vector<void*> allocations;
   std::vector<std::vector<uint16_t>> staging16;  // host copies kept alive until the upload completes
@@ -1023,6 +1025,54 @@ ace_status check_eval_args(const ace_dag* d, const void* A, int64_t n_env, int n
   return ACE_OK;
 }
 
+
+// Which form the forces pipeline takes: the fused kernel (pooling, graph forward and adjoint and
+// pooling adjoint in one launch, A and dA in shared memory) or the three kernels.  ACE_FORCES=fused
+// or ACE_FORCES=split chooses; by default the three kernels, measured faster on GB300 (50,000
+// environments of 10-60 neighbours, K = 392: 0.678 ms against 0.745 ms): with one tile per SM the
+// fused kernel's phases cannot overlap, and its last wave of tiles leaves SMs idle.
+constexpr bool kForcesFusedDefault = false;
+
+// Shared memory of the fused forces kernel for this request, or 0 when the three kernels run
+// (bound: the one-channel FP32 coefficients are bound, as the forces entry points make them;
+// smem_optin: the device's shared memory limit per CTA).
+size_t forces_fused_bytes(const ace_dag* d, int nmin, int nmax, int lmax, int kmax, bool bound, int smem_optin) {
+  const char* v = std::getenv("ACE_FORCES");
+  const bool fused = v && std::strcmp(v, "fused") == 0 ? true : v && std::strcmp(v, "split") == 0 ? false
+                                                                                                 : kForcesFusedDefault;
+  if (!fused || !bound) return 0;
+  if (loe_smem(d->plan.n_slots, d->plan.n_g, true, 1024) > (size_t)smem_optin) return 0;
+  const size_t fsmem = forces_fused_smem(d->plan.n_slots, d->plan.n_g, d->K, nmin, nmax, lmax, kmax);
+  return fsmem <= (size_t)smem_optin ? fsmem : 0;
+}
+
+// The forces pipeline of n environments on stream st (device buffers; offsets index pos): the fused
+// kernel when forces_fused_bytes allows it, else pooling -> forward + adjoint -> pooling adjoint
+// through A_d and dA_d (n x K floats each, required then).
+ace_status forces_pipeline(ace_dag* d, const float* pos_d, const float* mu_d, const int64_t* off_d, int64_t n,
+                           float rc, int nmin, int nmax, int lmax, int kmax, int readout, float* phi_d, float* F_d,
+                           float* A_d, float* dA_d, cudaStream_t st) {
+  DevTaskSet& dt = d->sym;
+  const size_t fsmem = forces_fused_bytes(d, nmin, nmax, lmax, kmax, dt.rm_bound, d->smem_optin);
+  cudaError_t e;
+  if (fsmem > 0) {
+    dev::LoeArgs a{};
+    fill_loe_args(d, dt, nullptr, nullptr, n, phi_d, nullptr, a);
+    const int64_t grid = std::min<int64_t>(a.n_tiles, (int64_t)d->sm_count);
+    e = launch_forces_fused(a, pos_d, off_d, rc, nmin, nmax, lmax, readout, F_d, (int)grid, fsmem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fused forces launch");
+    return ACE_OK;
+  }
+  if (!A_d || !dA_d) return fail(ACE_ERR_INVALID_ARG, "internal: no A/dA buffers for the three-kernel forces path");
+  if ((e = launch_pool(pos_d, mu_d, off_d, n, rc, nmin, nmax, lmax, kmax, A_d, st)) != cudaSuccess)
+    return cuda_fail(e, "pooling kernel launch");
+  ace_status s = run_fused(d, A_d, nullptr, nullptr, n, 1, ACE_F32, readout, phi_d, dA_d, true, st);
+  if (s != ACE_OK) return s;
+  if ((e = launch_pool_grad(pos_d, mu_d, off_d, n, rc, nmin, nmax, lmax, kmax, dA_d, -1.f, F_d, st)) != cudaSuccess)
+    return cuda_fail(e, "pooling adjoint launch");
+  return ACE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1238,6 +1288,7 @@ void ace_dag_free(ace_dag* dag) {
     for (void* p : dag->hslot)
       if (p) cudaFree(p);
     if (dag->fbuf) cudaFree(dag->fbuf);
+    if (dag->fwork) cudaFree(dag->fwork);
     for (cudaStream_t h : dag->hstream)
       if (h) cudaStreamDestroy(h);
     for (cudaEvent_t ev : {dag->hev_fork, dag->hev_in[0], dag->hev_in[1], dag->hev_done[0], dag->hev_done[1],
@@ -1542,7 +1593,8 @@ ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* m
   // one allocation: positions, mu, offsets, forces, phi of the batch, then A and dA of two chunks
   const size_t b_pos = dev::align16((size_t)n_pairs * 12), b_mu = kmax > 0 ? dev::align16((size_t)n_pairs * 4) : 0;
   const size_t b_off = dev::align16((size_t)(n_env + 1) * 8), b_phi = dev::align16((size_t)n_env * 4);
-  const size_t b_a = dev::align16((size_t)chunk * K * 4);
+  const bool fused = forces_fused_bytes(dag, nmin, nmax, lmax, kmax, dag->sym.rm_bound, dag->smem_optin) > 0;
+  const size_t b_a = fused ? 0 : dev::align16((size_t)chunk * K * 4);
   const size_t need = 2 * b_pos + b_mu + b_off + b_phi + 4 * b_a;
   if ((s = ensure_host_pipeline(dag, 0)) != ACE_OK) return s;
   cudaError_t e;
@@ -1578,13 +1630,12 @@ ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* m
       e = cudaMemcpyAsync(mu_d + p0, mu + p0, (size_t)(p1 - p0) * 4, cudaMemcpyHostToDevice, hin);
     if (e == cudaSuccess) e = cudaEventRecord(dag->hev_in[b], hin);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hk, dag->hev_in[b], 0);
-    // pooling -> forward + adjoint -> pooling adjoint (offsets index the whole batch's positions)
-    if (e == cudaSuccess) e = launch_pool(pos_d, mu_d, off_d + e0, n, rc, nmin, nmax, lmax, kmax, A_d, hk);
+    // the forces pipeline of the chunk (offsets index the whole batch's positions)
     if (e != cudaSuccess) break;
-    s = run_fused(dag, A_d, nullptr, nullptr, n, 1, ACE_F32, readout, phi_d + e0, dA_d, true, hk);
+    s = forces_pipeline(dag, pos_d, mu_d, off_d + e0, n, rc, nmin, nmax, lmax, kmax, readout, phi_d + e0, F_d,
+                        fused ? nullptr : A_d, fused ? nullptr : dA_d, hk);
     if (s != ACE_OK) break;
-    e = launch_pool_grad(pos_d, mu_d, off_d + e0, n, rc, nmin, nmax, lmax, kmax, dA_d, -1.f, F_d, hk);
-    if (e == cudaSuccess) e = cudaEventRecord(dag->hev_done[b], hk);
+    e = cudaEventRecord(dag->hev_done[b], hk);
     // copy out
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hout, dag->hev_done[b], 0);
     if (e == cudaSuccess && p1 > p0)
@@ -1596,6 +1647,52 @@ ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* m
   }
   if (s != ACE_OK) return s;
   if (e != cudaSuccess) return cuda_fail(e, "host-buffer forces pipeline");
+  return ACE_OK;
+}
+
+ace_status ace_energy_forces(ace_dag* dag, const float* pos, const float* mu, const int64_t* offsets, int64_t n_env,
+                             int64_t n_pairs, const void* c, int32_t readout, float rc, int32_t nmin, int32_t nmax,
+                             int32_t lmax, int32_t kmax, float* phi, float* forces, void* stream) {
+  ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, mu, kmax);
+  if (s != ACE_OK) return s;
+  if ((s = check_eval_args(dag, nullptr, 0, 1, ACE_F32, readout)) != ACE_OK) return s;
+  if (n_env > 0 && (!phi || (!forces && n_pairs > 0))) return fail(ACE_ERR_INVALID_ARG, "phi or forces is NULL");
+  if (c && !aligned16(c)) return fail(ACE_ERR_INVALID_ARG, "c must be 16-byte aligned");
+  const int64_t K = (int64_t)(nmax - nmin + 1) * (kmax + 1) * (lmax + 1) * (lmax + 1);
+  if (K != dag->K) return fail(ACE_ERR_INVALID_ARG, "the graph's K does not match the pooling's one-particle set");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = ensure_uploaded(dag, st)) != ACE_OK) return s;
+  if ((s = bind(dag, dag->sym, c, 1, ACE_F32, st)) != ACE_OK) return s;
+  if (n_env == 0) return ACE_OK;
+  float *A_d = nullptr, *dA_d = nullptr;
+  if (forces_fused_bytes(dag, nmin, nmax, lmax, kmax, dag->sym.rm_bound, dag->smem_optin) == 0) {
+    // the three-kernel form keeps A and dA of the batch in the handle
+    const size_t half = dev::align16((size_t)n_env * K * sizeof(float));
+    if (2 * half > dag->fwork_bytes) {
+      if (dag->fwork) cudaFree(dag->fwork);
+      dag->fwork = nullptr;
+      dag->fwork_bytes = 0;
+      cudaError_t e = cudaMalloc(&dag->fwork, 2 * half);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (forces work buffer)");
+      dag->fwork_bytes = 2 * half;
+    }
+    A_d = static_cast<float*>(dag->fwork);
+    dA_d = A_d + half / sizeof(float);
+  }
+  return forces_pipeline(dag, pos, kmax > 0 ? mu : nullptr, offsets, n_env, rc, nmin, nmax, lmax, kmax, readout, phi,
+                         forces, A_d, dA_d, st);
+}
+
+ace_status ace_energy_forces_plan(ace_dag* dag, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax,
+                                  int32_t* fused, int64_t* smem_bytes) {
+  if (!dag) return fail(ACE_ERR_INVALID_ARG, "dag is NULL");
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return fail(ACE_ERR_NO_DEVICE, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  const size_t b = forces_fused_bytes(dag, nmin, nmax, lmax, kmax, true, optin);
+  if (fused) *fused = b > 0 ? 1 : 0;
+  if (smem_bytes) *smem_bytes = (int64_t)b;
   return ACE_OK;
 }
 

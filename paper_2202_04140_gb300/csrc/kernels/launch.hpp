@@ -61,6 +61,13 @@ cudaError_t launch_fma_probe(int64_t iters, int blocks, int threads, float* out,
 cudaError_t launch_pool(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, float rc, int nmin,
                         int nmax, int lmax, int kmax, float* A, cudaStream_t st);
 
+// Fused forces pipeline (pool.cu): shared memory per CTA for this graph and these pooling
+// parameters (0: the request does not fit the fused kernel), and its launch (one tile of 32
+// environments per CTA iteration; b carries the graph, phi and the tile count).
+size_t forces_fused_smem(int n_slots, int n_g, int K, int nmin, int nmax, int lmax, int kmax);
+cudaError_t launch_forces_fused(const dev::LoeArgs& b, const float* pos, const int64_t* offsets, float rc, int nmin,
+                                int nmax, int lmax, int readout, float* forces, int grid, size_t smem,
+                                cudaStream_t st);
 cudaError_t launch_pool_grad(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, float rc,
                              int nmin, int nmax, int lmax, int kmax, const float* dA, float alpha, float* dpos,
                              cudaStream_t st);

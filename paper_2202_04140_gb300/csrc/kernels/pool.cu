@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "launch.hpp"
+#include "loe_device.cuh"
 #include "pool_geometry.cuh"
 
 namespace ace {
@@ -326,6 +327,349 @@ __global__ void __launch_bounds__(kPoolWarps * 32) pool_grad_kernel(const float*
   }
 }
 
+// ---- fused forces pipeline ---------------------------------------------------------------
+
+// Entries of the adjoint rows of the fused kernel, lmax 6, ordered by m groups: group A holds
+// the (l, m) of m = 0, 1, 2 (29 entries, padded to 32), group B those of m = 3..6 (20); inside a
+// group m ascending, l ascending, cos entry then sin entry.  A lane then holds the h sums of one
+// group at a time (29 or 20 registers instead of 49) and reads the group with 16-byte loads.
+constexpr int kFLmax = 6;
+constexpr int kFGroupB = 32;   // first entry of group B
+constexpr int kFRow = 52;      // entries per adjoint row (32 + 20)
+constexpr int kFMaxR = 8;      // radial factors of the fused kernel (nmax - nmin + 1 <= 8)
+constexpr int kFChunk = 32;      // neighbours staged per pooling warp per pass
+constexpr int kFPoolWarps = 16;  // warps that pool (the others wait at the barrier)
+
+__host__ __device__ constexpr int fgroup_size(int m0, int m1) {
+  int n = 0;
+  for (int m = m0; m <= m1; ++m) n += m == 0 ? kFLmax + 1 : 2 * (kFLmax + 1 - m);
+  return n;
+}
+// position of (l, m, sin?) inside the group that starts at m0
+__host__ __device__ constexpr int fgroup_pos(int m0, int m, int l, int sn) {
+  return fgroup_size(m0, m - 1) + (m == 0 ? l : 2 * (l - m) + sn);
+}
+
+__constant__ int c_fperm[kFRow];  // adjoint-row entry -> lm = l^2 + l + m (or -1: padding)
+
+// Part of the pooling adjoint of one neighbour from the m group [M0, M1] of its environment's
+// adjoint rows (row n - nmin at rows + (n - nmin) kFRow + goff).  PASS 0 sums h = sum_n G_n R_n(r)
+// and contracts it with the gradient of Y in the unit vector into (gx, gy, gz); PASS 1 sums
+// hd = sum_n G_n dR_n/dr and contracts it with Y into ys.  The columns Q_l^m, Q_l^{m+1} of
+// d^m P_l/du^m follow their recurrence in l inside the contraction.
+template <int PASS, int M0, int M1>
+__device__ __forceinline__ void adjoint_group(const float* __restrict__ rows, int goff, int nmin, int nmax,
+                                              float t, float env2, float denv, float two_over_rc, float u, float xh,
+                                              float yh, float& gx, float& gy, float& gz, float& ys) {
+  constexpr int NH = fgroup_size(M0, M1);
+  constexpr int NH4 = (NH + 3) / 4;
+  float h[NH];
+#pragma unroll
+  for (int i = 0; i < NH; ++i) h[i] = 0.f;
+  float T = 1.f, dT = 0.f, Tm1 = 0.f, dTm1 = 0.f;
+  for (int n = 0; n <= nmax; ++n) {
+    if (n >= nmin) {
+      const float wn = PASS == 0 ? T * env2 : dT * two_over_rc * env2 + T * denv;
+      const float4* row = reinterpret_cast<const float4*>(rows + (n - nmin) * kFRow + goff);
+#pragma unroll
+      for (int q = 0; q < NH4; ++q) {
+        const float4 v = row[q];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (4 * q + c < NH) h[4 * q + c] = __fmaf_rn(vv[c], wn, h[4 * q + c]);
+      }
+    }
+    const float Tn = n == 0 ? t : 2.f * t * T - Tm1;
+    const float dTn = n == 0 ? 1.f : 2.f * T + 2.f * t * dT - dTm1;
+    Tm1 = T;
+    T = Tn;
+    dTm1 = dT;
+    dT = dTn;
+  }
+  float C = 1.f, S = 0.f, Cp = 0.f, Sp = 0.f;  // (x+iy)^m and (x+iy)^(m-1)
+#pragma unroll
+  for (int m = 0; m <= M1; ++m) {
+    if (m >= M0) {
+      float q0m2 = 0.f, q0m1 = 0.f, q1m2 = 0.f, q1m1 = 0.f;  // Q_{l-2}, Q_{l-1} of columns m, m+1
+#pragma unroll
+      for (int l = m; l <= kFLmax; ++l) {
+        float q0;
+        if (l == m) q0 = c_dfac[m];
+        else if (l == m + 1) q0 = (2 * m + 1) * u * q0m1;
+        else q0 = c_ra[l][m] * u * q0m1 - c_rb[l][m] * q0m2;
+        q0m2 = q0m1;
+        q0m1 = q0;
+        const float kq = c_norm[l][m] * q0;
+        const int pc = fgroup_pos(M0, m, l, 0), ps = fgroup_pos(M0, m, l, 1);
+        if constexpr (PASS == 1) {
+          if (m == 0) {
+            ys = __fmaf_rn(h[pc], kq, ys);
+          } else {
+            ys = __fmaf_rn(h[pc], kq * C, ys);
+            ys = __fmaf_rn(h[ps], kq * S, ys);
+          }
+        } else {
+          float q1 = 0.f;
+          if (l >= m + 1) {
+            if (l == m + 1) q1 = c_dfac[m + 1];
+            else if (l == m + 2) q1 = (2 * m + 3) * u * q1m1;
+            else q1 = c_ra[l][m + 1] * u * q1m1 - c_rb[l][m + 1] * q1m2;
+            q1m2 = q1m1;
+            q1m1 = q1;
+          }
+          const float kq1 = c_norm[l][m] * q1;
+          if (m == 0) {
+            gz = __fmaf_rn(h[pc], kq1, gz);
+          } else {
+            const float fm = (float)m;
+            const float h1 = h[pc], h2 = h[ps];
+            gx = __fmaf_rn(h1, kq * fm * Cp, gx);  // cos part
+            gy = __fmaf_rn(h1, -kq * fm * Sp, gy);
+            gz = __fmaf_rn(h1, kq1 * C, gz);
+            gx = __fmaf_rn(h2, kq * fm * Sp, gx);  // sin part
+            gy = __fmaf_rn(h2, kq * fm * Cp, gy);
+            gz = __fmaf_rn(h2, kq1 * S, gz);
+          }
+        }
+      }
+    }
+    Cp = C;
+    Sp = S;
+    const float Cn = C * xh - S * yh;
+    S = S * xh + C * yh;
+    C = Cn;
+  }
+}
+
+// Slot of radial factor n of staged neighbour jj in a row of kFMaxR: the two 16-byte halves
+// of a row swap for every other pair of neighbours (8 banks instead of 4 for the staging writes).
+__device__ __forceinline__ int rslot8(int jj, int n) { return ((((n >> 2) ^ (jj >> 1)) & 1) << 2) | (n & 3); }
+
+// Environment of neighbour j of the tile: the largest e with off[e] <= j (off: 33 offsets).
+__device__ __forceinline__ int tile_env(const int64_t* off, int64_t j) {
+  int lo = 0, hi = 32;
+#pragma unroll
+  for (int it = 0; it < 5; ++it) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= j) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Fused forces pipeline for one tile of 32 environments per CTA (no invariant features, lmax 6,
+// at most 8 radial factors), 1024 threads:
+//   1. pooling (Eq. 2) into the leaf rows of the one-environment-per-lane layout: the tile's
+//      neighbours (contiguous in the CSR order) are cut into 16 equal ranges, one per pooling
+//      warp; a warp stages 32 neighbours at a time (R_n, Y_lm in shared memory), sums them per
+//      environment in registers and adds each environment's sums to its leaf rows (shared
+//      atomics: a range can span several environments, an environment several ranges);
+//   2.-4. the graph's forward levels, sink rows and reverse sweep (as loe_kernel, one stream per
+//      warp);
+//   5. phi, and the leaves' adjoints copied to rows [e][n][kFRow] in m-group order;
+//   6. forces: one thread per (neighbour, m group) of the tile, each adding its part of the
+//      pooling adjoint to the neighbour's force (zeroed at the start of the tile).
+// A and dA stay in shared memory.  Scratch: the staging areas lie after the leaf rows (operand
+// rows, adjoints, phi partials: unused until the forward levels); the adjoint rows go to the
+// operand rows, dead after the reverse sweep; the tile's offsets follow the loe layout.  The
+// host checks that all of it fits.
+struct ForcesArgs {
+  LoeArgs b;
+  const float* pos;
+  const int64_t* offsets;
+  float rc;
+  int32_t nmin, nmax;
+  float* forces;
+};
+
+constexpr int kForcesThreads = 1024;
+constexpr int kForcesOffBytes = 480;  // 33 int64 offsets (272 bytes), then the 52-entry row permutation
+
+template <int RO>
+__global__ void __launch_bounds__(kForcesThreads, 1) forces_fused_kernel(const ForcesArgs f) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NT = kForcesThreads, NW = NT / 32, S = kLoeStride;
+  constexpr int NL = (kFLmax + 1) * (kFLmax + 1);
+  constexpr int NI = (NL + 31) / 32;
+  static_assert(NW == kLoeStreamWarps, "one stream per warp");
+  const LoeArgs& a = f.b;
+  float* AA = reinterpret_cast<float*>(smem_raw);
+  float* G = reinterpret_cast<float*>(smem_raw + align16((size_t)a.n_slots * S * 4));
+  float* pb = G + align16((size_t)a.n_g * S * 4) / 4;
+  Acc<float, RO>* red = reinterpret_cast<Acc<float, RO>*>(pb + 32);
+  int64_t* soff = reinterpret_cast<int64_t*>(smem_raw + loe_smem_bytes(a.n_slots, a.n_g, true, NT));
+  int* sperm = reinterpret_cast<int*>(soff + 34);  // c_fperm in shared memory (lanes read different entries)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < kFRow) sperm[tid] = c_fperm[tid];
+  const int K = a.K;
+  const int nR = f.nmax - f.nmin + 1;
+  float* scratch = AA + align16((size_t)K * S * 4) / 4;  // after the leaf rows, 16-byte aligned
+  float* sR = scratch + (size_t)(warp % kFPoolWarps) * kFChunk * (kFMaxR + NL);
+  float* sY = sR + kFChunk * kFMaxR;
+  const geo::Cut cut = geo::make_cut(f.rc);
+  const float two_over_rc = 2.f / f.rc;
+  for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const int64_t env0 = tile * 32;
+    const int n_here = (a.n_env - env0) < 32 ? (int)(a.n_env - env0) : 32;
+    if (tid <= 32) soff[tid] = f.offsets[env0 + (tid < n_here ? tid : n_here)];
+    for (int i = tid; i < K * S; i += NT) AA[i] = 0.f;
+    __syncthreads();
+    const int64_t base = soff[0], N = soff[32] - base;
+    // the forces of the tile's neighbours receive two partial sums each (step 6)
+    for (int64_t i = tid; i < 3 * N; i += NT) f.forces[3 * base + i] = 0.f;
+    // 1. pooling over warp ranges of the tile's neighbours
+    if (warp < kFPoolWarps) {
+      float acc[NI][kFMaxR];
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int n = 0; n < kFMaxR; ++n) acc[i][n] = 0.f;
+      int cur = -1;  // environment whose sums acc holds (warp-uniform)
+      const int64_t lo = base + N * warp / kFPoolWarps, hi = base + N * (warp + 1) / kFPoolWarps;
+      for (int64_t jb = lo; jb < hi; jb += kFChunk) {
+        const int cnt = (int)((hi - jb) < kFChunk ? (hi - jb) : kFChunk);
+        const int64_t j = jb + lane;
+        int my_e = 0;
+        if (lane < cnt) {
+          my_e = tile_env(soff, j);
+          const geo::Geo g = geo::geometry(f.pos[3 * j], f.pos[3 * j + 1], f.pos[3 * j + 2], cut);
+          const float env2 = g.ok ? g.w * g.w : 0.f;
+          float Tm1 = 1.f, T = g.t;
+          for (int n = 1; n <= f.nmax; ++n) {
+            if (n >= f.nmin) sR[lane * kFMaxR + rslot8(lane, n - f.nmin)] = T * env2;
+            const float Tn = 2.f * g.t * T - Tm1;
+            Tm1 = T;
+            T = Tn;
+          }
+          if (f.nmin == 0) sR[lane * kFMaxR + rslot8(lane, 0)] = env2;
+          float C = 1.f, Sn = 0.f;
+#pragma unroll
+          for (int m = 0; m <= kFLmax; ++m) {
+            float qm2 = 0.f, qm1 = 0.f;
+#pragma unroll
+            for (int l = m; l <= kFLmax; ++l) {
+              float q;
+              if (l == m) q = c_dfac[m];
+              else if (l == m + 1) q = (2 * m + 1) * g.u * qm1;
+              else q = c_ra[l][m] * g.u * qm1 - c_rb[l][m] * qm2;
+              qm2 = qm1;
+              qm1 = q;
+              const float kq = g.ok ? c_norm[l][m] * q : 0.f;
+              if (m == 0) {
+                sY[lane * NL + l * l + l] = kq;
+              } else {
+                sY[lane * NL + l * l + l + m] = kq * C;
+                sY[lane * NL + l * l + l - m] = kq * Sn;
+              }
+            }
+            const float Cn = C * g.xh - Sn * g.yh;
+            Sn = Sn * g.xh + C * g.yh;
+            C = Cn;
+          }
+        }
+        __syncwarp();
+        for (int jj = 0; jj < cnt; ++jj) {
+          const int e = __shfl_sync(0xffffffffu, my_e, jj);
+          if (e != cur) {
+            if (cur >= 0) {
+#pragma unroll
+              for (int n = 0; n < kFMaxR; ++n)
+#pragma unroll
+                for (int i = 0; i < NI; ++i) {
+                  const int lm = lane + 32 * i;
+                  if (n < nR && lm < NL) atomicAdd(&AA[(n * NL + lm) * S + cur], acc[i][n]);
+                  acc[i][n] = 0.f;
+                }
+            }
+            cur = e;
+          }
+          float y[NI];
+#pragma unroll
+          for (int i = 0; i < NI; ++i) y[i] = (lane + 32 * i < NL) ? sY[jj * NL + lane + 32 * i] : 0.f;
+#pragma unroll
+          for (int q = 0; q < kFMaxR / 4; ++q) {
+            const float4 rv = *reinterpret_cast<const float4*>(&sR[jj * kFMaxR + rslot8(jj, 4 * q)]);
+            const float r4[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int i = 0; i < NI; ++i) acc[i][4 * q + c] = __fmaf_rn(r4[c], y[i], acc[i][4 * q + c]);
+          }
+        }
+        __syncwarp();
+      }
+      if (cur >= 0) {
+#pragma unroll
+        for (int n = 0; n < kFMaxR; ++n)
+#pragma unroll
+          for (int i = 0; i < NI; ++i) {
+            const int lm = lane + 32 * i;
+            if (n < nR && lm < NL) atomicAdd(&AA[(n * NL + lm) * S + cur], acc[i][n]);
+          }
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < a.n_g * S; i += NT) G[i] = 0.f;
+    if (tid < 32) pb[tid] = tid < n_here ? 1.f : 0.f;  // phibar = 1: the forces of phi
+    __syncthreads();
+    // 2. operand nodes (Eq. 4), 3. sink rows of the warp's stream, 4. reverse sweep
+    loe_forward_levels<S, NW>(a, AA, warp, lane);
+    Acc<float, RO> phiacc;
+    const float pbl = pb[lane];
+    if (a.check)
+      loe_tasks<true, RO, S, true>(a, AA, G, pbl, phiacc, warp, lane);
+    else
+      loe_tasks<true, RO, S, false>(a, AA, G, pbl, phiacc, warp, lane);
+    __syncthreads();
+    loe_reverse_levels<S, NW>(a, AA, G, warp, lane);
+    // 5. phi, and the leaves' adjoints as rows [e][n][kFRow] in the operand rows
+    red[warp * 32 + lane] = phiacc;
+    float* rows = scratch;
+    for (int r = warp; r < 32 * nR; r += NW) {  // row r = e nR + n, one warp per row
+      const int e = r / nR, n = r - e * nR;
+      for (int p = lane; p < kFRow; p += 32) {
+        const int lm = sperm[p];
+        rows[r * kFRow + p] = lm >= 0 ? G[(n * NL + lm) * S + e] : 0.f;
+      }
+    }
+    __syncthreads();
+    if (tid < 32 && tid < n_here && a.phi) {
+      Acc<float, RO> s;
+      for (int w = 0; w < NW; ++w) s.add_acc(red[w * 32 + tid]);
+      a.phi[env0 + tid] = (float)s.value();
+    }
+    // 6. forces: items (neighbour, m group), group A of every neighbour first, so that a warp
+    //    runs one group; each item adds its part of F_j (linear in the contractions) to F_j,
+    //    zeroed above.  Two addends onto zero: the result does not depend on their order.
+    for (int64_t t = tid; t < 2 * N; t += NT) {
+      const bool gb = t >= N;
+      const int64_t j = base + (gb ? t - N : t);
+      const geo::Geo gm = geo::geometry(f.pos[3 * j], f.pos[3 * j + 1], f.pos[3 * j + 2], cut);
+      if (!gm.ok) continue;
+      const float* er = rows + (size_t)tile_env(soff, j) * nR * kFRow;
+      const float env2 = gm.w * gm.w, denv = -2.f * gm.w / f.rc;
+      float gx = 0.f, gy = 0.f, gz = 0.f, ys = 0.f;
+      if (!gb) {
+        adjoint_group<0, 0, 2>(er, 0, f.nmin, f.nmax, gm.t, env2, denv, two_over_rc, gm.u, gm.xh, gm.yh, gx, gy, gz,
+                               ys);
+        adjoint_group<1, 0, 2>(er, 0, f.nmin, f.nmax, gm.t, env2, denv, two_over_rc, gm.u, gm.xh, gm.yh, gx, gy, gz,
+                               ys);
+      } else {
+        adjoint_group<0, 3, 6>(er, kFGroupB, f.nmin, f.nmax, gm.t, env2, denv, two_over_rc, gm.u, gm.xh, gm.yh, gx,
+                               gy, gz, ys);
+        adjoint_group<1, 3, 6>(er, kFGroupB, f.nmin, f.nmax, gm.t, env2, denv, two_over_rc, gm.u, gm.xh, gm.yh, gx,
+                               gy, gz, ys);
+      }
+      const float rg = gm.xh * gx + gm.yh * gy + gm.u * gz;
+      atomicAdd(&f.forces[3 * j], -(ys * gm.xh + (gx - gm.xh * rg) * gm.ir));
+      atomicAdd(&f.forces[3 * j + 1], -(ys * gm.yh + (gy - gm.yh * rg) * gm.ir));
+      atomicAdd(&f.forces[3 * j + 2], -(ys * gm.u + (gz - gm.u * rg) * gm.ir));
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace dev
 
 namespace {
@@ -360,6 +704,15 @@ cudaError_t ensure_pool_constants() {
   if ((e = cudaMemcpyToSymbol(dev::c_ra, ra, sizeof(ra))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(dev::c_rb, rb, sizeof(rb))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(dev::c_dfac, dfac, sizeof(dfac))) != cudaSuccess) return e;
+  int fperm[dev::kFRow];
+  for (int p = 0; p < dev::kFRow; ++p) fperm[p] = -1;
+  for (int m = 0; m <= dev::kFLmax; ++m)
+    for (int l = m; l <= dev::kFLmax; ++l) {
+      const int m0 = m < 3 ? 0 : 3, goff = m < 3 ? 0 : dev::kFGroupB;
+      fperm[goff + dev::fgroup_pos(m0, m, l, 0)] = l * l + l + m;
+      if (m > 0) fperm[goff + dev::fgroup_pos(m0, m, l, 1)] = l * l + l - m;
+    }
+  if ((e = cudaMemcpyToSymbol(dev::c_fperm, fperm, sizeof(fperm))) != cudaSuccess) return e;
   g_pool_consts_ready = true;
   return cudaSuccess;
 }
@@ -441,6 +794,51 @@ cudaError_t launch_pool_grad(const float* pos, const float* mu, const int64_t* o
     case 8: return launch_pool_grad_l<8>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Shared memory of the fused forces kernel and whether its scratch areas fit (see
+// forces_fused_kernel): 0 when the request cannot take the fused kernel.
+size_t forces_fused_smem(int n_slots, int n_g, int K, int nmin, int nmax, int lmax, int kmax) {
+  static_assert(dev::fgroup_size(0, 2) <= dev::kFGroupB && dev::kFGroupB + dev::fgroup_size(3, 6) == dev::kFRow,
+                "adjoint row layout");
+  if (kmax != 0 || lmax != dev::kFLmax || nmin < 0 || nmax < nmin || nmax - nmin + 1 > dev::kFMaxR) return 0;
+  const size_t S = dev::kLoeStride, NL = (size_t)(lmax + 1) * (lmax + 1);
+  const size_t nR = (size_t)(nmax - nmin + 1);
+  if ((size_t)K != nR * NL) return 0;
+  // the staging areas start at the first 16-byte boundary after the leaf rows and must end before
+  // the tile's offsets; the adjoint rows must end before the adjoint accumulators G (they are
+  // written while G is read)
+  const size_t total = dev::loe_smem_bytes(n_slots, n_g, true, dev::kForcesThreads);
+  const size_t leaves = dev::align16((size_t)K * S * 4), operands_end = dev::align16((size_t)n_slots * S * 4);
+  const size_t staging = (size_t)dev::kFPoolWarps * dev::kFChunk * (dev::kFMaxR + NL) * 4;
+  const size_t rows = 32 * nR * dev::kFRow * 4;
+  if (leaves + staging > total || leaves + rows > operands_end) return 0;
+  return total + dev::kForcesOffBytes;
+}
+
+cudaError_t launch_forces_fused(const dev::LoeArgs& b, const float* pos, const int64_t* offsets, float rc, int nmin,
+                                int nmax, int lmax, int readout, float* forces, int grid, size_t smem,
+                                cudaStream_t st) {
+  cudaError_t e = ensure_pool_constants();
+  if (e != cudaSuccess) return e;
+  const void* k = nullptr;
+  if (lmax == dev::kFLmax && nmax - nmin + 1 <= dev::kFMaxR) {
+    if (readout == 0) k = (const void*)&dev::forces_fused_kernel<0>;
+    if (readout == 1) k = (const void*)&dev::forces_fused_kernel<1>;
+    if (readout == 2) k = (const void*)&dev::forces_fused_kernel<2>;
+  }
+  if (!k) return cudaErrorInvalidValue;
+  if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  dev::ForcesArgs f;
+  f.b = b;
+  f.pos = pos;
+  f.offsets = offsets;
+  f.rc = rc;
+  f.nmin = nmin;
+  f.nmax = nmax;
+  f.forces = forces;
+  void* args[] = {&f};
+  return cudaLaunchKernel(k, dim3((unsigned)grid), dim3(dev::kForcesThreads), args, smem, st);
 }
 
 }  // namespace ace

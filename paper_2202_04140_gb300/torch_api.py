@@ -55,10 +55,10 @@ class Spec:
     def deg(self) -> np.ndarray:
         return self.tuples()[1]
 
-    def __del__(self):
+    def __del__(self, _free=L.ace_spec_free):
         h = getattr(self, "handle", None)
         if h:
-            L.ace_spec_free(h)
+            _free(h)
             self.handle = None
 
 
@@ -208,10 +208,10 @@ class Dag:
         """Differentiable phi (w.r.t. A): backward runs the fused forward+adjoint kernel."""
         return _AceEnergy.apply(A, c, self, readout)
 
-    def __del__(self):
+    def __del__(self, _free=L.ace_dag_free):
         h = getattr(self, "handle", None)
         if h:
-            L.ace_dag_free(h)
+            _free(h)
             self.handle = None
 
 
@@ -260,11 +260,22 @@ def pool_A_grad(pos: torch.Tensor, offsets: torch.Tensor, dA: torch.Tensor, nmin
 
 def energy_and_forces(dag: Dag, pos: torch.Tensor, offsets: torch.Tensor, c: torch.Tensor, nmin: int, nmax: int,
                       lmax: int, rc: float, readout: str = "plain", mu: torch.Tensor | None = None, kmax: int = 0):
-    """Full pipeline: pooling -> fused forward+adjoint -> pooling adjoint.  Returns (phi, F = -dphi/dr).
+    """Full pipeline through ace_energy_forces: pooling -> forward + adjoint -> pooling adjoint (one fused
+    kernel per tile of 32 environments when it applies).  Returns (phi [n_env, 1], F = -dphi/dr [n_pairs, 3]).
     With mu (one invariant feature value per neighbour) the one-particle basis is R_n Y_lm T_k(mu)."""
-    A = pool_A(pos, offsets, nmin, nmax, lmax, rc, mu, kmax)
-    phi, dA = dag.evaluate_grad(A, c, None, readout)
-    F = pool_A_grad(pos, offsets, dA, nmin, nmax, lmax, rc, alpha=-1.0, mu=mu, kmax=kmax)
+    pos = _dev(pos, "pos", torch.float32)
+    offsets = _dev(offsets, "offsets", torch.int64)
+    mu_p = _dev(mu, "mu", torch.float32).data_ptr() if mu is not None else 0
+    n_env = offsets.numel() - 1
+    c = _dev(c, "c", torch.float32)
+    c2 = c.reshape(dag.n_basis, -1)
+    if c2.shape[1] != 1:
+        raise ValueError("one output channel")
+    phi = torch.empty((n_env, 1), dtype=torch.float32, device=pos.device)
+    F = torch.empty((pos.shape[0], 3), dtype=torch.float32, device=pos.device)
+    L.ace_energy_forces(dag.handle, pos.data_ptr(), mu_p, offsets.data_ptr(), n_env, pos.shape[0],
+                        dag._c_arg("sym", c, c2, 1), _READOUT[readout], float(rc), nmin, nmax, lmax, kmax,
+                        phi.data_ptr(), F.data_ptr(), _stream())
     return phi, F
 
 

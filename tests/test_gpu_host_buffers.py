@@ -138,7 +138,9 @@ def test_forces_host_matches_oracle(dev, chunk):
     phi, F = energy_and_forces_host(d, P32.pin_memory(), off.pin_memory(), cd, w.nmin, w.nmax, w.lmax, w.rc,
                                     chunk_env=chunk)
     phi_d, F_d = energy_and_forces(d, P32.to(dev), off.to(dev), cd, w.nmin, w.nmax, w.lmax, w.rc)
-    assert torch.equal(phi, phi_d.reshape(-1).cpu())
+    # chunks cut the batch into other tiles than one call does (the fused kernel's pooling sums
+    # each tile's neighbours in warp ranges): equal up to the order of the FP32 sums
+    assert torch.allclose(phi, phi_d.reshape(-1).cpu(), rtol=1e-5, atol=1e-7)
     A = pool_A(P, offsets, w.nmin, w.nmax, w.lmax, w.rc)
     Aabs = abs_pool(P, offsets, w)
     assert normalized_error(phi.numpy()[:, None], phi_naive(A, o, c), error_scale(Aabs, o, c)) < TOL32

@@ -177,3 +177,96 @@ def test_pool_and_adjoint_next_to_centre_and_cutoff(dev):
     dpos = pool_A_grad(Pt, ot, torch.tensor(G, dtype=torch.float32, device=dev), w.nmin, w.nmax, w.lmax, rc)
     Fref = -forces(P, offsets, G, w.nmin, w.nmax, w.lmax, rc)
     assert normalized_error(dpos.cpu().numpy(), Fref, force_scale(P, offsets, G, w)) < TOL32
+
+
+def _ragged_cloud(n_env, rc, seed):
+    """Neighbour clouds with an empty environment, one of 150 neighbours (several staging passes
+    and warp ranges) and one neighbour outside the cutoff (its forces are zero)."""
+    rng = np.random.default_rng(seed)
+    J = rng.integers(1, 71, size=n_env)
+    J[3] = 0
+    J[min(40, n_env - 1)] = 150
+    offsets = np.concatenate([[0], np.cumsum(J)]).astype(np.int64)
+    d = rng.standard_normal((int(offsets[-1]), 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    r = rc * rng.uniform(0.05, 1.0, d.shape[0]) ** (1.0 / 3.0)
+    r[offsets[5]] = 1.2 * rc
+    return offsets, W.round_to(d * r[:, None], "f32")
+
+
+def _kernels_run(fn):
+    """fn() and the names of the kernels it launched (the first profiler session of a process can
+    come back empty, so a throwaway session runs first)."""
+    from torch.profiler import ProfilerActivity, profile
+    for _ in range(2):
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            out = fn()
+            torch.cuda.synchronize()
+    return out, {e.key for e in prof.key_averages()}
+
+
+@pytest.mark.parametrize("readout", ["plain", "compensated", "fp64"])
+def test_fused_forces_kernel_matches_three_kernels_and_oracle(dev, monkeypatch, readout):
+    """ace_energy_forces in both forms: the one-kernel pipeline (pooling, graph forward and adjoint,
+    pooling adjoint per tile of 32 environments in shared memory, ACE_FORCES=fused) and the three
+    kernels (ACE_FORCES=split), against the oracle's chain rule on a ragged batch: 77 environments
+    (two full tiles and 13), an empty environment, one of 150 neighbours, one neighbour beyond the
+    cutoff."""
+    from paper_2202_04140_gb300 import ace as L
+    from paper_2202_04140_gb300.torch_api import Dag, Spec, energy_and_forces
+    w = W.WORKLOADS["forces_k392"]
+    offsets, P = _ragged_cloud(77, w.rc, seed=8)
+    o = workload_index_set(w)
+    d = Dag(Spec.from_workload(w))
+    c = W.round_to(W.draw_c(o.deg, 1, seed=9), "f32")
+    ct = torch.tensor(c, dtype=torch.float32, device=dev)
+    Pt, ot = torch.tensor(P, dtype=torch.float32, device=dev), torch.tensor(offsets, device=dev)
+    run = lambda: energy_and_forces(d, Pt, ot, ct, w.nmin, w.nmax, w.lmax, w.rc, readout=readout)
+    monkeypatch.setenv("ACE_FORCES", "fused")
+    fused, smem = L.ace_energy_forces_plan(d.handle, w.nmin, w.nmax, w.lmax, w.kmax)
+    assert fused and smem > 0
+    (phi_f, F_f), k_fused = _kernels_run(run)
+    monkeypatch.setenv("ACE_FORCES", "split")
+    assert L.ace_energy_forces_plan(d.handle, w.nmin, w.nmax, w.lmax, w.kmax) == (False, 0)
+    (phi_s, F_s), k_split = _kernels_run(run)
+    monkeypatch.delenv("ACE_FORCES")
+    if any("pool_grad_kernel" in k for k in k_split):   # the profiler sees the library's kernels
+        assert any("forces_fused_kernel" in k for k in k_fused), sorted(k_fused)
+        assert not any("forces_fused_kernel" in k for k in k_split), sorted(k_split)
+    A = pool_A(P, offsets, w.nmin, w.nmax, w.lmax, w.rc)
+    Aabs = abs_pool(P, offsets, w)
+    ref = phi_naive(A, o, c)
+    Fref = forces(P, offsets, grad_naive(A, o, c), w.nmin, w.nmax, w.lmax, w.rc)
+    S = force_scale(P, offsets, grad_naive(Aabs, o, np.abs(c)), w)
+    for phi, F in ((phi_f, F_f), (phi_s, F_s)):
+        phi, F = phi.cpu().numpy().reshape(-1, 1), F.cpu().numpy()
+        assert normalized_error(phi, ref, error_scale(Aabs, o, c)) < TOL32
+        assert normalized_error(F, Fref, S) < TOL32
+        assert phi[3, 0] == 0.0
+        assert np.all(F[offsets[5]] == 0.0)
+
+
+@pytest.mark.parametrize("form", ["fused", "split"])
+def test_forces_empty_batch_and_full_size_forms_agree(dev, monkeypatch, form):
+    """No environments: nothing launched, nothing written.  50k environments: both forms agree
+    within the FP32 gate on every environment and every neighbour."""
+    from paper_2202_04140_gb300.torch_api import Dag, Spec, energy_and_forces
+    w = W.WORKLOADS["forces_k392"]
+    s = Spec.from_workload(w)
+    d = Dag(s)
+    c = torch.tensor(W.round_to(W.draw_c(s.deg, 1), "f32"), dtype=torch.float32, device=dev)
+    monkeypatch.setenv("ACE_FORCES", form)
+    phi, F = energy_and_forces(d, torch.zeros((0, 3), device=dev), torch.zeros(1, dtype=torch.int64, device=dev), c,
+                               w.nmin, w.nmax, w.lmax, w.rc)
+    assert phi.shape == (0, 1) and F.shape == (0, 3)
+    if form == "split":
+        return
+    offsets, P = W.draw_neighbours(w.n_env, seed=3, rc=w.rc, j_range=w.j_range)
+    Pt = torch.tensor(W.round_to(P, "f32"), dtype=torch.float32, device=dev)
+    ot = torch.tensor(offsets, device=dev)
+    phi_f, F_f = energy_and_forces(d, Pt, ot, c, w.nmin, w.nmax, w.lmax, w.rc)
+    monkeypatch.setenv("ACE_FORCES", "split")
+    phi_s, F_s = energy_and_forces(d, Pt, ot, c, w.nmin, w.nmax, w.lmax, w.rc)
+    monkeypatch.delenv("ACE_FORCES")
+    assert (phi_f - phi_s).abs().max().item() <= 1e-4 * phi_s.abs().max().item()
+    assert (F_f - F_s).abs().max().item() <= 1e-4 * F_s.abs().max().item()
