@@ -320,8 +320,17 @@ class Step:
             return self.dag.evaluate_grad(x, self.c, None, self.readout)
         return self.dag.evaluate(x, self.c, self.readout), None
 
+    def forces_form(self):
+        """'fused' (one kernel per tile) or 'three kernels': the form ace_energy_forces takes here."""
+        from paper_2202_04140_gb300 import ace as L
+        w = self.w
+        fused, _ = L.ace_energy_forces_plan(self.dag.handle, w.nmin, w.nmax, w.lmax, w.kmax)
+        return "fused" if fused else "three kernels"
+
     def launches_per_step(self):
-        return 3 if self.w.pooling else 1
+        if not self.w.pooling:
+            return 1
+        return 1 if self.forces_form() == "fused" else 3
 
     def capture(self):
         """One CUDA graph per buffer set (the step's launches, outputs in the graph's pool)."""
@@ -592,7 +601,8 @@ def main():
                        "n_nodes": dag.n_nodes, "n_aux": dag.n_aux, "n_operands": dag.n_operands,
                        "n_sinks": dag.n_sinks, "mode": mode, "readout": args.readout,
                        "graph": {"algorithm": args.algo, **({"n": args.n_split} if args.algo == 2 else {})},
-                       "kernel_config": {"kernel": tuned["kernel"], "E": tuned["E"], "by": "autotuner"},
+                       "kernel_config": {"kernel": tuned["kernel"], "E": tuned["E"], "by": "autotuner",
+                                         **({"forces_form": step.forces_form()} if w.pooling else {})},
                        "launch": "direct" if args.no_graph else "CUDA graph replay (one graph per buffer set)",
                        "l2": f"inputs larger than L2: {n_sets} rotating buffer sets of {per_set / 1e6:.0f} MB"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_flops / 1e12, "unit": "TFLOP/s",
