@@ -144,6 +144,14 @@ __device__ __forceinline__ void loe_tasks(const LoeArgs& a, float* AA, float* G,
   const int4* p = a.stream + a.wbeg[warp];
   const int4* const pend = a.stream + a.wbeg[warp + 1];
   if (p >= pend) return;
+  if constexpr (S == 32) {
+    // global-workspace variant: the warp's whole stream is requested into L2 at once, so that its
+    // sequential reads do not wait on the workspace traffic that evicts it
+    if (lane == 0)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)),
+                   "r"((unsigned)((pend - p) * (int)sizeof(int4)))
+                   : "memory");
+  }
   int4 h = __ldg(p);
   int4 cur[kPairBatch];
 #pragma unroll
