@@ -19,9 +19,8 @@ Contents (each function cites the passage of the paper it follows):
                                                       (Eq. 2, section 2.4)
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
-brute force, the paper's closed forms or identities of the mathematics, except
-the O(3) auxiliary-node counts of Algorithm 1, for which the paper prints no
-number (its figures carry no data): that count is "parity unpinned" beyond the
-structural invariants and the torus closed form of Theorem 3.2(ii), which
-exercises the same builder.
+brute force, the paper's closed forms, graphs worked out by hand from the
+algorithms' steps, or identities of the mathematics.  The O(3) auxiliary-node
+counts of the larger workloads have no printed value in the paper (its figures
+carry no data); they are outputs of the pinned graph builder.
 """
