@@ -190,13 +190,14 @@ ace_status ace_dag_upload(ace_dag* dag, void* stream);
  * memory (FP32, one channel, graph small enough); a tile of E environments per
  * CTA with the stored values in shared memory (any dtype and n_out, up to
  * 65535 stored values per environment); and, for graphs whose stored values do
- * not fit on chip (e.g. millions of basis functions), one environment per lane
- * with the stored values in a global-memory workspace of
- * grid x (n_slots + n_g) x 32 floats, allocated by the first such call and kept
- * in the graph handle (FP32, one channel); for FP32 forward requests with several
+ * not fit on chip (e.g. millions of basis functions), the stored values in a
+ * global-memory workspace allocated by the first such call and kept in the graph
+ * handle (FP32, one channel): by default two environments per lane, 64 per CTA,
+ * grid x (n_slots + n_g) x 64 floats, or one environment per lane, 32 per CTA,
+ * grid x (n_slots + n_g) x 32 floats; for FP32 forward requests with several
  * channels, one environment per lane with the stored values in that workspace and
- * each entry's coefficient row read once per warp.  ACE_KERNEL=lon|loe|loeg|loem
- * forces one.
+ * each entry's coefficient row read once per warp.  ACE_KERNEL=lon|loe|loeg|loeg2|loem
+ * forces one (loeg2: two environments per lane).
  * Errors: INVALID_ARG (null/misaligned pointer, n_env < 0, n_out), UNSUPPORTED,
  * NO_DEVICE, CUDA, OOM.  n_env = 0 is a no-op. */
 ace_status ace_eval(ace_dag* dag, const void* A, const void* c, int64_t n_env, int32_t n_out,
@@ -244,7 +245,8 @@ ace_status ace_eval_grad_host(ace_dag* dag, const void* A, const void* c, const 
 
 /* Autotuner (not in the paper): time every compiled kernel configuration for
  * this request — the one-environment-per-lane kernel with its stored values in
- * shared memory and in a global workspace, its several-channel forward form, and
+ * shared memory and in a global workspace (one or two environments per lane), its
+ * several-channel forward form, and
  * the tile-per-lane kernel with each tile size E of 1, 2, 4, 8, 16 environments — on n_env
  * environments of small constant inputs, and keep the fastest in the graph handle; later
  * ace_eval / ace_eval_grad calls with the same dtype, n_out and mode use it.
@@ -252,9 +254,10 @@ ace_status ace_eval_grad_host(ace_dag* dag, const void* A, const void* c, const 
  * and leaves no coefficients bound.  best_kind (1 tile per lane, 2 one
  * environment per lane, 3 one environment per lane with the global workspace,
  * 4 one environment per lane with several channels: FP32 forward, n_out > 1,
- * stored values in the global workspace, coefficient rows read once per warp),
- * best_E and best_ms (mean of 3 launches) may be NULL.
- * Environment variables ACE_KERNEL=lon|loe|loeg|loem and ACE_TILE_E=<E> override both
+ * stored values in the global workspace, coefficient rows read once per warp,
+ * 5 two environments per lane with the global workspace), best_E and best_ms
+ * (mean of 3 launches) may be NULL.
+ * Environment variables ACE_KERNEL=lon|loe|loeg|loeg2|loem and ACE_TILE_E=<E> override both
  * the tuned and the default choice.  Errors: as ace_eval, UNSUPPORTED when no
  * configuration runs. */
 ace_status ace_dag_autotune(ace_dag* dag, int64_t n_env, int32_t n_out, int32_t dtype, int32_t grad, int32_t readout,

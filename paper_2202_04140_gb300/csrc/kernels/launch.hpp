@@ -29,6 +29,12 @@ cudaError_t launch_bind_loe(const float* c, const int4* tasks, const int32_t* to
                             const int32_t* ebasis, const uint8_t* ew2, const int32_t* slot_basis,
                             const int32_t* hpos, int32_t n_tasks, int4* stream, cudaStream_t st);
 
+// Two environments per lane, global workspace (loe_wide.cu): kernel, shared memory, workspace
+// bytes per CTA (64 environments).
+const void* loe_wide_kernel_ptr(bool grad, int readout, int* nt);
+size_t loe_wide_smem(int nt);
+size_t loe_wide_bytes_per_cta(int n_slots, int n_g, bool grad);
+
 // Several channels, one environment per lane (loe_multi.cu, forward only): kernel, shared
 // memory, launch with the index-bound streams and the coefficient table c[n_basis][16].
 const void* loe_multi_kernel_ptr(int readout, int* nt);

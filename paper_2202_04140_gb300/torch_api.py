@@ -87,7 +87,8 @@ class Dag:
         kind, E, ms = L.ace_dag_autotune(self.handle, n_env, n_out, _DTYPE[dtype], grad, _READOUT[readout],
                                          _stream())
         self._bound.clear()          # the tuner leaves no coefficients bound
-        names = {1: "tile_per_lane", 2: "env_per_lane", 3: "env_per_lane_global", 4: "env_per_lane_multi"}
+        names = {1: "tile_per_lane", 2: "env_per_lane", 3: "env_per_lane_global", 4: "env_per_lane_multi",
+                 5: "env_pair_per_lane_global"}
         return {"kernel": names[kind], "E": E, "ms": ms}
 
     def _c_arg(self, mode: str, c: torch.Tensor, c2: torch.Tensor, n_out: int) -> int:

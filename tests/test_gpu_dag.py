@@ -83,7 +83,7 @@ def test_fwd_grad_k392_fp64(dev, n_out):
 
 # ---- FP32: the forward + adjoint workload (K = 392, nu <= 4, D = 16, 4096 environments) ---------
 
-@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg"])
+@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg", "loeg2"])
 @pytest.mark.parametrize("readout", ["plain", "compensated", "fp64"])
 def test_fwd_grad_k392_fp32_all_envs(dev, readout, kernel, monkeypatch):
     """Both fused kernels (tiles of tasks per lane, and one environment per lane) on every environment."""
@@ -120,7 +120,7 @@ def test_fwd_grad_k392_autograd_and_finite_differences(dev):
         assert abs(fd - g32[ei, k]) <= TOL32 * gscale[ei, k] + 1e-7 * abs(fd)
 
 
-@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg"])
+@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg", "loeg2"])
 def test_coefficient_rebinding_and_edge_sizes(dev, kernel, monkeypatch):
     """n_env = 0 is a no-op; n_env = 1 and ragged tiles; c bound once then reused; new c rebinds."""
     monkeypatch.setenv("ACE_KERNEL", kernel)
@@ -154,7 +154,7 @@ def test_coefficient_rebinding_and_edge_sizes(dev, kernel, monkeypatch):
     assert normalized_error(phi3.cpu().numpy(), phi_naive(A32, o, c32), error_scale(A32, o, c32)) < TOL32
 
 
-@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg"])
+@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg", "loeg2"])
 def test_checked_mode_status_word(dev, monkeypatch, kernel):
     """Bounds-checked kernels run clean on a valid plan and leave the status word at ACE_OK."""
     monkeypatch.setenv("ACE_CHECKED", "1")
@@ -287,7 +287,8 @@ def test_autotune_then_evaluate(dev, name, n_out, grad):
     w, o, _, A, c = setup(name, n_env=301)
     d = Dag(_CACHE[(name, "balanced")][2])          # own graph handle: the tuned choice stays local
     res = d.autotune(n_env=4096, n_out=n_out, dtype=torch.float32, grad=grad)
-    assert res["kernel"] in ("tile_per_lane", "env_per_lane", "env_per_lane_multi") and res["ms"] > 0
+    assert res["kernel"] in ("tile_per_lane", "env_per_lane", "env_per_lane_global", "env_per_lane_multi",
+                             "env_pair_per_lane_global") and res["ms"] > 0
     if res["kernel"] == "tile_per_lane":
         assert res["E"] in (1, 2, 4, 8, 16)
     if n_out > 1:

@@ -35,7 +35,7 @@ def _capture(fn):
     return g, out
 
 
-@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg"])
+@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg", "loeg2"])
 def test_graph_replay_fused_grad(dev, kernel, monkeypatch):
     from paper_2202_04140_gb300.torch_api import Dag, Spec
     monkeypatch.setenv("ACE_KERNEL", kernel)

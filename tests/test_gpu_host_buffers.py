@@ -37,7 +37,7 @@ def case():
     return w, o, s, A, c, pb
 
 
-@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg"])
+@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg", "loeg2"])
 @pytest.mark.parametrize("chunk", [0, 300, 4096])
 def test_grad_host_matches_device(dev, case, kernel, chunk, monkeypatch):
     from paper_2202_04140_gb300.torch_api import Dag

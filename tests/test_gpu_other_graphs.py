@@ -38,7 +38,7 @@ def dev():
 
 @pytest.mark.parametrize("algo", [1, 2])
 @pytest.mark.parametrize("case", sorted(CASES))
-@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg"])
+@pytest.mark.parametrize("kernel", ["lon", "loe", "loeg", "loeg2"])
 def test_graph_variants(dev, case, algo, kernel, monkeypatch):
     from paper_2202_04140_gb300.torch_api import Dag, Spec
     monkeypatch.setenv("ACE_KERNEL", kernel)

@@ -33,9 +33,11 @@ def dev():
     return torch.device("cuda:0")
 
 
-def test_paper_degree_d16_global_workspace(dev, monkeypatch):
+@pytest.mark.parametrize("kernel", ["loeg", "loeg2"])
+def test_paper_degree_d16_global_workspace(dev, monkeypatch, kernel):
+    """Both global-workspace forms (one and two environments per lane) on the D = 16 paper-degree set."""
     from paper_2202_04140_gb300.torch_api import Dag, Spec
-    monkeypatch.setenv("ACE_KERNEL", "loeg")
+    monkeypatch.setenv("ACE_KERNEL", kernel)
     w = W.workload("paper_degree_d20_k810", deg_max=16)
     o = workload_index_set(w)
     s = Spec.from_workload(w)
