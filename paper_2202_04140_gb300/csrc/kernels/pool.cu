@@ -717,39 +717,50 @@ cudaError_t ensure_pool_constants() {
   return cudaSuccess;
 }
 
-// CTAs for n_groups warp work items (environments, or groups of them), at most 8 per SM.
-int pool_grid(int64_t n_groups) {
-  int dev_id = 0, sms = 148;
+// CTAs for n_groups warp work items (environments, or groups of them): at most as many as are
+// resident at once (kernel's occupancy with smem bytes of shared memory), so that no partial
+// second wave of CTAs leaves SMs idle; the warps take their items round-robin.
+int pool_grid(int64_t n_groups, const void* kernel, size_t smem) {
+  int dev_id = 0, sms = 148, bps = 0;
   cudaGetDevice(&dev_id);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, dev::kPoolWarps * 32, smem) != cudaSuccess || bps < 1)
+    bps = 1;
   int64_t need = (n_groups + dev::kPoolWarps - 1) / dev::kPoolWarps;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * bps));
 }
 
 }  // namespace
 
-#define ACE_POOL_DISPATCH(KERNEL, ...)                                                              \
-  switch (lmax) {                                                                                   \
-    case 0: dev::KERNEL<0><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
-    case 1: dev::KERNEL<1><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
-    case 2: dev::KERNEL<2><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
-    case 3: dev::KERNEL<3><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
-    case 4: dev::KERNEL<4><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
-    case 5: dev::KERNEL<5><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
-    case 6: dev::KERNEL<6><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
-    case 7: dev::KERNEL<7><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
-    case 8: dev::KERNEL<8><<<grid, dev::kPoolWarps * 32, 0, st>>>(__VA_ARGS__); break;              \
-    default: return cudaErrorInvalidValue;                                                          \
-  }
+namespace {
+
+template <int LMAX>
+cudaError_t launch_pool_l(cudaStream_t st, const float* pos, const float* mu, const int64_t* offsets, int64_t n_env,
+                          float rc, int nmin, int nmax, int kf, float* A) {
+  const int grid = pool_grid(n_env, (const void*)&dev::pool_kernel<LMAX>, 0);
+  dev::pool_kernel<LMAX><<<grid, dev::kPoolWarps * 32, 0, st>>>(pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+  return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t launch_pool(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, float rc, int nmin,
                         int nmax, int lmax, int kmax, float* A, cudaStream_t st) {
   cudaError_t e = ensure_pool_constants();
   if (e != cudaSuccess) return e;
-  const int grid = pool_grid(n_env);
   const int kf = kmax + 1;
-  ACE_POOL_DISPATCH(pool_kernel, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A)
-  return cudaGetLastError();
+  switch (lmax) {
+    case 0: return launch_pool_l<0>(st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+    case 1: return launch_pool_l<1>(st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+    case 2: return launch_pool_l<2>(st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+    case 3: return launch_pool_l<3>(st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+    case 4: return launch_pool_l<4>(st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+    case 5: return launch_pool_l<5>(st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+    case 6: return launch_pool_l<6>(st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+    case 7: return launch_pool_l<7>(st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+    case 8: return launch_pool_l<8>(st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, A);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 namespace {
@@ -757,7 +768,7 @@ namespace {
 // The adjoint kernel for one lmax: its shared memory (G of kPoolGroupEnvs environments
 // per warp) can pass the 48 KB default (16 radial x feature rows at lmax 8 take 86 KB).
 template <int LMAX>
-cudaError_t launch_pool_grad_l(int grid, size_t smem, cudaStream_t st, const float* pos, const float* mu,
+cudaError_t launch_pool_grad_l(int64_t n_groups, size_t smem, cudaStream_t st, const float* pos, const float* mu,
                                const int64_t* offsets, int64_t n_env, float rc, int nmin, int nmax, int kf,
                                const float* dA, float alpha, float* dpos) {
   if (smem > 48 * 1024) {  // a per-device attribute: set on every such launch
@@ -765,6 +776,7 @@ cudaError_t launch_pool_grad_l(int grid, size_t smem, cudaStream_t st, const flo
         cudaFuncSetAttribute(dev::pool_grad_kernel<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  const int grid = pool_grid(n_groups, (const void*)&dev::pool_grad_kernel<LMAX>, smem);
   dev::pool_grad_kernel<LMAX><<<grid, dev::kPoolWarps * 32, smem, st>>>(pos, mu, offsets, n_env, rc, nmin, nmax, kf,
                                                                          dA, alpha, dpos);
   return cudaGetLastError();
@@ -779,19 +791,18 @@ cudaError_t launch_pool_grad(const float* pos, const float* mu, const int64_t* o
   if (e != cudaSuccess) return e;
   const int kf = kmax + 1;
   const int64_t n_groups = (n_env + dev::kPoolGroupEnvs - 1) / dev::kPoolGroupEnvs;
-  const int grid = pool_grid(n_groups);
   const int NLP = 4 * (((lmax + 1) * (lmax + 1) + 3) / 4);
   const size_t smem = (size_t)dev::kPoolWarps * dev::kPoolGroupEnvs * (nmax - nmin + 1) * kf * NLP * sizeof(float);
   switch (lmax) {
-    case 0: return launch_pool_grad_l<0>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
-    case 1: return launch_pool_grad_l<1>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
-    case 2: return launch_pool_grad_l<2>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
-    case 3: return launch_pool_grad_l<3>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
-    case 4: return launch_pool_grad_l<4>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
-    case 5: return launch_pool_grad_l<5>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
-    case 6: return launch_pool_grad_l<6>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
-    case 7: return launch_pool_grad_l<7>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
-    case 8: return launch_pool_grad_l<8>(grid, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 0: return launch_pool_grad_l<0>(n_groups, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 1: return launch_pool_grad_l<1>(n_groups, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 2: return launch_pool_grad_l<2>(n_groups, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 3: return launch_pool_grad_l<3>(n_groups, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 4: return launch_pool_grad_l<4>(n_groups, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 5: return launch_pool_grad_l<5>(n_groups, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 6: return launch_pool_grad_l<6>(n_groups, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 7: return launch_pool_grad_l<7>(n_groups, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
+    case 8: return launch_pool_grad_l<8>(n_groups, smem, st, pos, mu, offsets, n_env, rc, nmin, nmax, kf, dA, alpha, dpos);
     default: return cudaErrorInvalidValue;
   }
 }
