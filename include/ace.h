@@ -220,8 +220,11 @@ ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void*
  * chunk is evaluated on a second, and its phi (and dA) copied back on a third:
  * while chunk i is evaluated, chunk i+1 is copied in and chunk i-1 out (two
  * staging slots).  Evaluations run one after another, as ace_eval_grad would.
- * chunk_env = 0 takes a third of the batch but at least 8 MiB of A and 4 x SMs
- * tiles of the kernel form per chunk (a smaller batch is one chunk).
+ * chunk_env = 0 takes a short first and last chunk (whole waves of the kernel
+ * form, SMs x environments per tile, at least 2 MiB of A: their copy-in and
+ * copy-out overlap nothing) around two long chunks that take the rest; a batch
+ * too small for that takes a third of the batch but at least 8 MiB of A and 4
+ * waves per chunk (a smaller batch is one chunk).
  *  A       : host [n_env][K] in dtype, read.
  *  c       : dev [n_basis][n_out] in dtype, or NULL (bound coefficients), as ace_eval.
  *  phi_bar : host [n_env][n_out] in dtype, or NULL (ones); ace_eval_grad_host only.

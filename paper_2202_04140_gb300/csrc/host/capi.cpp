@@ -961,6 +961,29 @@ ace_status ensure_host_pipeline(ace_dag* d, size_t bytes) {
   return ACE_OK;
 }
 
+// Chunk sizes of a host-buffer evaluation: equal chunks of `chunk` environments when the caller
+// gives a size; otherwise a short first and last chunk (whole waves of the kernel form, SMs x
+// environments per tile, at least 2 MiB of A) around two long ones that take the rest, because
+// nothing overlaps the copy-in of the first chunk and the copy-out of the last (measured on the
+// stress workload: end to end 5.72 M env/s with thirds, 5.85 with 8 MiB edges).  Batches too small
+// for that take the automatic size of auto_chunk.
+std::vector<int64_t> chunk_plan(const ace_dag* d, const DevTaskSet& dt, int dtype, int n_out, int readout, bool grad,
+                                int64_t n_env, size_t row_bytes, int64_t chunk) {
+  std::vector<int64_t> out;
+  if (chunk == 0) {
+    const int64_t wave = (int64_t)std::max(d->sm_count, 1) * tile_envs_of(d, dt, dtype, n_out, readout, grad, n_env);
+    const int64_t by_bytes = (int64_t)((2u << 20) / row_bytes) + 1;
+    const int64_t edge = (std::max<int64_t>(by_bytes, wave) + wave - 1) / wave * wave;
+    const int64_t rest = n_env - 2 * edge;
+    const int64_t mid = rest / (2 * wave) * wave;
+    if (mid >= 2 * edge) return {edge, mid, rest - mid, edge};
+    chunk = auto_chunk(d, dt, dtype, n_out, readout, grad, n_env, row_bytes);
+  }
+  chunk = std::min(chunk, n_env);
+  for (int64_t off = 0; off < n_env; off += chunk) out.push_back(std::min(chunk, n_env - off));
+  return out;
+}
+
 // Chunked evaluation with host buffers: chunk i is copied in on hstream[0], evaluated on
 // hstream[1] and copied out on hstream[2]; slot i mod 2 is reused by chunk i + 2 once the
 // evaluation of chunk i has read its A and the copy-out of chunk i has read its outputs.
@@ -972,8 +995,8 @@ ace_status eval_host(ace_dag* d, const void* A, const void* c, const void* phiba
   if ((s = bind(d, dt, c, n_out, dtype, st)) != ACE_OK) return s;
   if (n_env == 0) return ACE_OK;
   const size_t tsz = dtype == ACE_F32 ? 4 : 8;
-  if (chunk == 0) chunk = auto_chunk(d, dt, dtype, n_out, readout, grad, n_env, (size_t)d->K * tsz);
-  chunk = std::min(chunk, n_env);
+  const std::vector<int64_t> plan = chunk_plan(d, dt, dtype, n_out, readout, grad, n_env, (size_t)d->K * tsz, chunk);
+  chunk = *std::max_element(plan.begin(), plan.end());
   const size_t a_bytes = dev::align16((size_t)chunk * d->K * tsz);
   const size_t o_bytes = dev::align16((size_t)chunk * n_out * tsz);
   const size_t slot_bytes = a_bytes * (grad ? 2 : 1) + o_bytes * (grad ? 2 : 1);
@@ -988,8 +1011,9 @@ ace_status eval_host(ace_dag* d, const void* A, const void* c, const void* phiba
   unsigned char* dAh = static_cast<unsigned char*>(dA);
   const size_t row_a = (size_t)d->K * tsz, row_o = (size_t)n_out * tsz;
   s = ACE_OK;
-  for (int64_t k = 0, off = 0; off < n_env && e == cudaSuccess && s == ACE_OK; ++k, off += chunk) {
-    const int64_t n = std::min(chunk, n_env - off);
+  int64_t off = 0;
+  for (size_t k = 0; k < plan.size() && e == cudaSuccess && s == ACE_OK; off += plan[k], ++k) {
+    const int64_t n = plan[k];
     const int b = (int)(k & 1);
     unsigned char* slot = static_cast<unsigned char*>(d->hslot[b]);
     unsigned char* Ad = slot;
@@ -1598,9 +1622,8 @@ ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* m
   if ((s = ensure_uploaded(dag, st)) != ACE_OK) return s;
   if ((s = bind(dag, dag->sym, c, 1, ACE_F32, st)) != ACE_OK) return s;
   if (n_env == 0) return ACE_OK;
-  int64_t chunk = chunk_env;
-  if (chunk == 0) chunk = auto_chunk(dag, dag->sym, ACE_F32, 1, readout, true, n_env, (size_t)K * 4);
-  chunk = std::min(chunk, n_env);
+  const std::vector<int64_t> plan = chunk_plan(dag, dag->sym, ACE_F32, 1, readout, true, n_env, (size_t)K * 4, chunk_env);
+  const int64_t chunk = *std::max_element(plan.begin(), plan.end());
   // one allocation: positions, mu, offsets, forces, phi of the batch, then A and dA of two chunks
   const size_t b_pos = dev::align16((size_t)n_pairs * 12), b_mu = kmax > 0 ? dev::align16((size_t)n_pairs * 4) : 0;
   const size_t b_off = dev::align16((size_t)(n_env + 1) * 8), b_phi = dev::align16((size_t)n_env * 4);
@@ -1629,8 +1652,9 @@ ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* m
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h, dag->hev_fork, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(off_d, offsets, (size_t)(n_env + 1) * 8, cudaMemcpyHostToDevice, hin);
   s = ACE_OK;
-  for (int64_t k = 0, e0 = 0; e0 < n_env && e == cudaSuccess && s == ACE_OK; ++k, e0 += chunk) {
-    const int64_t n = std::min(chunk, n_env - e0);
+  int64_t e0 = 0;
+  for (size_t k = 0; k < plan.size() && e == cudaSuccess && s == ACE_OK; e0 += plan[k], ++k) {
+    const int64_t n = plan[k];
     const int64_t p0 = offsets[e0], p1 = offsets[e0 + n];
     const int b = (int)(k & 1);
     float* A_d = reinterpret_cast<float*>(slots + (size_t)b * 2 * b_a);
