@@ -34,7 +34,7 @@ constexpr int kMaxLevels = 8;
 // out per warp).
 constexpr int kLoeStreamWarps = 32;
 // Zero items allocated after the last stream (the kernel reads up to this many items ahead).
-constexpr int kLoeStreamPad = 8;
+constexpr int kLoeStreamPad = 16;
 // Block units of the streams: header {m, rows << 8 | kLoeBlockFlag, 0, 0}, kLoeBlockCols / 4
 // items of columns, then per row a header {x, flags, z, row coefficient} and kLoeBlockCols / 4
 // items of coefficients.

@@ -16,6 +16,11 @@ namespace ace {
 namespace dev {
 
 constexpr int kWideRow = 64;  // environments per CTA and floats per workspace row
+// Entry pairs loaded together per warp: more gathers in flight (measured at D = 20: 2 pairs 33.1 ms,
+// 4 34.8, 5 27.2, 6 27.4, 7 33.0, 8 32.0; from 7 on, register spills outweigh them).
+constexpr int kWideBatch = 5;
+// the next task's first kWideBatch pair items are read past its header: inside the stream padding
+static_assert(kWideBatch < kLoeStreamPad, "read-ahead beyond the stream padding");
 
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
@@ -139,9 +144,9 @@ __device__ __forceinline__ void wide_tasks(const LoeArgs& a, const float* AA, fl
                  "r"((unsigned)((pend - p) * (int)sizeof(int4)))
                  : "memory");
   int4 h = __ldg(p);
-  int4 cur[kPairBatch];
+  int4 cur[kWideBatch];
 #pragma unroll
-  for (int u = 0; u < kPairBatch; ++u) cur[u] = __ldg(p + 1 + u);
+  for (int u = 0; u < kWideBatch; ++u) cur[u] = __ldg(p + 1 + u);
   while (true) {
     if (h.y & kLoeBlockFlag) {
       const int4* const pn = wide_block<GRAD, RO, CHECK>(a, AA, G, pbl, phi0, phi1, p, h, cur[0], cur[1], lane);
@@ -149,7 +154,7 @@ __device__ __forceinline__ void wide_tasks(const LoeArgs& a, const float* AA, fl
       p = pn;
       h = __ldg(p);
 #pragma unroll
-      for (int u = 0; u < kPairBatch; ++u) cur[u] = __ldg(p + 1 + u);
+      for (int u = 0; u < kWideBatch; ++u) cur[u] = __ldg(p + 1 + u);
       continue;
     }
     const int np = h.y >> 8;
@@ -158,16 +163,16 @@ __device__ __forceinline__ void wide_tasks(const LoeArgs& a, const float* AA, fl
     const int4 hn = __ldg(pn);
     float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int u = 0; u < kPairBatch; ++u)
+    for (int u = 0; u < kWideBatch; ++u)
       if (u < np) wide_pair<CHECK>(a, AA, cur[u], lane, acc0, acc1);
 #pragma unroll
-    for (int u = 0; u < kPairBatch; ++u) cur[u] = __ldg(pn + 1 + u);
-    for (int b = kPairBatch; b < np; b += kPairBatch) {
-      int4 bt[kPairBatch];
+    for (int u = 0; u < kWideBatch; ++u) cur[u] = __ldg(pn + 1 + u);
+    for (int b = kWideBatch; b < np; b += kWideBatch) {
+      int4 bt[kWideBatch];
 #pragma unroll
-      for (int u = 0; u < kPairBatch; ++u) bt[u] = __ldg(p + 1 + b + u);
+      for (int u = 0; u < kWideBatch; ++u) bt[u] = __ldg(p + 1 + b + u);
 #pragma unroll
-      for (int u = 0; u < kPairBatch; ++u)
+      for (int u = 0; u < kWideBatch; ++u)
         if (b + u < np) wide_pair<CHECK>(a, AA, bt[u], lane, acc0, acc1);
     }
     wide_epilogue<GRAD, RO, CHECK>(a, AA, G, pbl, phi0, phi1, h, make_float2(acc0.x + acc1.x, acc0.y + acc1.y),
