@@ -160,7 +160,10 @@ ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_si
  * of the row-major tasks as one stream per warp of the one-environment-per-lane
  * kernel: "loe_wbeg" (33 values: first 16-byte item of each of the 32 warps'
  * streams, then the total) and "loe_hpos" (item of each task's header; task t
- * belongs to warp t mod 32 and its entry pairs follow its header).
+ * belongs to warp t mod 32 and its entry pairs follow its header); "g_perm"
+ * (the tile-per-lane kernel's adjoint row of each of the n_g slots with an adjoint,
+ * a permutation chosen so that the adjoint updates one warp issues together fall
+ * in different shared-memory banks).
  * Every array is exported as int32.  *count receives the number of int32
  * values; out (host) may be NULL to query the size.  Errors: INVALID_ARG for an
  * unknown name. */

@@ -153,6 +153,9 @@ struct Plan {
   PullList pull;                      // the same sweep, gathered per target
   TaskSet sym;                        // symmetric sink form (forward + adjoint)
   TaskSet one;                        // one-sided sink form (forward only)
+  // Adjoint row of each slot with an adjoint (a permutation of [0, n_g)) for the tile-per-lane
+  // kernel, chosen so that the adjoint updates issued together fall in different banks.
+  std::vector<int32_t> g_perm;
 };
 
 // stored_limit(K, n_g): at most this many slots are kept for the tile-per-lane

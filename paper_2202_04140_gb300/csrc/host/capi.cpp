@@ -118,6 +118,8 @@ struct ace_dag {
   int32_t *rev_slot = nullptr, *rev_l = nullptr, *rev_r = nullptr;
   int4* pull = nullptr;  // {consumer slot, partner slot, target slot, 0}
   std::vector<int4> pull_host;
+  bool genc = false;                 // the sym tasks and pull triples carry permuted adjoint rows
+  int32_t* g_perm_dev = nullptr;     // [n_g] adjoint row of each slot (the dA copy of the leaves)
   int32_t *node_left = nullptr, *node_right = nullptr, *node_basis = nullptr, *slot_basis = nullptr;
   DevTaskSet sym, one;
   void* loe_ws = nullptr;  // global workspace of the one-environment-per-lane kernel for large graphs
@@ -195,16 +197,23 @@ int32_t segment_bits(const std::vector<Task>& tasks, size_t sl, int j) {
   return bits;
 }
 
-std::vector<int4> device_tasks(const std::vector<Task>& tasks) {
+// perm (or NULL): adjoint row of each slot with an adjoint; the adjoint targets of a task (the row
+// of a task that is not a top operand, the two factors of one that is) then carry their row in
+// the high 16 bits above the slot (both below 2^15).
+std::vector<int4> device_tasks(const std::vector<Task>& tasks, const int32_t* perm) {
   std::vector<int4> t4(tasks.size());
-  for (size_t i = 0; i < tasks.size(); ++i)
-    t4[i] = make_int4(tasks[i].row, tasks[i].flags | segment_bits(tasks, i / 32, (int)(i % 32)), tasks[i].pl,
-                      tasks[i].pr);
+  auto enc = [&](int32_t v) { return perm && v >= 0 ? v | (perm[v] << 16) : v; };
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    const Task& t = tasks[i];
+    const bool top = (t.flags & 2) != 0;
+    t4[i] = make_int4(top ? t.row : enc(t.row), t.flags | segment_bits(tasks, i / 32, (int)(i % 32)),
+                      top ? enc(t.pl) : t.pl, top ? enc(t.pr) : t.pr);
+  }
   return t4;
 }
 
-ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStream_t st) {
-  std::vector<int4> t4 = device_tasks(ts.tasks);
+ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStream_t st, const int32_t* perm) {
+  std::vector<int4> t4 = device_tasks(ts.tasks, perm);
   d->staging_int4.push_back(std::move(t4));
   ace_status s;
   if ((s = upload_vec(d, d->staging_int4.back(), &dt.tasks, st)) != ACE_OK) return s;
@@ -264,7 +273,7 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   dt.n_cold_slices = ts.n_cold_slices();
   dt.n_cold_pad = (int64_t)ts.cold_ca.size();
   if (dt.n_cold_slices > 0) {
-    std::vector<int4> c4 = device_tasks(ts.cold_tasks);
+    std::vector<int4> c4 = device_tasks(ts.cold_tasks, perm);
     std::vector<int32_t> hdr(ts.cold_slice_steps.size());
     for (size_t sl = 0; sl < hdr.size(); ++sl)
       hdr[sl] = ts.cold_slice_steps[sl] | (reduction_rounds(ts.cold_tasks, sl) << 16);
@@ -439,8 +448,12 @@ ace_status ensure_uploaded(ace_dag* d, cudaStream_t st) {
   if ((s = upload_vec(d, p.rev.slot, &d->rev_slot, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.rev.l, &d->rev_l, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.rev.r, &d->rev_r, st)) != ACE_OK) return s;
+  // the tile-per-lane kernel's adjoint rows: permuted (Plan::g_perm) when every row fits 15 bits
+  d->genc = p.n_g <= 32767 && p.g_perm.size() == (size_t)p.n_g;
+  if (d->genc && (s = upload_vec(d, p.g_perm, &d->g_perm_dev, st)) != ACE_OK) return s;
   // {consumer, partner, target, rounds}: rounds of the segmented warp sum of the 32-triple chunk
-  // (counted from the level's first triple, as the kernel walks them) holding the triple
+  // (counted from the level's first triple, as the kernel walks them) holding the triple; the
+  // consumer and the target as adjoint rows
   d->pull_host.resize(p.pull.src.size());
   for (size_t lv = 0; lv + 1 < p.pull.lvl.size(); ++lv)
     for (int32_t c0 = p.pull.lvl[lv]; c0 < p.pull.lvl[lv + 1]; c0 += 32) {
@@ -452,15 +465,17 @@ ace_status ensure_uploaded(ace_dag* d, cudaStream_t st) {
       }
       int rounds = 0;
       while ((1 << rounds) < longest) ++rounds;
-      for (int32_t j = c0; j < c1; ++j) d->pull_host[j] = make_int4(p.pull.src[j], p.pull.par[j], p.pull.tgt[j], rounds);
+      for (int32_t j = c0; j < c1; ++j)
+        d->pull_host[j] = d->genc ? make_int4(p.g_perm[p.pull.src[j]], p.pull.par[j], p.g_perm[p.pull.tgt[j]], rounds)
+                                  : make_int4(p.pull.src[j], p.pull.par[j], p.pull.tgt[j], rounds);
     }
   if ((s = upload_vec(d, d->pull_host, &d->pull, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, d->g.left, &d->node_left, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, d->g.right, &d->node_right, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, d->g.node_basis, &d->node_basis, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, p.slot_basis, &d->slot_basis, st)) != ACE_OK) return s;
-  if ((s = upload_tasks(d, p.sym, d->sym, st)) != ACE_OK) return s;
-  if ((s = upload_tasks(d, p.one, d->one, st)) != ACE_OK) return s;
+  if ((s = upload_tasks(d, p.sym, d->sym, st, d->genc ? p.g_perm.data() : nullptr)) != ACE_OK) return s;
+  if ((s = upload_tasks(d, p.one, d->one, st, nullptr)) != ACE_OK) return s;
   void* stw = nullptr;
   if ((e = cudaMalloc(&stw, 16)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   d->allocations.push_back(stw);
@@ -864,6 +879,8 @@ ace_status run_fused(ace_dag* d, const void* A, const void* c, const void* phiba
     a.off4 = dt.off4;
     a.vals4 = dt.vals4;
     a.gs = dev::g_stride(p.n_g);
+    a.genc = grad && d->genc ? 1 : 0;
+    a.gperm = grad && d->genc ? d->g_perm_dev : nullptr;
     a.vals = static_cast<const TT*>(dt.vals);
     a.lin = static_cast<const TT*>(dt.lin);
     a.cold_tasks = dt.cold_tasks;
@@ -1301,6 +1318,7 @@ ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out
   else if (n == "pull_src") v = &p.pull.src;
   else if (n == "pull_par") v = &p.pull.par;
   else if (n == "pull_lvl") v = &p.pull.lvl;
+  else if (n == "g_perm") v = &p.g_perm;
   else if (n.rfind("sym_", 0) == 0) {
     if (!from_ts(p.sym, n.substr(4))) v = nullptr;
   } else if (n.rfind("one_", 0) == 0) {

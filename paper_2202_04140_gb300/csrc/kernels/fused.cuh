@@ -54,6 +54,11 @@ struct FusedArgs {
   int64_t n_tiles;
   int32_t K, n_slots, n_g, n_out;  // n_slots: slots kept in shared memory (leaves, inner, stored top)
   int32_t gs;  // stride between environments in G (n_g rounded up to 32)
+  // genc = 1: the adjoint targets of the tasks carry their adjoint row in the high 16 bits (the
+  // slot in the low 16), the pull triples' consumer and target are adjoint rows, and gperm gives
+  // the row of each leaf (rows permuted so that updates issued together fall in different banks)
+  int32_t genc;
+  const int32_t* gperm;
   const int32_t* fwd_slot;
   const int32_t* fwd_l;
   const int32_t* fwd_r;
@@ -504,18 +509,26 @@ __device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __
   const int gs = a.gs;
   const bool top = (task.y & 2) != 0;
   bool valid = task.x >= 0;
+  // slots (rows of AA) and adjoint rows (rows of G) of the task's targets: the row of a task that
+  // is not a top operand, the two factors of one that is (a top operand may not be stored: its
+  // value is the product of its factors)
+  const bool enc = GRAD && a.genc;
+  int row = enc && !top ? (task.x & 0xffff) : task.x, row_g = enc && !top ? (task.x >> 16) : task.x;
+  int pl = enc ? (task.z & 0xffff) : task.z, pl_g = enc ? (task.z >> 16) : task.z;
+  int pr = enc ? (task.w & 0xffff) : task.w, pr_g = enc ? (task.w >> 16) : task.w;
   if constexpr (CHECK) {
-    bool bad = valid && !top && (unsigned)task.x >= (unsigned)a.n_slots;
-    if (valid && top) bad |= (unsigned)task.z >= (unsigned)a.n_g || (unsigned)task.w >= (unsigned)a.n_g;
-    if (GRAD && valid && !top) bad |= (unsigned)task.x >= (unsigned)a.n_g;
+    bool bad = valid && !top && (unsigned)row >= (unsigned)a.n_slots;
+    if (valid && top)
+      bad |= (unsigned)pl >= (unsigned)a.n_g || (unsigned)pr >= (unsigned)a.n_g ||
+             (unsigned)pl_g >= (unsigned)a.n_g || (unsigned)pr_g >= (unsigned)a.n_g;
+    if (GRAD && valid && !top) bad |= (unsigned)row >= (unsigned)a.n_g || (unsigned)row_g >= (unsigned)a.n_g;
     if (bad) {
       atomicOr(a.status, kStatusBounds);
       valid = false;
     }
   }
-  const int row = valid ? task.x : 0;
-  // factors of a top operand; its value is their product (a top operand may not be stored)
-  const int pl = (valid && top) ? task.z : 0, pr = (valid && top) ? task.w : 0;
+  if (!valid) row = row_g = 0;
+  if (!(valid && top)) pl = pl_g = pr = pr_g = 0;
   T xl[E], xr[E], ap[E];
   if (top) {
     load_slot<T, E>(AA + (size_t)pl * E, xl);
@@ -549,7 +562,7 @@ __device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __
     // sum leaves each run's total in its first lane, which does one atomic.  The
     // plan stores the runs with the task (bit 8 + r: lane + 2^r is in the same
     // run; bit 13: first lane of its run), so no target is shuffled here.
-    const int key = valid ? (top ? pl : row) : 0;
+    const int key = valid ? (top ? pl_g : row_g) : 0;
     T va[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) va[e] = top ? g[e] * xr[e] : g[e];
@@ -569,7 +582,7 @@ __device__ __forceinline__ void task_epilogue(const FusedArgs<T>& a, const T* __
     // "B" target: the second factor of a top operand, one atomic per lane
     if (valid && top) {
 #pragma unroll
-      for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * gs + pr, g[e] * xl[e]);
+      for (int e = 0; e < E; ++e) atomicAdd(G + (size_t)e * gs + pr_g, g[e] * xl[e]);
     }
   }
 }
@@ -892,7 +905,7 @@ __global__ void __launch_bounds__(NT) fused_kernel(const FusedArgs<T> a) {
       for (int i = tid; i < E * K; i += NT) {
         const int e = i / K, k = i - e * K;
         const int64_t env = env0 + e;
-        if (env < a.n_env) a.dA[env * K + k] = G[(size_t)e * a.gs + k];
+        if (env < a.n_env) a.dA[env * K + k] = G[(size_t)e * a.gs + (a.gperm ? __ldg(a.gperm + k) : k)];
       }
     }
     // 5. phi: the per-warp partials (already in shared memory) combined in fixed warp order by the
