@@ -544,3 +544,44 @@ def test_plain_f64_sizes_refused_without_wrapping():
             L.ace_eval_plain_f64_static(d.handle, p, p, 0, n_env, 1, p, p, 0)
         assert e.value.status == -1 and "static scratch" in str(e.value)
     assert L.ace_eval_plain_workspace_bytes(d.handle, 10, 1) == 10 * per_env
+
+
+def _slice_bank_loads(tasks, rows):
+    """Per slice of 32 tasks: the largest number of distinct first targets (run heads) and of second
+    targets that share a bank (row mod 32) once mapped through rows."""
+    a_load = b_load = 0
+    for sl in tasks.reshape(-1, 32, 4):
+        v = sl[:, 0] >= 0
+        if not v.any():
+            continue
+        top = ((sl[:, 1] & 2) != 0) & v
+        heads = np.unique(np.where(top, sl[:, 2], sl[:, 0])[v])
+        a_load += np.bincount(rows[heads] % 32, minlength=32).max()
+        if top.any():
+            b_load += np.bincount(rows[sl[top, 3]] % 32, minlength=32).max()
+    return a_load, b_load
+
+
+@pytest.mark.parametrize("name", ["fwd_grad_k392", "stress_k810"])
+def test_adjoint_row_permutation(name):
+    """The tile kernel's adjoint rows: g_perm is a permutation of the n_g slots with an adjoint; slices
+    repeat a second target only where the slice had to be completed from the tasks that followed
+    (a repeat is two updates of one address, still correct); and the rows spread the updates one
+    warp issues together over the banks better than the slots themselves do."""
+    d = Dag(Spec.from_workload(W.WORKLOADS[name]))
+    n_g = int(L.ace_dag_plan_array(d.handle, "n_g")[0])
+    perm = L.ace_dag_plan_array(d.handle, "g_perm")
+    assert sorted(perm.tolist()) == list(range(n_g))
+    tasks = L.ace_dag_plan_array(d.handle, "sym_tasks")
+    slices = tasks.reshape(-1, 32, 4)
+    repeats = 0
+    for sl in slices:
+        top = ((sl[:, 1] & 2) != 0) & (sl[:, 0] >= 0)
+        repeats += len(np.unique(sl[top, 3])) < int(top.sum())
+    if name == "stress_k810":   # 8 of 736 slices with this plan
+        assert repeats <= 0.02 * len(slices)
+    ident = _slice_bank_loads(tasks, np.arange(n_g))
+    permuted = _slice_bank_loads(tasks, perm)
+    assert sum(permuted) < sum(ident)
+    if name == "stress_k810":   # measured with this plan: 826 + 1,239 against 1,206 + 2,071
+        assert sum(permuted) <= 0.7 * sum(ident)
