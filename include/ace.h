@@ -183,6 +183,13 @@ ace_status ace_dag_upload(ace_dag* dag, void* stream);
  *  c   : dev [n_basis][n_out] in dtype, canonical basis order.  Bound into the
  *        plan by a small gather kernel on `stream`; NULL reuses the
  *        coefficients bound by the previous call with the same n_out and dtype.
+ *        A CUDA graph that captured an evaluation reads the coefficients bound
+ *        when it was captured, from buffers of the handle: binding other
+ *        coefficients (another c, dtype or n_out) to the handle afterwards
+ *        changes what a replay reads.  Buffers replaced by a larger binding stay
+ *        allocated until ace_dag_free, so a replay never reads freed memory; a
+ *        global workspace replaced by a larger request is freed, so replaying a
+ *        graph captured before such a request is not valid.
  *  phi : dev [n_env][n_out] in dtype, written.
  *  n_out in {1, 2, 4, 8, 16}.  readout: ACE_READOUT_PLAIN (FP32 sums),
  *  ACE_READOUT_COMPENSATED (per-task partial sums in FP32, combined by Kahan's

@@ -503,14 +503,14 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
   const size_t lb = std::max<size_t>((size_t)dt.n_slices * 32 * npad * tsz, 16);
   cudaError_t e;
   if (vb > dt.vals_bytes) {
-    if (dt.vals) cudaFree(dt.vals);
+    if (dt.vals) d->allocations.push_back(dt.vals);  // kept: a captured graph may read it
     dt.vals = nullptr;
     dt.vals_bytes = 0;
     if ((e = cudaMalloc(&dt.vals, vb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     dt.vals_bytes = vb;
   }
   if (lb > dt.lin_bytes) {
-    if (dt.lin) cudaFree(dt.lin);
+    if (dt.lin) d->allocations.push_back(dt.lin);  // kept: a captured graph may read it
     dt.lin = nullptr;
     dt.lin_bytes = 0;
     if ((e = cudaMalloc(&dt.lin, lb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -522,7 +522,7 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
   if (dtype == ACE_F32 && n_out == 1 && dt.col4) {
     const size_t b4 = std::max<size_t>((size_t)dt.n_pack * 4, 16);
     if (b4 > dt.vals4_bytes) {
-      if (dt.vals4) cudaFree(dt.vals4);
+      if (dt.vals4) d->allocations.push_back(dt.vals4);  // kept: a captured graph may read it
       dt.vals4 = nullptr;
       dt.vals4_bytes = 0;
       if ((e = cudaMalloc(&dt.vals4, b4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -534,7 +534,7 @@ ace_status bind(ace_dag* d, DevTaskSet& dt, const void* c, int n_out, int dtype,
   if (dt.n_cold_slices > 0) {
     const size_t cb = std::max<size_t>((size_t)dt.n_cold_pad * npad * tsz, 16);
     if (cb > dt.cold_vals_bytes) {
-      if (dt.cold_vals) cudaFree(dt.cold_vals);
+      if (dt.cold_vals) d->allocations.push_back(dt.cold_vals);  // kept: a captured graph may read it
       dt.cold_vals = nullptr;
       dt.cold_vals_bytes = 0;
       if ((e = cudaMalloc(&dt.cold_vals, cb)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
