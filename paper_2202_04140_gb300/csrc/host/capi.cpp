@@ -759,35 +759,10 @@ ace_status run_loe(ace_dag* d, DevTaskSet& dt, const void* A, const void* phibar
       d->loe_ws_bytes = need;
     }
   }
-  const Plan& p = d->plan;
-  dev::LoeArgs a{};
-  a.ws = static_cast<float*>(d->loe_ws);
-  a.A = static_cast<const float*>(A);
-  a.phibar = static_cast<const float*>(phibar);
-  a.phi = static_cast<float*>(phi);
-  a.dA = static_cast<float*>(dA);
-  a.n_env = n_env;
-  a.n_tiles = n_tiles;
-  a.K = p.K;
-  a.n_slots = p.n_slots;
-  a.n_g = p.n_g;
-  a.fwd_slot = d->fwd_slot;
-  a.fwd_l = d->fwd_l;
-  a.fwd_r = d->fwd_r;
-  a.rev_slot = d->rev_slot;
-  a.rev_l = d->rev_l;
-  a.rev_r = d->rev_r;
-  a.n_fwd_levels = (int32_t)p.fwd.off.size() - 1;
-  a.n_rev_levels = (int32_t)p.rev.off.size() - 1;
-  for (int i = 0; i <= dev::kMaxLevels; ++i) {
-    a.fwd_off[i] = i < (int)p.fwd.off.size() ? p.fwd.off[i] : 0;
-    a.rev_off[i] = i < (int)p.rev.off.size() ? p.rev.off[i] : 0;
-  }
   static_assert(kLoeWarps == dev::kLoeStreamWarps, "per-warp stream layout and kernel disagree");
-  a.stream = dt.loe_stream;
-  for (int w = 0; w <= kLoeWarps; ++w) a.wbeg[w] = dt.loe_wbeg[w];
-  a.check = checked_mode() ? 1 : 0;
-  a.status = d->status;
+  dev::LoeArgs a{};
+  fill_loe_args(d, dt, A, phibar, n_env, phi, dA, a);
+  a.n_tiles = n_tiles;  // 64 environments per tile for the two-environments-per-lane form
   void* args[] = {&a};
   e = cudaLaunchKernel(k, dim3((unsigned)grid), dim3(nt), args, smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
