@@ -585,3 +585,27 @@ def test_adjoint_row_permutation(name):
     assert sum(permuted) < sum(ident)
     if name == "stress_k810":   # measured with this plan: 826 + 1,239 against 1,206 + 2,071
         assert sum(permuted) <= 0.7 * sum(ident)
+
+
+def test_device_forces_entry_point_checks_arguments_before_the_device():
+    """ace_energy_forces (device buffers) rejects bad requests before any CUDA call (no GPU needed): a
+    graph over another one-particle set, missing outputs, a non-positive cutoff, sizes out of range;
+    ace_energy_forces_plan rejects a missing graph."""
+    w = W.WORKLOADS["forces_k392"]
+    d = Dag(Spec.from_workload(w))
+    buf = np.zeros(64, np.float32)
+    off = np.zeros(4, np.int64)
+    p = buf.ctypes.data
+
+    def call(lmax=w.lmax, rc=w.rc, phi=p, forces=p, n_env=3, n_pairs=6, nmin=w.nmin):
+        L.ace_energy_forces(d.handle, p, 0, off.ctypes.data, n_env, n_pairs, 0, 0, rc, nmin, w.nmax, lmax, 0,
+                            phi, forces, 0)
+
+    for kw, word in ((dict(lmax=w.lmax - 1), "K"), (dict(phi=0), "NULL"), (dict(forces=0), "NULL"),
+                     (dict(rc=0.0), "rc"), (dict(n_env=-1), ">= 0"), (dict(nmin=w.nmax + 1), "nmin")):
+        with pytest.raises(L.AceError) as e:
+            call(**kw)
+        assert e.value.status == -1 and word in str(e.value), (kw, str(e.value))
+    with pytest.raises(L.AceError) as e:
+        L.ace_energy_forces_plan(0, w.nmin, w.nmax, w.lmax, 0)
+    assert e.value.status == -1
