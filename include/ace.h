@@ -304,12 +304,11 @@ ace_status ace_eval_plain_f64(ace_dag* dag, const double* A, const double* c, co
  * fails with ACE_ERR_INVALID_ARG before any CUDA call, with a message giving
  * the bytes needed and the largest n_env that fits; nothing is truncated or
  * split.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it for the life of the process; make that
- * first call before any stream capture.  The cached address does not survive
- * cudaDeviceReset (or any other teardown of the device's primary context):
- * after one, do not call this entry point again in the same process.  Every
- * call on a device shares the array and the kernel
- * writes each scratch value before reading it, so nothing is cleared between
+ * (cudaGetSymbolAddress) and caches it for the life of the process.  The
+ * cached address does not survive cudaDeviceReset (or any other teardown of
+ * the device's primary context): after one, do not call this entry point
+ * again in the same process.  Every call on a device shares the array and the
+ * kernel writes each scratch value before reading it, so nothing is cleared between
  * calls; calls whose work overlaps on the GPU (other streams, other threads)
  * race on the array and must be serialised by the caller.  The graph handle is
  * used on the host only (no upload).  Arguments and results are those of
