@@ -33,6 +33,10 @@ import time
 
 import numpy as np
 
+# kernel forms by their ACE_KERNEL value, named as the autotuner names them
+_FORCED_NAMES = {"lon": "tile_per_lane", "loe": "env_per_lane", "loeg": "env_per_lane_global",
+                 "loeg2": "env_pair_per_lane_global", "loem": "env_per_lane_multi"}
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
@@ -397,6 +401,12 @@ def main():
     dag = Dag(spec, algo=args.algo, n_split=args.n_split)
     # kernel form and environments per CTA chosen by the autotuner for exactly this request
     tuned = dag.autotune(w.n_env, w.n_out, torch.float32, w.grad, args.readout)
+    tuned["by"] = "autotuner"
+    forced = {k: os.environ[k] for k in ("ACE_KERNEL", "ACE_TILE_E") if os.environ.get(k)}
+    if forced:
+        # an environment override makes every launch take the forced form, whatever the tuner kept
+        tuned = {"kernel": _FORCED_NAMES.get(forced.get("ACE_KERNEL", "lon"), forced.get("ACE_KERNEL")),
+                 "E": int(forced.get("ACE_TILE_E", 0)), "by": " ".join(f"{k}={v}" for k, v in forced.items())}
     n_ge2 = dag.n_nodes - dag.K
     mode = "forward" if not w.grad else "forward+adjoint"
     ops_env = algorithmic_ops(w, n_ge2, dag.n_basis, mode)
@@ -605,7 +615,7 @@ def main():
                        "n_nodes": dag.n_nodes, "n_aux": dag.n_aux, "n_operands": dag.n_operands,
                        "n_sinks": dag.n_sinks, "mode": mode, "readout": args.readout,
                        "graph": {"algorithm": args.algo, **({"n": args.n_split} if args.algo == 2 else {})},
-                       "kernel_config": {"kernel": tuned["kernel"], "E": tuned["E"], "by": "autotuner",
+                       "kernel_config": {"kernel": tuned["kernel"], "E": tuned["E"], "by": tuned["by"],
                                          **({"forces_form": step.forces_form()} if w.pooling else {})},
                        "launch": "direct" if args.no_graph else "CUDA graph replay (one graph per buffer set)",
                        "l2": f"inputs larger than L2: {n_sets} rotating buffer sets of {per_set / 1e6:.0f} MB"},
