@@ -369,8 +369,11 @@ ace_status ace_pool_A_feat_grad(const float* pos, const float* mu, const int64_t
  *   three-kernel ace_pool_A_feat -> ace_eval_grad -> ace_pool_A_feat_grad through A and dA
  *               buffers of the batch kept in the handle (allocated by the first such call).
  * The three-kernel form runs by default (measured faster on GB300 with 50,000 environments of
- * 10-60 neighbours and K = 392: 0.678 ms against 0.745 ms); ACE_FORCES=fused selects the fused
- * form where it applies.  ace_energy_forces_plan tells which one runs.
+ * 10-60 neighbours and K = 392: 0.645 ms against 0.759 ms); ACE_FORCES=fused selects the fused
+ * form where it applies.  ace_energy_forces_plan tells which one runs.  Calls on one handle share
+ * its A and dA buffers and its bound coefficients, so calls that overlap on the GPU (several
+ * streams or threads) race and must be serialised by the caller; the buffers are replaced (the
+ * old ones freed) when a larger batch arrives.
  *  pos, mu, offsets : dev, as ace_pool_A_feat (offsets are not checked: device memory).
  *  c       : dev [n_basis] float, or NULL (the bound coefficients of the adjoint form).
  *  phi     : dev [n_env] float, written.  forces: dev [n_pairs][3] float, written.
