@@ -1056,7 +1056,7 @@ ace_status check_eval_args(const ace_dag* d, const void* A, int64_t n_env, int n
 // Which form the forces pipeline takes: the fused kernel (pooling, graph forward and adjoint and
 // pooling adjoint in one launch, A and dA in shared memory) or the three kernels.  ACE_FORCES=fused
 // or ACE_FORCES=split chooses; by default the three kernels, measured faster on GB300 (50,000
-// environments of 10-60 neighbours, K = 392: 0.678 ms against 0.745 ms): with one tile per SM the
+// environments of 10-60 neighbours, K = 392: 0.645 ms against 0.759 ms): with one tile per SM the
 // fused kernel's phases cannot overlap, and its last wave of tiles leaves SMs idle.
 constexpr bool kForcesFusedDefault = false;
 
