@@ -609,3 +609,22 @@ def test_device_forces_entry_point_checks_arguments_before_the_device():
     with pytest.raises(L.AceError) as e:
         L.ace_energy_forces_plan(0, w.nmin, w.nmax, w.lmax, 0)
     assert e.value.status == -1
+
+
+def test_binding_without_the_library_fails_loudly(tmp_path):
+    """The product path has no fallback: a copy of the package without libace.so cannot be imported
+    (the ctypes binding and the tensor API both raise ImportError naming the missing library)."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "paper_2202_04140_gb300"
+    pkg.mkdir()
+    for name in os.listdir(os.path.join(ROOT, "paper_2202_04140_gb300")):
+        if name.endswith(".py"):
+            shutil.copy(os.path.join(ROOT, "paper_2202_04140_gb300", name), pkg / name)
+    assert not (pkg / "libace.so").exists()
+    for mod in ("paper_2202_04140_gb300.ace", "paper_2202_04140_gb300.torch_api"):
+        r = subprocess.run([sys.executable, "-c", f"import {mod}"], cwd=tmp_path, capture_output=True, text=True,
+                           env={**os.environ, "PYTHONPATH": str(tmp_path)})
+        assert r.returncode != 0, mod
+        assert "ImportError" in r.stderr and "libace.so is not built" in r.stderr, r.stderr[-500:]
