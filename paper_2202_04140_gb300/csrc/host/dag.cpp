@@ -17,7 +17,7 @@
 //  * Node ids follow insertion order; leaves (the K one-particle nodes) are
 //    0..K-1; auxiliary = order >= 2 and not in the basis set.
 #include <algorithm>
-#include <unordered_map>
+#include <vector>
 
 #include "ace_internal.hpp"
 
@@ -40,6 +40,50 @@ struct KeyHash {
   }
 };
 
+// Node ids by tuple: open addressing with linear probing over a power-of-two table.  The empty
+// slot holds the all-padding key, which no tuple has (ids are below 0xFFFF and a tuple has at
+// least one).  Grown by doubling past a load of 3/4.
+class NodeTable {
+ public:
+  void reserve(size_t n) {
+    size_t cap = 1024;
+    while (3 * cap < 4 * n) cap <<= 1;
+    if (cap > keys_.size()) rehash(cap);
+  }
+  int32_t find(const Key& k) const {
+    if (keys_.empty()) return -1;
+    for (size_t i = KeyHash()(k) & mask_;; i = (i + 1) & mask_) {
+      if (keys_[i] == k) return vals_[i];
+      if (keys_[i] == kEmpty) return -1;
+    }
+  }
+  void insert(const Key& k, int32_t v) {  // k not present
+    if (4 * (used_ + 1) > 3 * keys_.size()) rehash(keys_.empty() ? 1024 : 2 * keys_.size());
+    size_t i = KeyHash()(k) & mask_;
+    while (!(keys_[i] == kEmpty)) i = (i + 1) & mask_;
+    keys_[i] = k;
+    vals_[i] = v;
+    ++used_;
+  }
+
+ private:
+  static constexpr Key kEmpty{~0ULL, ~0ULL};
+  std::vector<Key> keys_;
+  std::vector<int32_t> vals_;
+  size_t mask_ = 0, used_ = 0;
+
+  void rehash(size_t cap) {
+    std::vector<Key> ok = std::move(keys_);
+    std::vector<int32_t> ov = std::move(vals_);
+    keys_.assign(cap, kEmpty);
+    vals_.assign(cap, -1);
+    mask_ = cap - 1;
+    used_ = 0;
+    for (size_t i = 0; i < ok.size(); ++i)
+      if (!(ok[i] == kEmpty)) insert(ok[i], ov[i]);
+  }
+};
+
 struct Tup {
   int32_t n = 0;
   int32_t v[kMaxNu];
@@ -54,35 +98,37 @@ struct Tup {
   }
 };
 
+// Most k1 position sets of one size: C(8, 4) for tuples of at most 8 elements.
+static_assert(kMaxNu <= 8, "Key packs at most 8 ids");
+constexpr int kMaxSubsets = 70;
+
 struct Builder {
   const Spec& s;
   int split_rule;
   int n_split;
   Graph& g;
-  std::unordered_map<Key, int32_t, KeyHash> ids;
+  NodeTable ids;
 
   Builder(const Spec& s_, int rule, int ns, Graph& g_) : s(s_), split_rule(rule), n_split(ns), g(g_) {}
 
   int32_t add(const Tup& t, int32_t l, int32_t r) {
     int32_t id = (int32_t)g.left.size();
-    ids.emplace(t.key(), id);
+    ids.insert(t.key(), id);
     g.left.push_back(l);
     g.right.push_back(r);
     g.order.push_back(t.n);
     return id;
   }
 
-  int32_t find(const Tup& t) const {
-    auto it = ids.find(t.key());
-    return it == ids.end() ? -1 : it->second;
-  }
+  int32_t find(const Tup& t) const { return ids.find(t.key()); }
 
   // Try every decomposition in the fixed order; add k with the first pair found.
   bool try_pairs(const Tup& t) {
     const int nu = t.n;
     for (int step = 0; step < nu / 2; ++step) {
       const int sz = split_rule == ACE_SPLIT_PEEL ? step + 1 : nu / 2 - step;
-      std::vector<Key> seen;
+      Key seen[kMaxSubsets];  // the k1 multisets already tried for this size
+      int n_seen = 0;
       int pos[kMaxNu];
       for (int i = 0; i < sz; ++i) pos[i] = i;
       while (true) {
@@ -95,9 +141,9 @@ struct Builder {
           else b.v[bi++] = t.v[i];
         }
         Key ka = a.key();
-        bool dup = std::find(seen.begin(), seen.end(), ka) != seen.end();
+        bool dup = std::find(seen, seen + n_seen, ka) != seen + n_seen;
         if (!dup) {
-          seen.push_back(ka);
+          seen[n_seen++] = ka;
           int32_t ia = find(a);
           if (ia >= 0) {
             int32_t ib = find(b);
@@ -175,7 +221,7 @@ ace_status build_graph(const Spec& spec, int algo, int split_rule, int n_split, 
   g.K = spec.K;
   g.nu_max = spec.nu_max;
   Builder b(spec, split_rule, n_split, g);
-  b.ids.reserve((size_t)spec.n_basis() * 2 + spec.K);
+  b.ids.reserve((size_t)spec.n_basis() + (size_t)spec.n_basis() / 16 + spec.K);  // basis, auxiliary, leaves
   for (int32_t k = 0; k < spec.K; ++k) {
     Tup t;
     t.n = 1;

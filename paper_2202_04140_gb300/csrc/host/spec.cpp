@@ -22,16 +22,20 @@ struct Walker {
   int32_t D;
   int32_t pnorm;  // 1, 2 or 0 (max)
   bool l_even;
-  // ids grouped by one-particle degree, each group ascending
-  std::vector<std::vector<int32_t>> by_deg;
+  int32_t maxd = 0;
+  // next[b * (K + 1) + k]: the smallest id >= k of one-particle degree <= b (K if none)
+  std::vector<int32_t> next;
   std::vector<std::vector<int32_t>> found;  // per nu: flattened tuples
   int32_t cur[kMaxNu];
 
   Walker(const Spec& s_, int32_t D_, int32_t p_, bool le) : s(s_), D(D_), pnorm(p_), l_even(le) {
-    int32_t maxd = 0;
     for (int32_t d : s.one_deg) maxd = std::max(maxd, d);
-    by_deg.assign(maxd + 1, {});
-    for (int32_t k = 0; k < s.K; ++k) by_deg[s.one_deg[k]].push_back(k);
+    const int32_t K = s.K;
+    next.assign((size_t)(maxd + 1) * (K + 1), K);
+    for (int32_t b = 0; b <= maxd; ++b) {
+      int32_t* nb = next.data() + (size_t)b * (K + 1);
+      for (int32_t k = K - 1; k >= 0; --k) nb[k] = s.one_deg[k] <= b ? k : nb[k + 1];
+    }
     found.assign(s.nu_max + 1, {});
   }
 
@@ -44,22 +48,19 @@ struct Walker {
       }
     }
     if (depth == s.nu_max) return;
-    // candidate children: ids >= last whose degree keeps the tuple within the budget,
-    // visited in ascending id order (merge of the degree groups)
-    std::vector<int32_t> cand;
-    for (size_t d = 0; d < by_deg.size(); ++d) {
-      int64_t nacc;
-      if (pnorm == 1) nacc = acc + (int64_t)d;
-      else if (pnorm == 2) nacc = acc + (int64_t)d * (int64_t)d;
-      else nacc = std::max<int64_t>(acc, (int64_t)d);
-      int64_t lim = (pnorm == 2) ? (int64_t)D * D : (int64_t)D;
-      if (nacc > lim) continue;
-      const auto& grp = by_deg[d];
-      auto it = std::lower_bound(grp.begin(), grp.end(), last);
-      cand.insert(cand.end(), it, grp.end());
-    }
-    std::sort(cand.begin(), cand.end());
-    for (int32_t k : cand) {
+    // children: ids >= last whose degree d keeps the tuple within the budget, in ascending id
+    // order; the budget is a largest admissible degree dlim (sum d <= D, sum d^2 <= D^2, max d <= D)
+    int64_t dlim;
+    if (pnorm == 1) dlim = (int64_t)D - acc;
+    else if (pnorm == 2) {
+      const int64_t r = (int64_t)D * D - acc;
+      dlim = r < 0 ? -1 : (int64_t)std::sqrt((double)r);
+      while (dlim >= 0 && dlim * dlim > r) --dlim;
+      while ((dlim + 1) * (dlim + 1) <= r) ++dlim;
+    } else dlim = D;
+    if (dlim < 0) return;
+    const int32_t* nb = next.data() + (size_t)std::min<int64_t>(dlim, maxd) * (s.K + 1);
+    for (int32_t k = nb[last]; k < s.K; k = nb[k + 1]) {
       int64_t d = s.one_deg[k];
       int64_t nacc = (pnorm == 1) ? acc + d : (pnorm == 2) ? acc + d * d : std::max<int64_t>(acc, d);
       cur[depth] = k;
