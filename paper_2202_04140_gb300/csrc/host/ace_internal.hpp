@@ -78,17 +78,21 @@ constexpr int kLoeBlockRows = 16;
 // stream item that is a block header.
 constexpr int kTaskBlockRow = 8;
 constexpr int kLoeBlockUnit = 16;
+// Most slots the tile-per-lane kernel can keep (its columns are 16-bit): a plan with more has
+// no tile-per-lane layout (the hot and cold tasks below stay empty).
+constexpr int32_t kTileMaxStored = 65535;
 
 struct TaskSet {
   // Tasks grouped in slices of 32 (one per lane); entries of a slice are
-  // interleaved: entry k of lane j sits at slice_off[s] + 32 k + j.
+  // interleaved: entry k of lane j sits at slice_off[s] + 32 k + j.  Built only
+  // when the plan keeps at most kTileMaxStored slots.
   std::vector<Task> tasks;            // [n_slices * 32]
   std::vector<int32_t> slice_off;     // [n_slices + 1] entry offsets
   std::vector<int32_t> slice_steps;   // [n_slices]
   std::vector<int32_t> col;           // [n_entries_padded] slot index
   std::vector<int32_t> ebasis;        // [n_entries_padded] basis index (-1 padding)
   std::vector<uint8_t> ew2;           // [n_entries_padded] 1: weight 2 (diagonal of the symmetric form)
-  int64_t n_entries = 0;              // real (unpadded) entries
+  int64_t n_entries = 0;              // real (unpadded) entries of all rows
   // Cold entries: entries whose column is a top operand that the tile-per-lane
   // kernel does not keep in shared memory (slots >= n_stored).  Such an entry
   // reads the operand's two factor slots (ca, cb < n_g) and multiplies them.

@@ -233,7 +233,7 @@ ace_status upload_tasks(ace_dag* d, const TaskSet& ts, DevTaskSet& dt, cudaStrea
   d->staging32.push_back(std::move(tb));
   if ((s = upload_vec(d, d->staging32.back(), &dt.tbasis, st)) != ACE_OK) return s;
   if ((s = upload_vec(d, ts.col, &dt.col, st)) != ACE_OK) return s;
-  if (d->plan.n_stored <= 65535) {
+  if (d->plan.n_stored <= kTileMaxStored) {
     d->staging16.emplace_back(ts.col.begin(), ts.col.end());
     if ((s = upload_vec(d, d->staging16.back(), &dt.col16, st)) != ACE_OK) return s;
     // packed copy: padding steps of a slice's last group get column 0 and no coefficient

@@ -254,13 +254,22 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
                  int task_len, TaskSet& ts) {
   const int32_t n_slots = (int32_t)rows.size();
   ts = TaskSet();
+  for (const auto& r : rows) ts.n_entries += (int64_t)r.size();
+  // the tile-per-lane layout, only where that kernel can run (every stored column below 2^16);
+  // otherwise no slices: both offset lists hold their final 0
+  const bool tile = n_stored <= kTileMaxStored;
+  if (!tile) {
+    ts.slice_off.assign(1, 0);
+    ts.cold_slice_off.assign(1, 0);
+  }
   // hot entries (column kept in shared memory) and cold ones
-  std::vector<std::vector<Entry>> hot(n_slots), cold(n_slots);
-  for (int32_t s = 0; s < n_slots; ++s)
-    for (const Entry& e : rows[s]) (e.col < n_stored ? hot : cold)[s].push_back(e);
+  std::vector<std::vector<Entry>> hot(tile ? n_slots : 0), cold(tile ? n_slots : 0);
+  if (tile)
+    for (int32_t s = 0; s < n_slots; ++s)
+      for (const Entry& e : rows[s]) (e.col < n_stored ? hot : cold)[s].push_back(e);
 
   // ---- hot tasks: interleaved, bank-scheduled entries
-  {
+  if (tile) {
     std::vector<Task> tasks;
     std::vector<Proto> protos;
     make_tasks(hot, slot_basis, n_g, true, slot_l, slot_r, task_len, tasks, protos);
@@ -280,7 +289,6 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
     ts.col.assign(off, 0);
     ts.ebasis.assign(off, -1);
     ts.ew2.assign(off, 0);
-    ts.n_entries = 0;
     std::vector<std::vector<Entry>> lane_store(32);
     for (int32_t s = 0; s < n_slices; ++s) {
       std::vector<const std::vector<Entry>*> lanes;
@@ -290,7 +298,6 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
         const auto& r = hot[tasks[ti].row];
         lane_store[j].assign(r.begin() + protos[ti].begin, r.begin() + protos[ti].begin + protos[ti].len);
         lanes.push_back(&lane_store[j]);
-        ts.n_entries += protos[ti].len;
       }
       const int64_t base = ts.slice_off[s];
       interleave(
@@ -305,7 +312,7 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
   }
 
   // ---- cold tasks: the operand's two factors per entry, entries in task order
-  {
+  if (tile) {
     std::vector<Task> tasks;
     std::vector<Proto> protos;
     make_tasks(cold, slot_basis, n_g, false, slot_l, slot_r, task_len, tasks, protos);
@@ -336,7 +343,6 @@ void build_tasks(const std::vector<std::vector<Entry>>& rows, const std::vector<
         const auto& r = cold[tasks[ti].row];
         lane_store[j].assign(r.begin() + protos[ti].begin, r.begin() + protos[ti].begin + protos[ti].len);
         lanes.push_back(&lane_store[j]);
-        ts.n_entries += protos[ti].len;
       }
       const int64_t base = ts.cold_slice_off[s];
       interleave(
@@ -614,7 +620,7 @@ ace_status build_plan(const Spec& spec, const Graph& g, int task_len, StoredLimi
     const int64_t n_all = (int64_t)plan.n_g + (int64_t)top_ids.size();
     const int64_t stored_limit = stored_limit_fn ? stored_limit_fn(K, plan.n_g) : 0;
     int64_t keep = (int64_t)top_ids.size();
-    if (stored_limit > 0 && n_all > stored_limit && stored_limit > plan.n_g && n_all <= 65535)
+    if (stored_limit > 0 && n_all > stored_limit && stored_limit > plan.n_g && n_all <= kTileMaxStored)
       keep = stored_limit - plan.n_g;
     if (keep < (int64_t)top_ids.size()) {
       std::vector<int32_t> deg(N, 0);

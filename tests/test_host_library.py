@@ -628,3 +628,25 @@ def test_binding_without_the_library_fails_loudly(tmp_path):
                            env={**os.environ, "PYTHONPATH": str(tmp_path)})
         assert r.returncode != 0, mod
         assert "ImportError" in r.stderr and "libace.so is not built" in r.stderr, r.stderr[-500:]
+
+
+def test_tile_layout_only_where_the_tile_kernel_can_run():
+    """A plan that keeps more than 65,535 slots (the 1.5-million-function set, D = 20) has no
+    tile-per-lane layout: no hot or cold tasks, offset lists holding only their final 0, every
+    entry still in the row-major streams.  A plan within the limit (K = 392, nu <= 4) keeps its layout."""
+    for name, big in (("paper_degree_d20_k810", True), ("fwd_grad_k392", False)):
+        dag = Dag(Spec.from_workload(W.WORKLOADS[name]))
+        n_stored = int(L.ace_dag_plan_array(dag.handle, "n_stored")[0])
+        assert (n_stored > 65535) == big
+        for mode in ("sym", "one"):
+            tasks = L.ace_dag_plan_array(dag.handle, f"{mode}_tasks")
+            slice_off = L.ace_dag_plan_array(dag.handle, f"{mode}_slice_off")
+            cold_off = L.ace_dag_plan_array(dag.handle, f"{mode}_cold_slice_off")
+            rm_off = L.ace_dag_plan_array(dag.handle, f"{mode}_rm_off")
+            assert len(rm_off) > 1 and rm_off[-1] > 0
+            if big:
+                assert len(tasks) == 0 and list(slice_off) == [0] and list(cold_off) == [0]
+                assert len(L.ace_dag_plan_array(dag.handle, f"{mode}_col")) == 0
+            else:
+                assert len(tasks) > 0 and slice_off[-1] == len(L.ace_dag_plan_array(dag.handle, f"{mode}_col"))
+        assert dag.n_entries > 0
