@@ -169,6 +169,13 @@ ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_si
  * unknown name. */
 ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out, int64_t* count);
 
+/* Host-side check of every plan index a kernel reads (forward and adjoint levels, tasks and
+ * their slices, cold entries, the adjoint gather list, the row-major tasks and the per-warp
+ * streams): the check the first upload performs before anything reaches a device.  Needs no
+ * device.  Errors: INVALID_ARG (NULL dag), BOUNDS (an index out of range or an inconsistent
+ * layout; the message names which). */
+ace_status ace_dag_validate(const ace_dag* dag);
+
 void ace_dag_free(ace_dag* dag);
 
 /* ---- evaluation (device) ------------------------------------------------------ */

@@ -1225,6 +1225,11 @@ ace_status ace_dag_plan_info(const ace_dag* dag, int64_t* n_slots, int64_t* n_si
   return ACE_OK;
 }
 
+ace_status ace_dag_validate(const ace_dag* dag) {
+  if (!dag) return fail(ACE_ERR_INVALID_ARG, "dag is NULL");
+  return validate_plan(dag->plan);
+}
+
 ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out, int64_t* count) {
   if (!dag || !name || !count) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
   const Plan& p = dag->plan;

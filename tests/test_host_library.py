@@ -650,3 +650,18 @@ def test_tile_layout_only_where_the_tile_kernel_can_run():
             else:
                 assert len(tasks) > 0 and slice_off[-1] == len(L.ace_dag_plan_array(dag.handle, f"{mode}_col"))
         assert dag.n_entries > 0
+
+
+@pytest.mark.parametrize("name,algo,stored", [(n, 1, None) for n in sorted(W.WORKLOADS) if n != "paper_degree_k810"] +
+                         [("fwd_grad_k392", 2, None), ("stress_k810", 2, None), ("fwd_grad_k392", 1, "600"),
+                          ("stress_k810", 1, "6000")])
+def test_plan_passes_the_library_validation(name, algo, stored, monkeypatch):
+    """Every workload's plan (Algorithm 1 and 2; the 1.5-million-function set without a tile
+    layout; plans forced onto the cold path by a small stored-slot limit) passes the host check
+    that the first upload runs before anything reaches the device."""
+    if stored:
+        monkeypatch.setenv("ACE_PLAN_STORED", stored)
+    dag = Dag(Spec.from_workload(W.WORKLOADS[name]), algo=algo)
+    L.ace_dag_validate(dag.handle)
+    if stored:
+        assert len(L.ace_dag_plan_array(dag.handle, "sym_cold_tasks")) > 0
