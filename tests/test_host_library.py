@@ -84,9 +84,8 @@ def test_dag_matches_oracle(kind, kw, ob, algo, rule):
     assert np.array_equal(ex["level"], od.order.astype(np.int32))
 
 
-# the 17.3-million-function set takes about two minutes to build; its digests are checked by
-# tests/test_gpu_paper_degree.py before the evaluation there
-@pytest.mark.parametrize("name", sorted(n for n in GOLDEN if n != "paper_degree_k810"))
+# every workload, the 17.3-million-function set included (about 25 s to build)
+@pytest.mark.parametrize("name", sorted(GOLDEN))
 def test_workload_digests(name):
     """Bit-exact against the oracle's digests (written by tests/golden/make_golden.py)."""
     g = GOLDEN[name]
@@ -652,12 +651,12 @@ def test_tile_layout_only_where_the_tile_kernel_can_run():
         assert dag.n_entries > 0
 
 
-@pytest.mark.parametrize("name,algo,stored", [(n, 1, None) for n in sorted(W.WORKLOADS) if n != "paper_degree_k810"] +
+@pytest.mark.parametrize("name,algo,stored", [(n, 1, None) for n in sorted(W.WORKLOADS)] +
                          [("fwd_grad_k392", 2, None), ("stress_k810", 2, None), ("fwd_grad_k392", 1, "600"),
                           ("stress_k810", 1, "6000")])
 def test_plan_passes_the_library_validation(name, algo, stored, monkeypatch):
-    """Every workload's plan (Algorithm 1 and 2; the 1.5-million-function set without a tile
-    layout; plans forced onto the cold path by a small stored-slot limit) passes the host check
+    """Every workload's plan (Algorithm 1 and 2; the paper-degree sets without a tile layout; plans
+    forced onto the cold path by a small stored-slot limit) passes the host check
     that the first upload runs before anything reaches the device."""
     if stored:
         monkeypatch.setenv("ACE_PLAN_STORED", stored)
