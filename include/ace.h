@@ -176,6 +176,25 @@ ace_status ace_dag_plan_array(const ace_dag* dag, const char* name, int32_t* out
  * layout; the message names which). */
 ace_status ace_dag_validate(const ace_dag* dag);
 
+/* Write a graph to the file `path`: the parameters of its index set, the options it was built
+ * with, and the graph itself (left factor, right factor and correlation order of every node, and
+ * the node of every basis function), as a versioned little-endian file ending in the FNV-1a
+ * 64-bit checksum of everything before it.  The evaluation plan is not stored (ace_dag_load
+ * rebuilds it).  `spec` must be the index set the graph was built from.  Host only.
+ * Errors: INVALID_ARG (NULL argument, a graph of another index set, the file cannot be
+ * written), OOM. */
+ace_status ace_dag_save(const ace_spec* spec, const ace_dag* dag, const char* path);
+
+/* Read a file written by ace_dag_save into a new index set and graph (both owned by the caller:
+ * ace_spec_free, ace_dag_free).  The index set is rebuilt from the stored parameters and must
+ * equal the stored one (size and checksum of its tuples); the graph is checked before use:
+ * leaves first, every other node the product of two earlier nodes with the sum of their orders,
+ * every basis function's node distinct, of its order and of its tuple (by a multiset hash); the
+ * plan is then rebuilt.  *params (may be NULL) receives the index set's parameters.  Host only.
+ * Errors: INVALID_ARG (unreadable file, wrong magic or version, checksum mismatch, sizes that do
+ * not match, an index set this library builds differently, a graph that fails a check), OOM. */
+ace_status ace_dag_load(const char* path, ace_spec_params* params, ace_spec** spec_out, ace_dag** dag_out);
+
 void ace_dag_free(ace_dag* dag);
 
 /* ---- evaluation (device) ------------------------------------------------------ */

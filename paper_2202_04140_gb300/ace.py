@@ -32,7 +32,7 @@ ACE_READOUT_PLAIN, ACE_READOUT_COMPENSATED, ACE_READOUT_FP64_FINAL = 0, 1, 2
 EXPORTED = [
     "ace_last_error", "ace_abi_version", "ace_build_spec", "ace_spec_info", "ace_spec_tuples",
     "ace_spec_free", "ace_build_dag", "ace_dag_info", "ace_dag_export", "ace_dag_plan_info",
-    "ace_dag_plan_array", "ace_dag_validate", "ace_dag_free", "ace_dag_upload", "ace_dag_autotune", "ace_eval", "ace_eval_grad",
+    "ace_dag_plan_array", "ace_dag_validate", "ace_dag_save", "ace_dag_load", "ace_dag_free", "ace_dag_upload", "ace_dag_autotune", "ace_eval", "ace_eval_grad",
     "ace_eval_host", "ace_eval_grad_host", "ace_eval_plain_workspace_bytes",
     "ace_eval_plain_f64", "ace_eval_plain_f64_static", "ace_pool_A", "ace_pool_A_grad", "ace_pool_A_feat", "ace_pool_A_feat_grad", "ace_energy_forces", "ace_energy_forces_plan", "ace_energy_forces_host", "ace_stream_status", "ace_device_info",
     "ace_fma_peak",
@@ -70,6 +70,8 @@ _SIG = {
     "ace_dag_plan_info": (C.c_int, [_p, _P(_i64), _P(_i64), _P(_i64), _P(_i64)]),
     "ace_dag_plan_array": (C.c_int, [_p, C.c_char_p, _p, _P(_i64)]),
     "ace_dag_validate": (C.c_int, [_p]),
+    "ace_dag_save": (C.c_int, [_p, _p, C.c_char_p]),
+    "ace_dag_load": (C.c_int, [C.c_char_p, _P(ace_spec_params), _P(_p), _P(_p)]),
     "ace_dag_free": (None, [_p]),
     "ace_dag_upload": (C.c_int, [_p, _p]),
     "ace_dag_autotune": (C.c_int, [_p, _i64, _i32, _i32, _i32, _i32, _p, _P(_i32), _P(_i32), _P(C.c_float)]),
@@ -185,6 +187,18 @@ def ace_dag_plan_array(dag: int, name: str) -> np.ndarray:
 
 def ace_dag_validate(dag: int):
     _check(_lib.ace_dag_validate(dag), "ace_dag_validate")
+
+
+def ace_dag_save(spec: int, dag: int, path: str):
+    _check(_lib.ace_dag_save(spec, dag, os.fsencode(path)), "ace_dag_save")
+
+
+def ace_dag_load(path: str):
+    """Returns (params as a dict, spec handle, dag handle) of a file written by ace_dag_save."""
+    prm = ace_spec_params()
+    s, d = C.c_void_p(), C.c_void_p()
+    _check(_lib.ace_dag_load(os.fsencode(path), C.byref(prm), C.byref(s), C.byref(d)), "ace_dag_load")
+    return {name: getattr(prm, name) for name, _ in ace_spec_params._fields_}, s.value, d.value
 
 
 def ace_dag_free(dag: int, _free=_lib.ace_dag_free):

@@ -50,6 +50,16 @@ struct Graph {
 
 ace_status build_graph(const Spec& spec, int algo, int split_rule, int n_split, Graph& g);
 
+// Options a graph and its plan were built with (kept with the graph, written to graph files).
+struct GraphOptions {
+  int32_t algo = 1, split_rule = 0, n_split = 2, task_len = 64;
+};
+
+// Graph files (checkpoint.cpp): the index set's parameters, the options and the graph, with a
+// checksum; load_graph rebuilds the index set, checks it and the graph, and fills g.
+ace_status save_graph(const std::string& path, const Spec& spec, const Graph& g, const GraphOptions& o);
+ace_status load_graph(const std::string& path, std::unique_ptr<Spec>& spec, Graph& g, GraphOptions& o);
+
 // Evaluation plan (section 2.6 recursion laid out for the fused kernels).
 //
 // Slots are the values kept per environment: [0, K) the leaves A_k, then the

@@ -110,6 +110,7 @@ struct ace_dag {
   int32_t K = 0;
   int64_t n_basis = 0;
   Graph g;
+  GraphOptions opts;  // how g and plan were built
   Plan plan;
   int device = -1;
   int sm_count = 0, smem_optin = 0;
@@ -1169,6 +1170,7 @@ ace_status ace_build_dag(const ace_spec* spec, int32_t algo, int32_t split_rule,
     if (st != ACE_OK) return st;
     int task_len = 64;
     if (const char* v = std::getenv("ACE_TASK_LEN")) task_len = std::max(1, std::atoi(v));
+    d->opts = GraphOptions{algo, split_rule, n_split, task_len};
     st = build_plan(*spec->s, d->g, task_len, stored_slot_limit, d->plan);
     if (st != ACE_OK) return st;
     d->K = spec->s->K;
@@ -1179,6 +1181,44 @@ ace_status ace_build_dag(const ace_spec* spec, int32_t algo, int32_t split_rule,
     return fail(ACE_ERR_OOM, "host allocation failed");
   } catch (...) {
     return fail(ACE_ERR_INVALID_ARG, "unexpected error building the graph");
+  }
+}
+
+ace_status ace_dag_save(const ace_spec* spec, const ace_dag* dag, const char* path) {
+  if (!spec || !dag || !path) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
+  if (spec->s->K != dag->K || spec->s->n_basis() != dag->n_basis ||
+      (int64_t)dag->g.basis_node.size() != dag->n_basis)
+    return fail(ACE_ERR_INVALID_ARG, "the graph was not built from this index set");
+  try {
+    return save_graph(path, *spec->s, dag->g, dag->opts);
+  } catch (const std::bad_alloc&) {
+    return fail(ACE_ERR_OOM, "host allocation failed");
+  }
+}
+
+ace_status ace_dag_load(const char* path, ace_spec_params* params, ace_spec** spec_out, ace_dag** dag_out) {
+  if (!path || !spec_out || !dag_out) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
+  *spec_out = nullptr;
+  *dag_out = nullptr;
+  try {
+    std::unique_ptr<Spec> s;
+    auto d = std::make_unique<ace_dag>();
+    ace_status st = load_graph(path, s, d->g, d->opts);
+    if (st != ACE_OK) return st;
+    st = build_plan(*s, d->g, d->opts.task_len, stored_slot_limit, d->plan);
+    if (st != ACE_OK) return st;
+    d->K = s->K;
+    d->n_basis = s->n_basis();
+    if (params) *params = s->p;
+    auto* h = new ace_spec;
+    h->s = std::move(s);
+    *spec_out = h;
+    *dag_out = d.release();
+    return ACE_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(ACE_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(ACE_ERR_INVALID_ARG, "unexpected error reading the graph file");
   }
 }
 

@@ -43,6 +43,17 @@ class Spec:
         self._tuples = None
 
     @classmethod
+    def _from_handle(cls, handle: int, params: dict) -> "Spec":
+        """Wrap an index-set handle the library built (params: its ace_spec_params)."""
+        self = cls.__new__(cls)
+        self.group = {v: k for k, v in _GROUP.items()}[params["group"]]
+        self.nu_max = params["nu_max"]
+        self.handle = handle
+        self.n_basis, self.K, self.counts_per_nu = L.ace_spec_info(handle, self.nu_max)
+        self._tuples = None
+        return self
+
+    @classmethod
     def from_workload(cls, w) -> "Spec":
         return cls("O3", w.nmin, w.nmax, w.lmax, w.nu_max, w.deg_max, w.wn, w.wl, 1, True, w.kmax, w.wk)
 
@@ -66,8 +77,23 @@ class Dag:
     """The computational graph G (section 2.6, Algorithm 1 or 2) and its device plan."""
 
     def __init__(self, spec: Spec, algo: int = 1, rule: str = "balanced", n_split: int = 2):
+        self._attach(spec, L.ace_build_dag(spec.handle, algo, _RULE[rule], n_split))
+
+    def save(self, path: str):
+        """Write the graph and its index set's parameters to a file (ace_dag_save)."""
+        L.ace_dag_save(self.spec.handle, self.handle, path)
+
+    @classmethod
+    def load(cls, path: str) -> "Dag":
+        """A graph read from a file written by save (ace_dag_load); .spec is its index set."""
+        params, sh, dh = L.ace_dag_load(path)
+        self = cls.__new__(cls)
+        self._attach(Spec._from_handle(sh, params), dh)
+        return self
+
+    def _attach(self, spec: Spec, handle: int):
         self.spec = spec
-        self.handle = L.ace_build_dag(spec.handle, algo, _RULE[rule], n_split)
+        self.handle = handle
         self.n_nodes, self.n_aux, self.n_operands, self.n_levels = L.ace_dag_info(self.handle)
         self.n_slots, self.n_sinks, self.n_entries, self.smem_bytes_f32 = L.ace_dag_plan_info(self.handle)
         self.K = spec.K
