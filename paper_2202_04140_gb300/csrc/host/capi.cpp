@@ -8,6 +8,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../kernels/fused.cuh"
 #include "../kernels/launch.hpp"
@@ -40,6 +41,14 @@ struct ace_spec {
 };
 
 namespace {
+
+// NVTX range over an entry point's host work (a no-op unless a profiler attaches to NVTX)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct DevTaskSet {
   int4* tasks = nullptr;
@@ -1110,6 +1119,7 @@ const char* ace_last_error(void) { return ace::last_error_cstr(); }
 int32_t ace_abi_version(void) { return ACE_ABI_VERSION; }
 
 ace_status ace_build_spec(const ace_spec_params* params, ace_spec** out) {
+  NvtxRange nvtx_range("ace_build_spec");
   if (!params || !out) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   try {
@@ -1162,16 +1172,24 @@ int64_t stored_slot_limit(int32_t K, int32_t n_g) {
 }
 
 ace_status ace_build_dag(const ace_spec* spec, int32_t algo, int32_t split_rule, int32_t n_split, ace_dag** out) {
+  NvtxRange nvtx_range("ace_build_dag");
   if (!spec || !out) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   try {
     auto d = std::make_unique<ace_dag>();
-    ace_status st = build_graph(*spec->s, algo, split_rule, n_split, d->g);
+    ace_status st;
+    {
+      NvtxRange phase("graph");
+      st = build_graph(*spec->s, algo, split_rule, n_split, d->g);
+    }
     if (st != ACE_OK) return st;
     int task_len = 64;
     if (const char* v = std::getenv("ACE_TASK_LEN")) task_len = std::max(1, std::atoi(v));
     d->opts = GraphOptions{algo, split_rule, n_split, task_len};
-    st = build_plan(*spec->s, d->g, task_len, stored_slot_limit, d->plan);
+    {
+      NvtxRange phase("plan");
+      st = build_plan(*spec->s, d->g, task_len, stored_slot_limit, d->plan);
+    }
     if (st != ACE_OK) return st;
     d->K = spec->s->K;
     d->n_basis = spec->s->n_basis();
@@ -1185,6 +1203,7 @@ ace_status ace_build_dag(const ace_spec* spec, int32_t algo, int32_t split_rule,
 }
 
 ace_status ace_dag_save(const ace_spec* spec, const ace_dag* dag, const char* path) {
+  NvtxRange nvtx_range("ace_dag_save");
   if (!spec || !dag || !path) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
   if (spec->s->K != dag->K || spec->s->n_basis() != dag->n_basis ||
       (int64_t)dag->g.basis_node.size() != dag->n_basis)
@@ -1197,6 +1216,7 @@ ace_status ace_dag_save(const ace_spec* spec, const ace_dag* dag, const char* pa
 }
 
 ace_status ace_dag_load(const char* path, ace_spec_params* params, ace_spec** spec_out, ace_dag** dag_out) {
+  NvtxRange nvtx_range("ace_dag_load");
   if (!path || !spec_out || !dag_out) return fail(ACE_ERR_INVALID_ARG, "NULL argument");
   *spec_out = nullptr;
   *dag_out = nullptr;
@@ -1382,12 +1402,14 @@ void ace_dag_free(ace_dag* dag) {
 }
 
 ace_status ace_dag_upload(ace_dag* dag, void* stream) {
+  NvtxRange nvtx_range("ace_dag_upload");
   if (!dag) return fail(ACE_ERR_INVALID_ARG, "dag is NULL");
   return ensure_uploaded(dag, (cudaStream_t)stream);
 }
 
 ace_status ace_eval(ace_dag* dag, const void* A, const void* c, int64_t n_env, int32_t n_out, int32_t dtype,
                     int32_t readout, void* phi, void* stream) {
+  NvtxRange nvtx_range("ace_eval");
   ace_status s = check_eval_args(dag, A, n_env, n_out, dtype, readout);
   if (s != ACE_OK) return s;
   if (n_env > 0 && !phi) return fail(ACE_ERR_INVALID_ARG, "phi is NULL");
@@ -1401,6 +1423,7 @@ ace_status ace_eval(ace_dag* dag, const void* A, const void* c, int64_t n_env, i
 
 ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void* phi_bar, int64_t n_env,
                          int32_t n_out, int32_t dtype, int32_t readout, void* phi, void* dA, void* stream) {
+  NvtxRange nvtx_range("ace_eval_grad");
   ace_status s = check_eval_args(dag, A, n_env, n_out, dtype, readout);
   if (s != ACE_OK) return s;
   if (n_env > 0 && !dA) return fail(ACE_ERR_INVALID_ARG, "dA is NULL");
@@ -1414,6 +1437,7 @@ ace_status ace_eval_grad(ace_dag* dag, const void* A, const void* c, const void*
 
 ace_status ace_eval_host(ace_dag* dag, const void* A, const void* c, int64_t n_env, int32_t n_out, int32_t dtype,
                          int32_t readout, void* phi, int64_t chunk_env, void* stream) {
+  NvtxRange nvtx_range("ace_eval_host");
   ace_status s = check_eval_args(dag, nullptr, 0, n_out, dtype, readout);
   if (s != ACE_OK) return s;
   if (n_env < 0 || chunk_env < 0) return fail(ACE_ERR_INVALID_ARG, "n_env and chunk_env must be >= 0");
@@ -1426,6 +1450,7 @@ ace_status ace_eval_host(ace_dag* dag, const void* A, const void* c, int64_t n_e
 ace_status ace_eval_grad_host(ace_dag* dag, const void* A, const void* c, const void* phi_bar, int64_t n_env,
                               int32_t n_out, int32_t dtype, int32_t readout, void* phi, void* dA, int64_t chunk_env,
                               void* stream) {
+  NvtxRange nvtx_range("ace_eval_grad_host");
   ace_status s = check_eval_args(dag, nullptr, 0, n_out, dtype, readout);
   if (s != ACE_OK) return s;
   if (n_env < 0 || chunk_env < 0) return fail(ACE_ERR_INVALID_ARG, "n_env and chunk_env must be >= 0");
@@ -1436,6 +1461,7 @@ ace_status ace_eval_grad_host(ace_dag* dag, const void* A, const void* c, const 
 
 ace_status ace_dag_autotune(ace_dag* dag, int64_t n_env, int32_t n_out, int32_t dtype, int32_t grad, int32_t readout,
                             void* stream, int32_t* best_kind, int32_t* best_E, float* best_ms) {
+  NvtxRange nvtx_range("ace_dag_autotune");
   ace_status s = check_eval_args(dag, nullptr, 0, n_out, dtype, readout);
   if (s != ACE_OK) return s;
   if (n_env < 1) return fail(ACE_ERR_INVALID_ARG, "n_env must be >= 1");
@@ -1527,6 +1553,7 @@ ace_status ace_eval_plain_workspace_bytes(const ace_dag* dag, int64_t n_env, int
 ace_status ace_eval_plain_f64(ace_dag* dag, const double* A, const double* c, const double* phi_bar,
                               int64_t n_env, int32_t n_out, double* phi, double* dA, void* workspace,
                               size_t workspace_bytes, void* stream) {
+  NvtxRange nvtx_range("ace_eval_plain_f64");
   ace_status s = check_eval_args(dag, A, n_env, n_out, ACE_F64, 0);
   if (s != ACE_OK) return s;
   if (n_env == 0) return ACE_OK;
@@ -1603,6 +1630,7 @@ static ace_status check_pool_args(const float* pos, const int64_t* offsets, int6
 
 ace_status ace_pool_A_feat(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env, int64_t n_pairs,
                            float rc, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax, float* A, void* stream) {
+  NvtxRange nvtx_range("ace_pool_A_feat");
   ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, mu, kmax);
   if (s != ACE_OK) return s;
   if (n_env == 0) return ACE_OK;
@@ -1616,6 +1644,7 @@ ace_status ace_pool_A_feat(const float* pos, const float* mu, const int64_t* off
 ace_status ace_pool_A_feat_grad(const float* pos, const float* mu, const int64_t* offsets, int64_t n_env,
                                 int64_t n_pairs, float rc, int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax,
                                 const float* dA, float alpha, float* dpos, void* stream) {
+  NvtxRange nvtx_range("ace_pool_A_feat_grad");
   ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, mu, kmax);
   if (s != ACE_OK) return s;
   if (n_env == 0) return ACE_OK;
@@ -1628,12 +1657,14 @@ ace_status ace_pool_A_feat_grad(const float* pos, const float* mu, const int64_t
 
 ace_status ace_pool_A(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
                       int32_t nmin, int32_t nmax, int32_t lmax, float* A, void* stream) {
+  NvtxRange nvtx_range("ace_pool_A");
   return ace_pool_A_feat(pos, nullptr, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, 0, A, stream);
 }
 
 ace_status ace_pool_A_grad(const float* pos, const int64_t* offsets, int64_t n_env, int64_t n_pairs, float rc,
                            int32_t nmin, int32_t nmax, int32_t lmax, const float* dA, float alpha, float* dpos,
                            void* stream) {
+  NvtxRange nvtx_range("ace_pool_A_grad");
   return ace_pool_A_feat_grad(pos, nullptr, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, 0, dA, alpha, dpos,
                               stream);
 }
@@ -1642,6 +1673,7 @@ ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* m
                                   int64_t n_env, int64_t n_pairs, const void* c, int32_t readout, float rc,
                                   int32_t nmin, int32_t nmax, int32_t lmax, int32_t kmax, float* phi, float* forces,
                                   int64_t chunk_env, void* stream) {
+  NvtxRange nvtx_range("ace_energy_forces_host");
   ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, mu, kmax);
   if (s != ACE_OK) return s;
   if ((s = check_eval_args(dag, nullptr, 0, 1, ACE_F32, readout)) != ACE_OK) return s;
@@ -1726,6 +1758,7 @@ ace_status ace_energy_forces_host(ace_dag* dag, const float* pos, const float* m
 ace_status ace_energy_forces(ace_dag* dag, const float* pos, const float* mu, const int64_t* offsets, int64_t n_env,
                              int64_t n_pairs, const void* c, int32_t readout, float rc, int32_t nmin, int32_t nmax,
                              int32_t lmax, int32_t kmax, float* phi, float* forces, void* stream) {
+  NvtxRange nvtx_range("ace_energy_forces");
   ace_status s = check_pool_args(pos, offsets, n_env, n_pairs, rc, nmin, nmax, lmax, mu, kmax);
   if (s != ACE_OK) return s;
   if ((s = check_eval_args(dag, nullptr, 0, 1, ACE_F32, readout)) != ACE_OK) return s;
