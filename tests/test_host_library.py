@@ -664,3 +664,19 @@ def test_plan_passes_the_library_validation(name, algo, stored, monkeypatch):
     L.ace_dag_validate(dag.handle)
     if stored:
         assert len(L.ace_dag_plan_array(dag.handle, "sym_cold_tasks")) > 0
+
+
+def test_per_warp_stream_emulation_paper_degree_d20():
+    """The streams the global-workspace kernels walk for the 1.5-million-function set (a plan
+    without a tile layout): forward and adjoint in FP64 on 2 environments against the oracle's
+    term-by-term sums (about 35 s)."""
+    w = W.WORKLOADS["paper_degree_d20_k810"]
+    o = workload_index_set(w)
+    s = Spec.from_workload(w)
+    dag = Dag(s)
+    A = W.draw_A(2, s.K, env_scale=w.env_scale)
+    c = W.draw_c(o.deg, 1)
+    pb = np.random.default_rng(3).standard_normal((2, 1))
+    phi, dA = emulate_loe_streams(dag, "sym", A, c, pb)
+    assert normalized_error(phi[:, None], phi_naive(A, o, c), error_scale(A, o, c)) < 1e-12
+    assert normalized_error(dA, grad_naive(A, o, c, pb), grad_error_scale(A, o, c, pb)) < 1e-12
