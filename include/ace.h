@@ -25,8 +25,12 @@
  *    CUDA device pointers on the current device, contiguous, 16-byte aligned;
  *    "host" pointers are ordinary host memory.  Row-major layouts throughout.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
- *    work is enqueued asynchronously; nothing synchronises except
- *    ace_stream_status.  Launch errors are reported at enqueue time.
+ *    work is enqueued asynchronously; the calls that wait are
+ *    ace_stream_status, the first use of a handle on a device (the plan upload
+ *    waits for its copies), and calls that allocate or replace a buffer of the
+ *    handle (cudaMalloc / cudaFree may synchronise the device): the first
+ *    request of a kind, or one larger than any before.  Launch errors are
+ *    reported at enqueue time.
  *  - One-particle ids: O(3) id = (n - nmin)(lmax+1)^2 + l^2 + (l + m);
  *    SO(2) id = (n - nmin)(2 lmax + 1) + (m + lmax); torus id = m + lmax.
  *  - Basis order ("canonical"): by correlation order nu, then lexicographic on
