@@ -18,7 +18,8 @@ import numpy as np
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libace.so")
 
 ACE_OK = 0
-ACE_ERR_TIMEOUT, ACE_ERR_BOUNDS = -4, -5
+ACE_ERR_INVALID_ARG, ACE_ERR_OOM, ACE_ERR_CUDA = -1, -2, -3
+ACE_ERR_TIMEOUT, ACE_ERR_BOUNDS, ACE_ERR_UNSUPPORTED, ACE_ERR_NO_DEVICE = -4, -5, -6, -7
 STATUS_NAMES = {0: "ACE_OK", -1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_OOM", -3: "ACE_ERR_CUDA",
                 -4: "ACE_ERR_TIMEOUT", -5: "ACE_ERR_BOUNDS", -6: "ACE_ERR_UNSUPPORTED",
                 -7: "ACE_ERR_NO_DEVICE"}

@@ -94,7 +94,7 @@ def test_damaged_and_foreign_files_are_refused(tmp_path):
             rewrite(bad, data)
         with pytest.raises(L.AceError) as err:
             Dag.load(bad)
-        assert err.value.status == -1 and words in str(err.value), str(err.value)
+        assert err.value.status == L.ACE_ERR_INVALID_ARG and words in str(err.value), str(err.value)
 
     # a flipped byte, a truncated file, another file type
     flipped = bytearray(raw)
@@ -130,11 +130,11 @@ def test_save_and_load_check_their_arguments(tmp_path):
     other = Spec.from_workload(W.WORKLOADS["fwd_grad_k392"])
     with pytest.raises(L.AceError) as err:
         L.ace_dag_save(other.handle, d.handle, str(tmp_path / "x"))
-    assert err.value.status == -1 and "not built from this index set" in str(err.value)
+    assert err.value.status == L.ACE_ERR_INVALID_ARG and "not built from this index set" in str(err.value)
     with pytest.raises(L.AceError) as err:
         L.ace_dag_load(str(tmp_path / "missing.acegraph"))
-    assert err.value.status == -1 and "cannot open" in str(err.value)
+    assert err.value.status == L.ACE_ERR_INVALID_ARG and "cannot open" in str(err.value)
     with pytest.raises(L.AceError) as err:
         d.save(str(tmp_path / "no_such_dir" / "g.acegraph"))
-    assert err.value.status == -1 and "cannot open" in str(err.value)
+    assert err.value.status == L.ACE_ERR_INVALID_ARG and "cannot open" in str(err.value)
     assert os.path.exists(str(tmp_path)) and not os.path.exists(str(tmp_path / "x"))
